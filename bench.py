@@ -1,0 +1,414 @@
+"""Throughput benchmark of the fused FDTD leapfrog (arXiv 2401.07416) on GB300.
+
+Workload (default): the 512 x 512 x 1024 throughput run (h = 0.05 bohr, 4-layer
+16 x 16 softened-Coulomb slab, cos^2 absorbing layers at the z ends, detector
+flux every step, norm/energy reductions every 20 steps), psi and V stored in FP32
+with Kahan-compensated updates, two time steps fused per kernel launch.  One
+bench step = one leapfrog time step of the whole grid.  Inputs are synthetic
+(seeded), larger than L2 (the state alone is ~10 GB), so no L2 flush is needed.
+
+Metric: grid-cell updates per second (cells x steps / device time), whole job.
+Also reported: the FP64 unfused GPU step on the same grid and the FP32 variants,
+the roofline of the dominant kernel (HBM bytes of the algorithm per launch over
+the launch's CUDA-event time, against the measured HBM copy bandwidth), the FP64
+oracle timed on this host's cores (a baseline, not the target), and the same
+metric end to end through the C ABI from pinned host buffers.
+
+Multi-GPU (torchrun): each rank advances its own replica (weak scaling, no data
+exchange), the time is the max over ranks.  `--impl reference` times the FP64
+CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+from paper_2401_07416_gb300 import workloads as W
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+FALLBACK_HBM = 6800.0
+METRIC = "3D FDTD cell-updates/s & %HBM roofline; FP32/batched/adjoint vs FP64 plain"
+
+# algorithmic HBM bytes per grid node and fused launch: fields read + written once
+BYTES_PER_NODE = {W.FP64: 40, W.FP32: 20, W.FP32_KAHAN: 36}
+PREC_NAME = {W.FP64: "f64", W.FP32: "f32", W.FP32_KAHAN: "f32+kahan"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="kahan", choices=["kahan", "fp32", "fp64"])
+    ap.add_argument("--tblock", type=int, default=2)
+    ap.add_argument("--no-extras", action="store_true", help="skip variants, e2e and CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.count(",") >= 8]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(os.path.join(ROOT, "paper_2401_07416_gb300", "csrc"))):
+        if name.startswith("step_kernels") or name.endswith(".cuh"):
+            with open(os.path.join(ROOT, "paper_2401_07416_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str, cells: int):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    scaled to `cells` grid nodes; None if absent or taken on another kernel build."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+        e = d[kernel_key]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return e["dram_bytes_per_launch"] * cells / e["cells"]
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def cpu_sample_workload():
+    """A bounded slab of the 512x512x1024 workload: 512 x 512 x 16 planes around the
+    packet start, the workload's atoms, walls at the slab faces."""
+    wl = W.config5()
+    g = wl.grid
+    z0 = int(round(wl.packet.r0[2] / g.hz)) - 8
+    sub = W.Grid(nx=g.nx, ny=g.ny, nz=16, hx=g.hx, hy=g.hy, hz=g.hz, dt=g.dt,
+                 bc=(W.PERIODIC, W.PERIODIC, W.DIRICHLET), obs_every=20)
+    return wl, sub, z0
+
+
+def oracle_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_state():
+    import oracle
+    wl, sub, z0 = cpu_sample_workload()
+    g = wl.grid
+    origin = (0.0, 0.0, z0 * g.hz)
+    period = g.lengths
+    V = oracle.potential_atoms_window(sub, origin, period, wl.atoms, rc=0.5 * min(period[:2]))
+    R0, I0 = oracle.wavepacket_window(sub, origin, wl.packet.r0, wl.packet.sigma, wl.packet.k0)
+    return sub, V, R0, oracle.init_half(sub, V, R0, I0)
+
+
+def time_oracle(seconds: float):
+    """FP64 oracle steps on the bounded sample until `seconds` of wall time."""
+    import oracle
+    sub, V, R, I = oracle_sample_state()
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        R, I, _, _ = oracle.run(sub, V, R, I, 2, use_mask=False, flux=False)
+        steps += 2
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    cores = oracle_cores()
+    return {"value": sub.cells * steps / el, "unit": "cell-updates/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps on a 512x512x16 z-slab of the 512x512x1024 "
+                      f"workload ({sub.cells} nodes), {el:.1f} s wall, OpenMP {cores} threads"}
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle as the reference implementation: W untimed and K timed
+    steps on the bounded sample of the workload (rank 0 only)."""
+    import oracle
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    sub, V, R, I = oracle_sample_state()
+    if args.warmup > 0:
+        R, I, _, _ = oracle.run(sub, V, R, I, args.warmup, use_mask=False, flux=False)
+    t0 = time.perf_counter()
+    R, I, _, _ = oracle.run(sub, V, R, I, args.steps, use_mask=False, flux=False)
+    el = time.perf_counter() - t0
+    value = sub.cells * args.steps / el
+    cores = oracle_cores()
+    sample = (f"{args.steps} timed FP64 oracle steps (after {args.warmup} untimed) on a "
+              f"512x512x16 z-slab of the 512x512x1024 workload ({sub.cells} nodes), "
+              f"OpenMP {cores} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "512x512x1024 grid, h=0.05, 4x16x16 softened-Coulomb slab "
+                               "(FP64 CPU oracle on a 16-plane sample)",
+                   "nx": 512, "ny": 512, "nz": 1024, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def make_ctx(T, wl, precision, tblock, V_dev=None):
+    from paper_2401_07416_gb300.sim import Sim
+    s = Sim(wl.grid, precision=precision, tblock=tblock)
+    if V_dev is None:
+        s.set_atoms(0, wl.atoms)
+    else:
+        s.set_potential(0, V_dev)
+    s.set_packet(0, wl.packet)
+    return s
+
+
+def timed_steps(torch, T, s, steps, warmup, barrier):
+    s.step(warmup)
+    torch.cuda.synchronize()
+    barrier()
+    T.tdse_set_profiling(s.ctx, True)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = T.tdse_get_profile(s.ctx)
+    T.tdse_set_profiling(s.ctx, False)
+    return ms, prof
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        barrier = dist.barrier
+    else:
+        torch.cuda.set_device(0)
+        barrier = lambda: None
+
+    from paper_2401_07416_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        barrier()
+    from paper_2401_07416_gb300 import tdse as T
+
+    prec = {"kahan": W.FP32_KAHAN, "fp32": W.FP32, "fp64": W.FP64}[args.precision]
+    tblock = 1 if prec == W.FP64 else args.tblock
+    wl = W.config5(prec)
+    g = wl.grid
+    cells = g.cells
+    hbm_peak, peak_kind = measured_peaks()
+
+    # headline: the fused step on the full grid
+    s = make_ctx(T, wl, prec, tblock)
+    V_dev = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
+    T.tdse_get_potential(s.ctx, 0, V_dev)
+    with ClockSampler(local) as clk:
+        ms, prof = timed_steps(torch, T, s, args.steps, args.warmup, barrier)
+    clocks = clk.summary()
+    obs = s.observables(0)
+    s.close()
+
+    t_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * cells * args.steps / (t_max * 1e-3)
+
+    launch_ms = prof["step_ms"] / max(1, prof["step_launches"])
+    bytes_launch = BYTES_PER_NODE[prec] * cells
+    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+    key = f"{PREC_NAME[prec]}_t{tblock}"
+    traffic = ncu_traffic(key, cells)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "kernel": f"fused_step_kernel ({key})",
+                "algorithmic_bytes_per_launch": bytes_launch,
+                "avg_launch_ms": launch_ms, "launches": prof["step_launches"],
+                "effective_frac_vs_unfused_fp32": value / world * 20 / 1e9 / hbm_peak}
+
+    extras = {}
+    e2e = None
+    cpu = None
+    if not args.no_extras:
+        # FP64 unfused step and the FP32 variants on the same grid (same potential)
+        variants = [(W.FP64, 1)] + [(p, t) for p in (W.FP32, W.FP32_KAHAN) for t in (1, 2)
+                                    if (p, t) != (prec, tblock)]
+        for vp, vt in variants:
+            steps_v = max(10, args.steps // (8 if vp == W.FP64 else 2))
+            sv = make_ctx(T, W.config5(vp), vp, vt, V_dev)
+            vms, vprof = timed_steps(torch, T, sv, steps_v, min(args.warmup, 6), barrier)
+            sv.close()
+            vlaunch = vprof["step_ms"] / max(1, vprof["step_launches"])
+            extras[f"{PREC_NAME[vp]}_t{vt}"] = {
+                "value": cells * steps_v / (vms * 1e-3), "unit": "cell-updates/s",
+                "steps": steps_v, "avg_launch_ms": vlaunch,
+                "hbm_frac": BYTES_PER_NODE[vp] * cells / (vlaunch * 1e-3) / 1e9 / hbm_peak}
+        if "f64_t1" in extras:
+            extras["speedup_vs_fp64_plain"] = value / world / extras["f64_t1"]["value"]
+
+        # end to end through the C ABI from pinned host buffers: potential in,
+        # packet set-up, the steps, flux map and observables out
+        V_host = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, pin_memory=True)
+        V_host.copy_(V_dev.cpu())
+        F_host = torch.empty((g.ny, g.nx), dtype=torch.float64, pin_memory=True)
+        from paper_2401_07416_gb300.sim import Sim
+        se = Sim(g, precision=prec, tblock=tblock)
+        se.set_potential(0, V_host)       # first call allocates; not timed
+        se.set_packet(0, wl.packet)
+        se.step(4)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        T.tdse_set_potential(se.ctx, 0, V_host)
+        se.set_packet(0, wl.packet)
+        se.step(args.steps)
+        T.tdse_get_flux_map(se.ctx, 0, F_host)
+        se.observables(0)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        barrier()
+        se.close()
+        e2e = {"value": world * cells * args.steps / el, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": V_host.numel() * 8 / args.steps,
+               "d2h_bytes_per_step": (F_host.numel() * 8 + 64) / args.steps,
+               "includes": "tdse_set_potential (pinned host V, FP64), tdse_set_wavepacket, "
+                           "tdse_step, tdse_get_flux_map, tdse_observables"}
+        del V_host
+        if rank == 0 and world == 1:
+            cpu = time_oracle(args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32+kahan": "f32", "f32": "f32", "f64": "f64"}[PREC_NAME[prec]],
+        "data": "synthetic",
+        "config": {"workload": "512x512x1024 grid, h=0.05, 4x16x16 softened-Coulomb slab, "
+                               "cos^2 absorbing layers, detector flux every step, "
+                               "Q/E every 20 steps",
+                   "precision": PREC_NAME[prec], "steps_per_launch": tblock,
+                   "nx": g.nx, "ny": g.ny, "nz": g.nz, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (state ~10 GB), no flush"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(prof["step_launches"] + prof["reduce_launches"]),
+        "clocks": clocks,
+        "variants": extras,
+        "final_obs": {"Q": obs["Q"], "energy": obs["energy"],
+                      "flux_integrated": obs["flux_integrated"]},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

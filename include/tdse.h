@@ -1,0 +1,219 @@
+/*
+ * tdse.h -- C ABI of libtdse: the FDTD leapfrog for the 3-D time-dependent
+ * Schrodinger equation on one GB300 (sm_103a).
+ *
+ * Method: Nagaya, Omatsu, Packwood, "Fast generation of quantum dynamics data
+ * using a GPU implementation of the time-dependent Schrodinger equation",
+ * arXiv 2401.07416.  psi = psi_R + i psi_I on a uniform grid (Sec. 2.1, Eqs. 5-7);
+ * psi_R lives at integer and psi_I at half-integer time levels and they are
+ * advanced in turn by Eq. 9 (psi_I += A psi_R) and Eq. 8 (psi_R -= A psi_I), where
+ *   A f = c_x (f[i+1] - 2 f + f[i-1]) + c_y (...) + c_z (...) - c_v V f,
+ *   c_a = hbar dt / (2 m h_a^2),  c_v = dt / hbar          (Sec. 2.1 after Eq. 9).
+ * Periodic axes wrap neighbours as in Eqs. 13-14; a walled axis reads zero
+ * outside [0, n).  Eq. 10's absorbing potential is replaced by a per-plane
+ * factor M_k = cos^2(eta (pi/2) d / W) on W-cell layers at the z ends (d = 1..W,
+ * the depth into the layer), applied to both parts after every step.  The
+ * detector (Eq. 15 stores the density on a plane) records here the probability
+ * flux through the face between planes det_k and det_k+1,
+ *   j = hbar / (m h_z) * (R[det_k] I[det_k+1] - R[det_k+1] I[det_k]),
+ * with R at step n and I at step n+1/2, and its time integral F = sum_n j dt.
+ *
+ * Conventions for every function:
+ *   - Arrays are [nz][ny][nx] with x fastest, unpadded, FP64, unless stated.
+ *   - Every call returns a tdse_status; nothing throws across the ABI.  On an
+ *     error, tdse_last_error() describes it; the context stays usable unless
+ *     the status is TDSE_ECUDA or TDSE_EUNSTABLE.
+ *   - The context owns all device memory it allocates (through the allocator
+ *     callbacks, cudaMalloc/cudaFree by default) and frees it in tdse_destroy.
+ *     Caller pointers are borrowed for the duration of the call only.
+ *   - `on_device` != 0 means a pointer is CUDA device memory on the current
+ *     device; otherwise it is host memory.
+ *   - All GPU work is issued on the stream given to tdse_set_stream (default:
+ *     the legacy default stream).  Functions that return host data synchronise
+ *     that stream.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - There is no CPU fallback: every computation runs in this library's CUDA
+ *     kernels, and a missing GPU is reported as TDSE_ECUDA.
+ */
+#ifndef TDSE_H
+#define TDSE_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define TDSE_API __attribute__((visibility("default")))
+#else
+#define TDSE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TDSE_OK = 0,
+    TDSE_EINVAL = -1,    /* bad argument: shape, NULL pointer, dt above the stability bound ... */
+    TDSE_ENOMEM = -2,    /* the allocator returned NULL */
+    TDSE_ECUDA = -3,     /* a CUDA runtime/driver call failed */
+    TDSE_EUNSTABLE = -4, /* non-finite values or growth of the invariant Q by > 1e-3 */
+    TDSE_ETIMEOUT = -5,  /* a bounded wait inside a kernel expired */
+    TDSE_ESTATE = -6     /* call out of order (e.g. step before set_wavepacket) */
+} tdse_status;
+
+enum { TDSE_BC_PERIODIC = 0, TDSE_BC_DIRICHLET = 1 };
+
+/* Storage and arithmetic of psi and of the potential term:
+ *   TDSE_FP64        FP64 fields and FP64 arithmetic;
+ *   TDSE_FP32        FP32 fields, FP32 stencil arithmetic;
+ *   TDSE_FP32_KAHAN  FP32 fields plus FP32 compensation terms of the Kahan
+ *                    (compensated) sum f += increment, persisted between calls.
+ * Reductions (norm, energy, flux) are FP64 in every mode. */
+enum { TDSE_FP64 = 0, TDSE_FP32 = 1, TDSE_FP32_KAHAN = 2 };
+
+typedef struct tdse_params {
+    int nx, ny, nz;          /* nodes per axis; nx must be a multiple of 4, ny, nz >= 1 */
+    double hx, hy, hz;       /* spacings (Sec. 2.1: r = (i hx, j hy, k hz), i, j, k >= 0) */
+    double dt;               /* time step; <= 0 selects Eq. 11, dt = m min(h)^2 / (5 hbar) */
+    double hbar, mass;       /* <= 0 selects 1 (atomic units) */
+    int bc[3];               /* TDSE_BC_* per axis x, y, z */
+    int mask_lo, mask_hi;    /* absorbing cells at the z = 0 and z = nz-1 ends (0: none) */
+    double mask_eta;         /* absorbing strength eta (M at the outermost cell = cos^2(eta pi/2)) */
+    int det_k;               /* detector face between planes det_k, det_k+1; -1: no detector */
+    int obs_every;           /* norm/energy reduction every obs_every steps (<= 0: 20, Sec. 2.3) */
+    int ckpt_every;          /* > 0: keep FP64 checkpoints every ckpt_every steps for tdse_adjoint */
+    int precision;           /* TDSE_FP64 / TDSE_FP32 / TDSE_FP32_KAHAN (same for all members) */
+    int tblock;              /* steps fused per kernel launch (temporal blocking); 0: automatic */
+    int reserved[6];         /* must be zero */
+} tdse_params;
+
+typedef struct tdse_obs {
+    double Q;                /* h^3 sum (R^n R^n + I^{n+1/2} I^{n-1/2}), exactly conserved by the
+                                scheme for real V without absorbing layer */
+    double norm_paper;       /* h^3 sum (R^n^2 + I^{n-1/2}^2), the density of Sec. 2.1 */
+    double energy;           /* (R.H R + I^{n+1/2}.H I^{n-1/2}) / (R.R + I^{n+1/2}.I^{n-1/2}) */
+    double flux;             /* hx hy sum_yx j^{n-1}: detector flux of the last step */
+    double flux_integrated;  /* hx hy sum_yx F: probability that crossed the face so far */
+    double t;                /* time n dt */
+    long long step;          /* n */
+} tdse_obs;
+
+typedef struct tdse_ctx tdse_ctx;
+
+typedef void *(*tdse_alloc_fn)(size_t bytes, void *user);
+typedef void (*tdse_free_fn)(void *ptr, void *user);
+
+/* Create a context for `batch` simulations; p[m] describes member m (Sec. 2.1,
+ * Eqs. 6-11).  Members may differ in shape, spacing, dt and boundaries, but
+ * share precision, tblock, obs_every and ckpt_every.  Validates everything
+ * (EINVAL: shape, spacing, dt above the leapfrog stability bound of the free
+ * part, nx not a multiple of 4, periodic axis shorter than 8, det_k outside
+ * [0, nz-2]); allocates no device memory.  *out receives the context. */
+TDSE_API tdse_status tdse_create(const tdse_params *p, int batch, tdse_ctx **out);
+
+/* Route device allocations through (alloc, free, user), e.g. a framework's
+ * caching allocator.  Allowed only before the first allocation (ESTATE). */
+TDSE_API tdse_status tdse_set_allocator(tdse_ctx *ctx, tdse_alloc_fn alloc, tdse_free_fn free_fn,
+                               void *user);
+
+/* Issue all work on `cuda_stream` (a cudaStream_t; NULL: legacy default stream). */
+TDSE_API tdse_status tdse_set_stream(tdse_ctx *ctx, void *cuda_stream);
+
+/* Potential V[nz][ny][nx] (FP64) of member m, Eq. 2's V(r) on the grid
+ * (Sec. 2.3 interpolates a DFT potential; any gridded V is accepted). */
+TDSE_API tdse_status tdse_set_potential(tdse_ctx *ctx, int member, const double *V, int on_device);
+
+/* Build V on the GPU from n atoms, xyzZ[n][4] = (x, y, z, Z):
+ * V(r) = -sum_a Z_a phi(|r - r_a|), phi = 1/sqrt(r^2 + a^2) minus its second-order
+ * Taylor polynomial in r^2 about r_cut for r < r_cut, 0 beyond; minimum-image
+ * distances along periodic axes.  soft_a2 = a^2; r_cut <= 0 selects half the
+ * shortest periodic length (no cut-off if no axis is periodic).  The atoms are
+ * kept for the chain rule of tdse_adjoint. */
+TDSE_API tdse_status tdse_set_atoms(tdse_ctx *ctx, int member, int n, const double *xyzZ,
+                           double soft_a2, double r_cut);
+
+/* Copy the potential V[nz][ny][nx] (FP64) of member m out (ESTATE if none was set). */
+TDSE_API tdse_status tdse_get_potential(tdse_ctx *ctx, int member, double *V, int on_device);
+
+/* Initial packet (Eq. 3 with a vector wave number): psi0 = prod_a g_a exp(i k0.(r - r0)),
+ * g_a = exp(-(r_a - r0_a)^2 / (2 sigma_a^2)), sigma_a <= 0 meaning no Gaussian factor
+ * along a; normalised so that h^3 sum |psi0|^2 = 1.  Sets R^0 = Re psi0 and
+ * I^{-1/2} = Im psi0 - A[Re psi0] / 2 (second-order start of the staggered scheme),
+ * resets the flux integral, observation history and checkpoints.  Without a
+ * potential, V = 0 is used. */
+TDSE_API tdse_status tdse_set_wavepacket(tdse_ctx *ctx, int member, const double r0[3],
+                                const double sigma[3], const double k0[3]);
+
+/* Set the state directly: R = psi_R^n, I = psi_I^{n-1/2} (FP64 [nz][ny][nx]). */
+TDSE_API tdse_status tdse_set_state(tdse_ctx *ctx, int member, const double *R, const double *I,
+                           int on_device);
+
+/* Advance every member by nsteps leapfrog steps (Eqs. 8-9 + absorbing layer),
+ * accumulating the detector flux, reducing Q and E every obs_every steps and
+ * recording checkpoints every ckpt_every steps.  Returns EUNSTABLE if a
+ * reduction saw non-finite values or Q above (1 + 1e-3) times its first value. */
+TDSE_API tdse_status tdse_step(tdse_ctx *ctx, long long nsteps);
+
+/* Observables of member m at the current step (computed now, FP64). */
+TDSE_API tdse_status tdse_observables(tdse_ctx *ctx, int member, tdse_obs *out);
+
+/* History of the periodic reductions of member m: up to `cap` records of
+ * (step, Q, norm_paper, energy) into out[4*i..4*i+3]; *count receives the
+ * number available. */
+TDSE_API tdse_status tdse_get_obs_history(tdse_ctx *ctx, int member, double *out, int cap, int *count);
+
+/* Copy the state out as FP64: R = psi_R^n, I = psi_I^{n-1/2} (Kahan mode: value
+ * plus compensation).  Either pointer may be NULL. */
+TDSE_API tdse_status tdse_get_state(tdse_ctx *ctx, int member, double *R, double *I, int on_device);
+
+/* Time-integrated detector flux F[ny][nx] = sum_n j^n dt (FP64). */
+TDSE_API tdse_status tdse_get_flux_map(tdse_ctx *ctx, int member, double *F, int on_device);
+
+/* Reverse-mode gradient of a loss L(F) of the time-integrated flux of member m,
+ * over all steps since tdse_set_wavepacket (requires ckpt_every > 0).
+ * dL_dF[ny][nx] is dL/dF; outputs (each may be NULL): dL_dV[nz][ny][nx] and,
+ * if the potential came from tdse_set_atoms, dL_datoms[n][4] = dL/d(x, y, z, Z).
+ * The leapfrog is run backward in time from the latest state (the map is
+ * invertible: R^n = R~ + A I~, I^{n-1/2} = I~ - A R^n with R~ = R^{n+1}/M,
+ * I~ = I^{n+1/2}/M), re-anchored at every FP64 checkpoint; the adjoint
+ * recursion is the transpose of the forward step.  The forward state is left
+ * unchanged. */
+TDSE_API tdse_status tdse_adjoint(tdse_ctx *ctx, int member, const double *dL_dF, double *dL_dV,
+                         double *dL_datoms, int on_device);
+
+/* Save / restore the whole context state (fields, compensation, flux integral,
+ * step counters, observation history) to / from a file; the file records the
+ * parameters and load_state rejects a mismatch (EINVAL). */
+TDSE_API tdse_status tdse_save_state(tdse_ctx *ctx, const char *path);
+TDSE_API tdse_status tdse_load_state(tdse_ctx *ctx, const char *path);
+
+/* Kernel timing, for benchmarks.  While enabled, every fused-step launch is
+ * bracketed by CUDA events (no CUDA graphs); tdse_get_profile returns the
+ * launches and total device milliseconds of the step kernels and of the
+ * reduction kernels since the last reset, and the cells and time steps per
+ * step launch (all members). */
+typedef struct tdse_profile {
+    long long step_launches;
+    double step_ms;
+    long long reduce_launches;
+    double reduce_ms;
+    long long cells_per_launch;     /* grid nodes updated by one step launch */
+    int steps_per_launch;           /* temporal depth of the last step launch */
+    int reserved;
+} tdse_profile;
+TDSE_API tdse_status tdse_set_profiling(tdse_ctx *ctx, int enable);
+TDSE_API tdse_status tdse_get_profile(tdse_ctx *ctx, tdse_profile *out);
+
+/* Description of the last error on this context (static storage, never NULL). */
+TDSE_API const char *tdse_last_error(const tdse_ctx *ctx);
+
+/* Library version string. */
+TDSE_API const char *tdse_version(void);
+
+/* Free every device allocation and the context (NULL is accepted). */
+TDSE_API tdse_status tdse_destroy(tdse_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDSE_H */

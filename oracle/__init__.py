@@ -62,6 +62,8 @@ def lib():
             "orc_apply_A": (None, [g, p, p, p]),
             "orc_mask": (None, [g, p]),
             "orc_potential_atoms": (None, [g, i, p, d, d, p]),
+            "orc_potential_atoms_at": (None, [g, p, p, i, p, d, d, p]),
+            "orc_wavepacket_at": (None, [g, p, p, p, p, p, p]),
             "orc_atom_gradient": (None, [g, i, p, d, d, p, p]),
             "orc_wavepacket": (None, [g, p, p, p, p, p]),
             "orc_init_half": (None, [g, p, p, p, i]),
@@ -135,6 +137,25 @@ def potential_atoms(g, atoms, a2=0.25, rc=None) -> np.ndarray:
     lib().orc_potential_atoms(ctypes.byref(_grid(g)), atoms.shape[0], _ptr(atoms), a2, rc,
                               _ptr(V))
     return V
+
+
+def potential_atoms_window(g, origin, period, atoms, a2=0.25, rc=0.0) -> np.ndarray:
+    """Potential on the window grid g whose node (0,0,0) sits at `origin` of a larger
+    grid with periods `period` (rc must be given: the larger grid's cut-off)."""
+    atoms = _f64(atoms)
+    V = np.empty(shape(g))
+    lib().orc_potential_atoms_at(ctypes.byref(_grid(g)), _ptr(_f64(origin)), _ptr(_f64(period)),
+                                 atoms.shape[0], _ptr(atoms), a2, rc, _ptr(V))
+    return V
+
+
+def wavepacket_window(g, origin, r0, sigma, k0):
+    """Eq. 3 packet on the window grid g at `origin`, normalised on the window."""
+    R = np.empty(shape(g))
+    I = np.empty(shape(g))
+    lib().orc_wavepacket_at(ctypes.byref(_grid(g)), _ptr(_f64(origin)), _ptr(_f64(r0)),
+                            _ptr(_f64(sigma)), _ptr(_f64(k0)), _ptr(R), _ptr(I))
+    return R, I
 
 
 def default_cutoff(g) -> float:

@@ -170,22 +170,23 @@ static void profile(double r2, double a2, double rc, double *phi, double *dphi_d
     *dphi_dr2 = -0.5 / (rho * rho * rho) - (-0.5 / rhoc3 + 0.75 * du / rhoc5);
 }
 
-/* V(r) = sum over atoms of -Z phi(|r - r_a|), r = (i hx, j hy, k hz).
- * atoms: [n][4] rows (x, y, z, Z). */
-void orc_potential_atoms(const orc_grid *g, int n, const double *atoms, double a2,
-                         double rc, double *V)
+/* V(r) = sum over atoms of -Z phi(|r - r_a|) at the nodes r = origin + (i hx, j hy, k hz)
+ * of grid g, with minimum-image distances of period `period[a]` along periodic
+ * axes.  atoms: [n][4] rows (x, y, z, Z).  With origin 0 and period n h this is
+ * the potential of the whole grid; other values evaluate a window of a larger grid. */
+void orc_potential_atoms_at(const orc_grid *g, const double origin[3], const double period[3],
+                            int n, const double *atoms, double a2, double rc, double *V)
 {
-    double L[3] = {g->nx * g->hx, g->ny * g->hy, g->nz * g->hz};
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < g->nz; ++k)
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i < g->nx; ++i) {
-                double r[3] = {i * g->hx, j * g->hy, k * g->hz};
+                double r[3] = {origin[0] + i * g->hx, origin[1] + j * g->hy, origin[2] + k * g->hz};
                 double v = 0.0;
                 for (int a = 0; a < n; ++a) {
                     double r2 = 0.0;
                     for (int ax = 0; ax < 3; ++ax) {
-                        double d = min_image(r[ax] - atoms[4 * a + ax], L[ax], g->bc[ax] == 0);
+                        double d = min_image(r[ax] - atoms[4 * a + ax], period[ax], g->bc[ax] == 0);
                         r2 += d * d;
                     }
                     double phi, dphi;
@@ -194,6 +195,14 @@ void orc_potential_atoms(const orc_grid *g, int n, const double *atoms, double a
                 }
                 V[at3(g, i, j, k)] = v;
             }
+}
+
+void orc_potential_atoms(const orc_grid *g, int n, const double *atoms, double a2, double rc,
+                         double *V)
+{
+    const double origin[3] = {0.0, 0.0, 0.0};
+    const double period[3] = {g->nx * g->hx, g->ny * g->hy, g->nz * g->hz};
+    orc_potential_atoms_at(g, origin, period, n, atoms, a2, rc, V);
 }
 
 /* Chain rule from dL/dV to the atom parameters: out[4a + (0,1,2,3)] =
@@ -233,16 +242,16 @@ void orc_atom_gradient(const orc_grid *g, int n, const double *atoms, double a2,
 
 /* Eq. 3 with a vector wave number: psi0 = prod_a g_a * exp(i k0 . (r - r0)),
  * g_a = exp(-(r_a - r0_a)^2 / (2 sigma_a^2)) (sigma_a <= 0: plane-wave axis,
- * g_a = 1), normalised on the grid so that sum |psi0|^2 hx hy hz = 1.
- * Writes Re psi0 to R and Im psi0 to I. */
-void orc_wavepacket(const orc_grid *g, const double r0[3], const double sigma[3],
-                    const double k0[3], double *R, double *I)
+ * g_a = 1), at the nodes r = origin + (i hx, j hy, k hz), normalised on this grid
+ * so that sum |psi0|^2 hx hy hz = 1.  Writes Re psi0 to R and Im psi0 to I. */
+void orc_wavepacket_at(const orc_grid *g, const double origin[3], const double r0[3],
+                       const double sigma[3], const double k0[3], double *R, double *I)
 {
     double sum = 0.0;
     for (int k = 0; k < g->nz; ++k)
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i < g->nx; ++i) {
-                double r[3] = {i * g->hx, j * g->hy, k * g->hz};
+                double r[3] = {origin[0] + i * g->hx, origin[1] + j * g->hy, origin[2] + k * g->hz};
                 double amp = 1.0, phase = 0.0;
                 for (int ax = 0; ax < 3; ++ax) {
                     double d = r[ax] - r0[ax];
@@ -259,6 +268,13 @@ void orc_wavepacket(const orc_grid *g, const double r0[3], const double sigma[3]
         R[c] *= s;
         I[c] *= s;
     }
+}
+
+void orc_wavepacket(const orc_grid *g, const double r0[3], const double sigma[3],
+                    const double k0[3], double *R, double *I)
+{
+    const double origin[3] = {0.0, 0.0, 0.0};
+    orc_wavepacket_at(g, origin, r0, sigma, k0, R, I);
 }
 
 /* Staggered start: psi_I lives at half-integer times (Sec. 2.1), so the state

@@ -1,0 +1,479 @@
+// Set-up, conversion and reduction kernels of libtdse (everything except the
+// fused step).  All arithmetic that feeds a reduction is FP64.
+#include <cmath>
+
+#include "tdse_internal.cuh"
+
+namespace tdse {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ long long pidx(const MemberDev &m, int x, int y, int z)
+{
+    return static_cast<long long>(z) * m.plane + static_cast<long long>(y + m.G) * m.pitch +
+           (x + m.G);
+}
+
+__device__ __forceinline__ long long uidx(const MemberDev &m, int x, int y, int z)
+{
+    return (static_cast<long long>(z) * m.ny + y) * m.nx + x;
+}
+
+template <typename Real>
+__device__ __forceinline__ double value(const MemberDev &m, const Real *f, const Real *c,
+                                        long long o)
+{
+    double v = static_cast<double>(f[o]);
+    if (c) v -= static_cast<double>(c[o]);
+    return v;
+}
+
+// Field value at unpadded (x, y, z) with |x - x0|, |y - y0| <= 1 of an interior
+// node: x/y come from the ghost zones, z wraps (periodic) or reads zero (wall).
+template <typename Real>
+__device__ __forceinline__ double nbr(const MemberDev &m, const Real *f, const Real *c, int x,
+                                      int y, int z)
+{
+    if (z < 0 || z >= m.nz) {
+        if (!m.per_z) return 0.0;
+        z = (z % m.nz + m.nz) % m.nz;
+    }
+    return value<Real>(m, f, c, pidx(m, x, y, z));
+}
+
+// ---------------------------------------------------------------- ghost zones
+
+template <typename Real>
+__global__ void fill_ghosts_kernel(MemberDev m, Real *f)
+{
+    const int wx = m.nx + 2 * m.G, wy = m.ny + 2 * m.G;
+    const long long n = static_cast<long long>(wx) * wy * m.nz;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int px = static_cast<int>(t % wx);
+        const int py = static_cast<int>((t / wx) % wy);
+        const int z = static_cast<int>(t / (static_cast<long long>(wx) * wy));
+        int x = px - m.G, y = py - m.G;
+        const bool gx = x < 0 || x >= m.nx, gy = y < 0 || y >= m.ny;
+        if (!gx && !gy) continue;
+        Real v = Real(0);
+        if ((!gx || m.per_x) && (!gy || m.per_y)) {
+            x = (x % m.nx + m.nx) % m.nx;
+            y = (y % m.ny + m.ny) % m.ny;
+            v = f[pidx(m, x, y, z)];
+        }
+        f[pidx(m, px - m.G, py - m.G, z)] = v;
+    }
+}
+
+// ---------------------------------------------------------------- potential
+
+// One softened-Coulomb atom: phi(u = r^2) = f(u) - [f(uc) + f'(uc)(u - uc) +
+// f''(uc)(u - uc)^2 / 2] for u < uc, f = (u + a^2)^-1/2, and 0 beyond.
+__device__ __forceinline__ double atom_phi(double r2, double a2, double rc)
+{
+    const double rho = sqrt(r2 + a2);
+    if (rc <= 0.0) return 1.0 / rho;
+    const double uc = rc * rc;
+    if (r2 >= uc) return 0.0;
+    const double rhoc = sqrt(uc + a2);
+    const double ic = 1.0 / rhoc, ic3 = ic * ic * ic, ic5 = ic3 * ic * ic;
+    const double du = r2 - uc;
+    return 1.0 / rho - (ic - 0.5 * du * ic3 + 0.375 * du * du * ic5);
+}
+
+__device__ __forceinline__ double min_image(double d, double L, int periodic)
+{
+    return periodic ? d - L * floor(d / L + 0.5) : d;
+}
+
+__global__ void potential_kernel(MemberDev m, const double *__restrict__ atoms, int n,
+                                 double a2, double rc, double *__restrict__ V)
+{
+    __shared__ double sa[4 * 256];
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    const int x = static_cast<int>(t % m.nx);
+    const int y = static_cast<int>((t / m.nx) % m.ny);
+    const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+    const double L[3] = {m.nx * m.hx, m.ny * m.hy, m.nz * m.hz};
+    const double r[3] = {x * m.hx, y * m.hy, z * m.hz};
+    double v = 0.0;
+    for (int a0 = 0; a0 < n; a0 += 256) {
+        const int na = min(256, n - a0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * na; i += blockDim.x) sa[i] = atoms[4 * a0 + i];
+        __syncthreads();
+        if (t < cells) {
+            for (int a = 0; a < na; ++a) {
+                const double dx = min_image(r[0] - sa[4 * a + 0], L[0], m.per_x);
+                const double dy = min_image(r[1] - sa[4 * a + 1], L[1], m.per_y);
+                const double dz = min_image(r[2] - sa[4 * a + 2], L[2], m.per_z);
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                v -= sa[4 * a + 3] * atom_phi(r2, a2, rc);
+            }
+        }
+    }
+    if (t < cells) V[t] = v;
+}
+
+// d = -2 (cx + cy + cz) - cv V into the padded Real array; V kept in FP64.
+template <typename Real>
+__global__ void build_d_kernel(MemberDev m, const double *__restrict__ V, Real *d,
+                               double *__restrict__ V64)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const double c0 = -2.0 * (m.cx + m.cy + m.cz);
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % m.nx);
+        const int y = static_cast<int>((t / m.nx) % m.ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+        const double v = V ? V[t] : 0.0;
+        V64[t] = v;
+        d[pidx(m, x, y, z)] = static_cast<Real>(c0 - m.cv * v);
+    }
+}
+
+// ---------------------------------------------------------------- wave packet
+
+struct PacketArgs {
+    double r0[3], sigma[3], k0[3];
+};
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (blockDim.x + 31) / 32; ++w) s += sh[w];
+    return s;   // valid in thread 0
+}
+
+__global__ void packet_kernel(MemberDev m, PacketArgs P, double *__restrict__ R,
+                              double *__restrict__ I, double *__restrict__ partials)
+{
+    __shared__ double sh[32];
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    double acc = 0.0;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % m.nx);
+        const int y = static_cast<int>((t / m.nx) % m.ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+        const double r[3] = {x * m.hx, y * m.hy, z * m.hz};
+        double amp = 1.0, phase = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double d = r[a] - P.r0[a];
+            if (P.sigma[a] > 0.0) amp *= exp(-d * d / (2.0 * P.sigma[a] * P.sigma[a]));
+            phase += P.k0[a] * d;
+        }
+        double sn, cs;
+        sincos(phase, &sn, &cs);
+        R[t] = amp * cs;
+        I[t] = amp * sn;
+        acc += amp * amp;
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void sum_partials_kernel(const double *__restrict__ partials, int n, double scale,
+                                    double *__restrict__ out)
+{
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[0] = 1.0 / sqrt(s * scale);
+}
+
+// R^0 = s Re psi0, I^{-1/2} = s (Im psi0 - A[Re psi0] / 2), stored as Real (+ compensation).
+template <typename Real>
+__global__ void scale_half_kernel(MemberDev m, const double *__restrict__ V64,
+                                  const double *__restrict__ R, const double *__restrict__ I,
+                                  const double *__restrict__ scale, int kahan, int buf)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const double s = scale[0];
+    Real *oR = reinterpret_cast<Real *>(m.R[buf]);
+    Real *oI = reinterpret_cast<Real *>(m.I[buf]);
+    Real *oCR = reinterpret_cast<Real *>(m.cR[buf]);
+    Real *oCI = reinterpret_cast<Real *>(m.cI[buf]);
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % m.nx);
+        const int y = static_cast<int>((t / m.nx) % m.ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+        auto at = [&](int xx, int yy, int zz) -> double {
+            if (xx < 0 || xx >= m.nx) {
+                if (!m.per_x) return 0.0;
+                xx = (xx % m.nx + m.nx) % m.nx;
+            }
+            if (yy < 0 || yy >= m.ny) {
+                if (!m.per_y) return 0.0;
+                yy = (yy % m.ny + m.ny) % m.ny;
+            }
+            if (zz < 0 || zz >= m.nz) {
+                if (!m.per_z) return 0.0;
+                zz = (zz % m.nz + m.nz) % m.nz;
+            }
+            return R[uidx(m, xx, yy, zz)];
+        };
+        const double r0 = R[t];
+        const double ar = m.cx * (at(x + 1, y, z) + at(x - 1, y, z)) +
+                          m.cy * (at(x, y + 1, z) + at(x, y - 1, z)) +
+                          m.cz * (at(x, y, z + 1) + at(x, y, z - 1)) +
+                          (-2.0 * (m.cx + m.cy + m.cz) - m.cv * V64[t]) * r0;
+        const double rv = s * r0;
+        const double iv = s * (I[t] - 0.5 * ar);
+        const long long o = pidx(m, x, y, z);
+        const Real rs = static_cast<Real>(rv), is = static_cast<Real>(iv);
+        oR[o] = rs;
+        oI[o] = is;
+        if (kahan) {
+            oCR[o] = static_cast<Real>(static_cast<double>(rs) - rv);
+            oCI[o] = static_cast<Real>(static_cast<double>(is) - iv);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- state copies
+
+template <typename Real>
+__global__ void set_state_kernel(MemberDev m, const double *__restrict__ R,
+                                 const double *__restrict__ I, int kahan, int buf)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    Real *oR = reinterpret_cast<Real *>(m.R[buf]);
+    Real *oI = reinterpret_cast<Real *>(m.I[buf]);
+    Real *oCR = reinterpret_cast<Real *>(m.cR[buf]);
+    Real *oCI = reinterpret_cast<Real *>(m.cI[buf]);
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % m.nx);
+        const int y = static_cast<int>((t / m.nx) % m.ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+        const long long o = pidx(m, x, y, z);
+        const Real rs = static_cast<Real>(R[t]), is = static_cast<Real>(I[t]);
+        oR[o] = rs;
+        oI[o] = is;
+        if (kahan) {
+            oCR[o] = static_cast<Real>(static_cast<double>(rs) - R[t]);
+            oCI[o] = static_cast<Real>(static_cast<double>(is) - I[t]);
+        }
+    }
+}
+
+template <typename Real>
+__global__ void get_state_kernel(MemberDev m, double *__restrict__ R, double *__restrict__ I,
+                                 int kahan, int buf)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const Real *iR = reinterpret_cast<const Real *>(m.R[buf]);
+    const Real *iI = reinterpret_cast<const Real *>(m.I[buf]);
+    const Real *iCR = kahan ? reinterpret_cast<const Real *>(m.cR[buf]) : nullptr;
+    const Real *iCI = kahan ? reinterpret_cast<const Real *>(m.cI[buf]) : nullptr;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % m.nx);
+        const int y = static_cast<int>((t / m.nx) % m.ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+        const long long o = pidx(m, x, y, z);
+        if (R) R[t] = value<Real>(m, iR, iCR, o);
+        if (I) I[t] = value<Real>(m, iI, iCI, o);
+    }
+}
+
+// ---------------------------------------------------------------- observables
+
+// Per block: sums of (R.R + I+.I, R^2 + I^2, R.AR + I+.AI) with I+ = I + A R.
+template <typename Real>
+__global__ void observables_kernel(MemberDev m, int kahan, int buf, double *__restrict__ partials)
+{
+    __shared__ double sh[32];
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const Real *R = reinterpret_cast<const Real *>(m.R[buf]);
+    const Real *I = reinterpret_cast<const Real *>(m.I[buf]);
+    const Real *CR = kahan ? reinterpret_cast<const Real *>(m.cR[buf]) : nullptr;
+    const Real *CI = kahan ? reinterpret_cast<const Real *>(m.cI[buf]) : nullptr;
+    const Real *D = reinterpret_cast<const Real *>(m.d);
+    double q = 0.0, pn = 0.0, e = 0.0;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % m.nx);
+        const int y = static_cast<int>((t / m.nx) % m.ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+        const long long o = pidx(m, x, y, z);
+        const double d = static_cast<double>(D[o]);
+        const double r0 = value<Real>(m, R, CR, o), i0 = value<Real>(m, I, CI, o);
+        const double ar = m.cx * (nbr<Real>(m, R, CR, x + 1, y, z) + nbr<Real>(m, R, CR, x - 1, y, z)) +
+                          m.cy * (nbr<Real>(m, R, CR, x, y + 1, z) + nbr<Real>(m, R, CR, x, y - 1, z)) +
+                          m.cz * (nbr<Real>(m, R, CR, x, y, z + 1) + nbr<Real>(m, R, CR, x, y, z - 1)) +
+                          d * r0;
+        const double ai = m.cx * (nbr<Real>(m, I, CI, x + 1, y, z) + nbr<Real>(m, I, CI, x - 1, y, z)) +
+                          m.cy * (nbr<Real>(m, I, CI, x, y + 1, z) + nbr<Real>(m, I, CI, x, y - 1, z)) +
+                          m.cz * (nbr<Real>(m, I, CI, x, y, z + 1) + nbr<Real>(m, I, CI, x, y, z - 1)) +
+                          d * i0;
+        const double ip = i0 + ar;
+        q += r0 * r0 + ip * i0;
+        pn += r0 * r0 + i0 * i0;
+        e += r0 * ar + ip * ai;
+    }
+    const double sq = block_sum(q, sh);
+    const double sp = block_sum(pn, sh);
+    const double se = block_sum(e, sh);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x + 0] = sq;
+        partials[3 * blockIdx.x + 1] = sp;
+        partials[3 * blockIdx.x + 2] = se;
+    }
+}
+
+// record = {step, Q, norm_paper, energy, flux_last, flux_integrated}; sets
+// status bit 1 on non-finite Q or Q > (1 + 1e-3) q_ref (q_ref <= 0: no check).
+__global__ void observables_finalize_kernel(MemberDev m, const double *__restrict__ partials,
+                                            int nparts, double *__restrict__ record,
+                                            int *status, double q_ref, long long step)
+{
+    __shared__ double sh[32];
+    double q = 0.0, pn = 0.0, e = 0.0, fl = 0.0, fi = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        q += partials[3 * i + 0];
+        pn += partials[3 * i + 1];
+        e += partials[3 * i + 2];
+    }
+    const long long npix = static_cast<long long>(m.nx) * m.ny;
+    if (m.det_k >= 0)
+        for (long long i = threadIdx.x; i < npix; i += blockDim.x) {
+            fl += m.jlast[i];
+            fi += m.flux[i];
+        }
+    q = block_sum(q, sh);
+    pn = block_sum(pn, sh);
+    e = block_sum(e, sh);
+    fl = block_sum(fl, sh);
+    fi = block_sum(fi, sh);
+    if (threadIdx.x == 0) {
+        const double h3 = m.hx * m.hy * m.hz;
+        const double hxy = m.hx * m.hy;
+        record[0] = static_cast<double>(step);
+        record[1] = q * h3;
+        record[2] = pn * h3;
+        record[3] = -(m.hbar / m.dt) * e / q;
+        record[4] = fl * hxy;
+        record[5] = fi * hxy;
+        if (!isfinite(q * h3) || !isfinite(e) || (q_ref > 0.0 && q * h3 > q_ref * (1.0 + 1e-3)))
+            atomicOr(status, 2);
+    }
+}
+
+int grid_for(long long n)
+{
+    long long g = (n + kThreads - 1) / kThreads;
+    if (g > 65535LL * 32) g = 65535LL * 32;
+    if (g < 1) g = 1;
+    return static_cast<int>(g);
+}
+
+}  // namespace
+
+cudaError_t launch_fill_ghosts(const MemberDev &m, void *field, int elem, cudaStream_t s)
+{
+    const long long n = static_cast<long long>(m.nx + 2 * m.G) * (m.ny + 2 * m.G) * m.nz;
+    if (elem == 8)
+        fill_ghosts_kernel<double><<<grid_for(n), kThreads, 0, s>>>(m, static_cast<double *>(field));
+    else
+        fill_ghosts_kernel<float><<<grid_for(n), kThreads, 0, s>>>(m, static_cast<float *>(field));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_potential_atoms(const MemberDev &m, const double *atoms, int n, double a2,
+                                   double rc, double *V, cudaStream_t s)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    potential_kernel<<<static_cast<unsigned>((cells + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        m, atoms, n, a2, rc, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_d(const MemberDev &m, int elem, const double *V, double *V64,
+                           cudaStream_t s)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    if (elem == 8)
+        build_d_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, V, static_cast<double *>(m.d), V64);
+    else
+        build_d_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, V, static_cast<float *>(m.d), V64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_packet(const MemberDev &m, const double *r0, const double *sigma,
+                          const double *k0, double *R64, double *I64, double *partials,
+                          int nparts, double *scale, cudaStream_t s)
+{
+    PacketArgs P;
+    for (int a = 0; a < 3; ++a) {
+        P.r0[a] = r0[a];
+        P.sigma[a] = sigma[a];
+        P.k0[a] = k0[a];
+    }
+    packet_kernel<<<nparts, kThreads, 0, s>>>(m, P, R64, I64, partials);
+    sum_partials_kernel<<<1, kThreads, 0, s>>>(partials, nparts, m.hx * m.hy * m.hz, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_half(const MemberDev &m, const double *V64, const double *R64,
+                              const double *I64, const double *scale, int precision, int buf,
+                              cudaStream_t s)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    if (precision == 0)
+        scale_half_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, V64, R64, I64, scale, 0, buf);
+    else
+        scale_half_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, V64, R64, I64, scale,
+                                                                     precision == 2, buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(const MemberDev &m, const double *R64, const double *I64,
+                             int precision, int buf, cudaStream_t s)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    if (precision == 0)
+        set_state_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, R64, I64, 0, buf);
+    else
+        set_state_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, R64, I64, precision == 2, buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(const MemberDev &m, double *R64, double *I64, int precision,
+                             int buf, cudaStream_t s)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    if (precision == 0)
+        get_state_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, R64, I64, 0, buf);
+    else
+        get_state_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, R64, I64, precision == 2, buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observables(const MemberDev &m, int precision, int buf, double *partials,
+                               double *record, int *status, double q_ref, long long step,
+                               cudaStream_t s)
+{
+    if (precision == 0)
+        observables_kernel<double><<<kObsParts, kThreads, 0, s>>>(m, 0, buf, partials);
+    else
+        observables_kernel<float><<<kObsParts, kThreads, 0, s>>>(m, precision == 2, buf, partials);
+    observables_finalize_kernel<<<1, kThreads, 0, s>>>(m, partials, kObsParts, record, status,
+                                                       q_ref, step);
+    return cudaGetLastError();
+}
+
+}  // namespace tdse

@@ -1,0 +1,875 @@
+// C ABI of libtdse (declared in include/tdse.h): contexts, device memory,
+// TMA descriptors, work planning and the launch sequence of tdse_step.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tdse.h"
+#include "tdse_internal.cuh"
+
+using namespace tdse;
+
+namespace {
+
+constexpr int kRecCap = 256;        // observation records buffered on the device per member
+constexpr int kRecLen = 6;
+
+struct Member {
+    tdse_params p;                  // resolved parameters
+    MemberDev dev;                  // device pointers and geometry (tensor maps per config below)
+    double *V64 = nullptr;          // FP64 potential, unpadded
+    bool have_potential = false;
+    bool have_state = false;
+    std::vector<double> atoms;      // [n][4] if the potential came from atoms
+    double soft_a2 = 0.25, r_cut = 0.0;
+    double q0 = 0.0;                // Q at the last set_wavepacket / set_state
+    std::vector<double> hist;       // 4 per record: step, Q, norm_paper, energy
+};
+
+struct StepPlan {
+    int tsteps = 0;
+    StepConfig cfg{};
+    MemberDev *d_members = nullptr; // members with tensor maps for this config's box
+    WorkDev *d_work = nullptr;
+    int grid = 0;
+};
+
+}  // namespace
+
+struct tdse_ctx {
+    std::vector<Member> m;
+    int precision = 0, tblock = 1, obs_every = 20, ckpt_every = 0;
+    tdse_alloc_fn alloc_fn = nullptr;
+    tdse_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+    cudaStream_t stream = nullptr;
+    bool device_ready = false;
+    std::vector<void *> allocations;
+    StepPlan plans[kMaxTblock + 1];
+    int *d_counter = nullptr;
+    int *d_status = nullptr;
+    double *d_partials = nullptr;
+    double *d_scale = nullptr;
+    double *d_records = nullptr;    // [B][kRecCap][kRecLen]
+    int cur = 0;                    // ping-pong buffer holding the state
+    long long step = 0;
+    int sms = 0;
+    bool profiling = false;
+    tdse_profile prof{};
+    std::vector<cudaEvent_t> event_pool;           // reused timing events
+    std::vector<std::pair<int, int>> pending;      // (start, stop) indices into event_pool
+    std::vector<int> pending_kind;                 // 0: step launch, 1: reductions
+    size_t events_used = 0;
+    std::string err;
+};
+
+namespace {
+
+const char *kVersion = "libtdse 1.0 (sm_103a)";
+
+tdse_status fail(tdse_ctx *c, tdse_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(ctx, TDSE_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                 \
+    } while (0)
+
+#define TRY(expr)                                                                            \
+    do {                                                                                     \
+        tdse_status s_ = (expr);                                                             \
+        if (s_ != TDSE_OK) return s_;                                                        \
+    } while (0)
+
+size_t elem_size(int precision) { return precision == TDSE_FP64 ? 8 : 4; }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+tdse_status dalloc(tdse_ctx *c, size_t bytes, void **out)
+{
+    void *p = nullptr;
+    if (c->alloc_fn) {
+        p = c->alloc_fn(bytes, c->alloc_user);
+        if (!p) return fail(c, TDSE_ENOMEM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess)
+            return fail(c, TDSE_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocations.push_back(p);
+    CUDA_TRY(c, cudaMemsetAsync(p, 0, bytes, c->stream));
+    *out = p;
+    return TDSE_OK;
+}
+
+void dfree(tdse_ctx *c, void *p)
+{
+    if (!p) return;
+    auto it = std::find(c->allocations.begin(), c->allocations.end(), p);
+    if (it != c->allocations.end()) c->allocations.erase(it);
+    if (c->free_fn)
+        c->free_fn(p, c->alloc_user);
+    else
+        cudaFree(p);
+}
+
+tdse_status validate(tdse_ctx *c, const tdse_params &q, int idx)
+{
+    if (q.nx < 4 || q.ny < 1 || q.nz < 3)
+        return fail(c, TDSE_EINVAL, "member %d: grid %dx%dx%d too small (nx >= 4, nz >= 3)", idx,
+                    q.nx, q.ny, q.nz);
+    if (q.nx % 4 != 0) return fail(c, TDSE_EINVAL, "member %d: nx=%d is not a multiple of 4", idx, q.nx);
+    if (!(q.hx > 0 && q.hy > 0 && q.hz > 0))
+        return fail(c, TDSE_EINVAL, "member %d: spacings must be positive", idx);
+    for (int a = 0; a < 3; ++a)
+        if (q.bc[a] != TDSE_BC_PERIODIC && q.bc[a] != TDSE_BC_DIRICHLET)
+            return fail(c, TDSE_EINVAL, "member %d: bad boundary flag on axis %d", idx, a);
+    if ((q.bc[0] == TDSE_BC_PERIODIC && q.nx < kGhost) || (q.bc[1] == TDSE_BC_PERIODIC && q.ny < kGhost))
+        return fail(c, TDSE_EINVAL, "member %d: periodic axis shorter than %d nodes", idx, kGhost);
+    if (q.mask_lo < 0 || q.mask_hi < 0 || q.mask_lo + q.mask_hi > q.nz)
+        return fail(c, TDSE_EINVAL, "member %d: absorbing layers exceed nz", idx);
+    if (q.det_k < -1 || q.det_k > q.nz - 2)
+        return fail(c, TDSE_EINVAL, "member %d: det_k=%d outside [-1, nz-2]", idx, q.det_k);
+    // free-particle stability of the leapfrog: dt * max eigenvalue of H / hbar < 2
+    const double emax = 2.0 * q.hbar / q.mass *
+                        (1.0 / (q.hx * q.hx) + 1.0 / (q.hy * q.hy) + 1.0 / (q.hz * q.hz));
+    if (!(q.dt > 0) || q.dt * emax >= 2.0)
+        return fail(c, TDSE_EINVAL, "member %d: dt=%g violates dt*max|E|/hbar < 2 (max %g)", idx,
+                    q.dt, 2.0 / emax);
+    for (int r : q.reserved)
+        if (r != 0) return fail(c, TDSE_EINVAL, "member %d: reserved fields must be zero", idx);
+    return TDSE_OK;
+}
+
+tdse_status check_member(tdse_ctx *c, int member)
+{
+    if (!c) return TDSE_EINVAL;
+    if (member < 0 || member >= static_cast<int>(c->m.size()))
+        return fail(c, TDSE_EINVAL, "member %d out of range [0, %zu)", member, c->m.size());
+    return TDSE_OK;
+}
+
+tdse_status encode_map(tdse_ctx *c, CUtensorMap *map, const Member &mb, void *ptr, int box_x,
+                       int box_y)
+{
+    auto fn = encode_fn();
+    if (!fn) return fail(c, TDSE_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    const size_t es = elem_size(c->precision);
+    const MemberDev &d = mb.dev;
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(d.nx + 2 * d.G),
+                          static_cast<cuuint64_t>(d.ny + 2 * d.G), static_cast<cuuint64_t>(d.nz)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(d.pitch) * es,
+                             static_cast<cuuint64_t>(d.plane) * es};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(box_x), static_cast<cuuint32_t>(box_y), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    3, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, TDSE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+    return TDSE_OK;
+}
+
+// z-chunk length minimising the estimated makespan ceil(items / P) * (L + 2T)
+// of the dynamically scheduled work list.
+int choose_chunk(const std::vector<int> &tiles, const std::vector<int> &nz, int tsteps, int P)
+{
+    int nzmax = *std::max_element(nz.begin(), nz.end());
+    double best = 1e300;
+    int bestL = nzmax;
+    for (int L = 8; L <= nzmax; ++L) {
+        long long items = 0;
+        for (size_t i = 0; i < tiles.size(); ++i) items += static_cast<long long>(tiles[i]) * ((nz[i] + L - 1) / L);
+        const double span = static_cast<double>((items + P - 1) / P) * (L + 2.0 * tsteps);
+        if (span < best - 1e-9 || (std::fabs(span - best) < 1e-9 && L > bestL)) {
+            best = span;
+            bestL = L;
+        }
+    }
+    return bestL;
+}
+
+tdse_status build_plans(tdse_ctx *c)
+{
+    const int B = static_cast<int>(c->m.size());
+    for (int T = 1; T <= c->tblock; ++T) {
+        if (T != 1 && T != c->tblock) continue;
+        StepPlan &pl = c->plans[T];
+        pl.tsteps = T;
+        if (!step_config(c->precision, T, &pl.cfg))
+            return fail(c, TDSE_EINVAL, "no kernel for precision %d with %d fused steps", c->precision, T);
+        std::vector<MemberDev> hm(B);
+        WorkDev w{};
+        w.nmembers = B;
+        std::vector<int> tiles(B), nzs(B);
+        for (int i = 0; i < B; ++i) {
+            const Member &mb = c->m[i];
+            hm[i] = mb.dev;
+            MemberDev &d = hm[i];
+            for (int b = 0; b < 2; ++b) {
+                TRY(encode_map(c, &d.tm_R[b], mb, d.R[b], pl.cfg.box_x, pl.cfg.box_y));
+                TRY(encode_map(c, &d.tm_I[b], mb, d.I[b], pl.cfg.box_x, pl.cfg.box_y));
+                if (c->precision == TDSE_FP32_KAHAN) {
+                    TRY(encode_map(c, &d.tm_cR[b], mb, d.cR[b], pl.cfg.box_x, pl.cfg.box_y));
+                    TRY(encode_map(c, &d.tm_cI[b], mb, d.cI[b], pl.cfg.box_x, pl.cfg.box_y));
+                }
+            }
+            TRY(encode_map(c, &d.tm_d, mb, d.d, pl.cfg.box_x, pl.cfg.box_y));
+            w.tiles_x[i] = (d.nx + pl.cfg.tile_x - 1) / pl.cfg.tile_x;
+            w.tiles_y[i] = (d.ny + pl.cfg.tile_y - 1) / pl.cfg.tile_y;
+            tiles[i] = w.tiles_x[i] * w.tiles_y[i];
+            nzs[i] = d.nz;
+        }
+        int occ = 1;
+        c->sms = 0;
+        int dev = 0;
+        CUDA_TRY(c, cudaGetDevice(&dev));
+        CUDA_TRY(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+        occ = std::max(1, pl.cfg.ctas_per_sm);
+        const int P = c->sms * occ;
+        const int L = choose_chunk(tiles, nzs, T, P);
+        int total = 0;
+        for (int i = 0; i < B; ++i) {
+            w.item_begin[i] = total;
+            w.chunk[i] = std::min(L, nzs[i]);
+            total += tiles[i] * ((nzs[i] + w.chunk[i] - 1) / w.chunk[i]);
+        }
+        w.item_begin[B] = total;
+        w.total = total;
+        pl.grid = std::min(total, P);
+        void *p = nullptr;
+        TRY(dalloc(c, sizeof(MemberDev) * B, &p));
+        pl.d_members = static_cast<MemberDev *>(p);
+        TRY(dalloc(c, sizeof(WorkDev), &p));
+        pl.d_work = static_cast<WorkDev *>(p);
+        CUDA_TRY(c, cudaMemcpyAsync(pl.d_members, hm.data(), sizeof(MemberDev) * B,
+                                    cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(pl.d_work, &w, sizeof(WorkDev), cudaMemcpyHostToDevice, c->stream));
+    }
+    return TDSE_OK;
+}
+
+// Allocate every device buffer of the context (first call only).
+tdse_status ensure_device(tdse_ctx *c)
+{
+    if (c->device_ready) return TDSE_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(c, TDSE_ECUDA, "no CUDA device available");
+    const size_t es = elem_size(c->precision);
+    for (Member &mb : c->m) {
+        MemberDev &d = mb.dev;
+        const size_t fbytes = static_cast<size_t>(d.plane) * d.nz * es;
+        void *p;
+        for (int b = 0; b < 2; ++b) {
+            TRY(dalloc(c, fbytes, &p)); d.R[b] = p;
+            TRY(dalloc(c, fbytes, &p)); d.I[b] = p;
+            if (c->precision == TDSE_FP32_KAHAN) {
+                TRY(dalloc(c, fbytes, &p)); d.cR[b] = p;
+                TRY(dalloc(c, fbytes, &p)); d.cI[b] = p;
+            }
+        }
+        TRY(dalloc(c, fbytes, &p)); d.d = p;
+        const size_t cells = static_cast<size_t>(d.nx) * d.ny * d.nz;
+        TRY(dalloc(c, cells * sizeof(double), &p)); mb.V64 = static_cast<double *>(p);
+        TRY(dalloc(c, static_cast<size_t>(d.nx) * d.ny * sizeof(double), &p)); d.flux = static_cast<double *>(p);
+        TRY(dalloc(c, static_cast<size_t>(d.nx) * d.ny * sizeof(double), &p)); d.jlast = static_cast<double *>(p);
+        // absorbing factor per plane: M = cos^2(eta (pi/2) depth / W) inside the layers
+        std::vector<double> M(d.nz, 1.0);
+        const tdse_params &q = mb.p;
+        for (int k = 0; k < d.nz; ++k) {
+            if (q.mask_lo > 0 && k < q.mask_lo) {
+                const double s = std::cos(q.mask_eta * 0.5 * M_PI * (q.mask_lo - k) / q.mask_lo);
+                M[k] = s * s;
+            }
+            if (q.mask_hi > 0 && k >= d.nz - q.mask_hi) {
+                const double s = std::cos(q.mask_eta * 0.5 * M_PI * (k - (d.nz - q.mask_hi) + 1) / q.mask_hi);
+                M[k] = s * s;
+            }
+        }
+        TRY(dalloc(c, d.nz * es, &p)); d.mask = p;
+        std::vector<float> Mf(M.begin(), M.end());
+        CUDA_TRY(c, cudaMemcpyAsync(d.mask, es == 8 ? static_cast<const void *>(M.data()) : Mf.data(),
+                                    d.nz * es, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    void *p;
+    TRY(dalloc(c, sizeof(int), &p)); c->d_counter = static_cast<int *>(p);
+    TRY(dalloc(c, sizeof(int), &p)); c->d_status = static_cast<int *>(p);
+    TRY(dalloc(c, kObsParts * 3 * sizeof(double), &p)); c->d_partials = static_cast<double *>(p);
+    TRY(dalloc(c, sizeof(double), &p)); c->d_scale = static_cast<double *>(p);
+    TRY(dalloc(c, c->m.size() * kRecCap * kRecLen * sizeof(double), &p));
+    c->d_records = static_cast<double *>(p);
+    TRY(build_plans(c));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->device_ready = true;
+    return TDSE_OK;
+}
+
+tdse_status fill_all_ghosts(tdse_ctx *c, Member &mb, int buf)
+{
+    const int es = static_cast<int>(elem_size(c->precision));
+    CUDA_TRY(c, launch_fill_ghosts(mb.dev, mb.dev.R[buf], es, c->stream));
+    CUDA_TRY(c, launch_fill_ghosts(mb.dev, mb.dev.I[buf], es, c->stream));
+    if (c->precision == TDSE_FP32_KAHAN) {
+        CUDA_TRY(c, launch_fill_ghosts(mb.dev, mb.dev.cR[buf], es, c->stream));
+        CUDA_TRY(c, launch_fill_ghosts(mb.dev, mb.dev.cI[buf], es, c->stream));
+    }
+    return TDSE_OK;
+}
+
+// Observation of member i at the current step into record slot `slot`.
+tdse_status observe(tdse_ctx *c, int i, int slot, double q_ref)
+{
+    Member &mb = c->m[i];
+    double *rec = c->d_records + (static_cast<size_t>(i) * kRecCap + slot) * kRecLen;
+    CUDA_TRY(c, launch_observables(mb.dev, c->precision, c->cur, c->d_partials, rec, c->d_status,
+                                   q_ref, c->step, c->stream));
+    return TDSE_OK;
+}
+
+tdse_status drain_records(tdse_ctx *c, int nrec)
+{
+    if (nrec <= 0) return TDSE_OK;
+    std::vector<double> host(c->m.size() * kRecCap * kRecLen);
+    CUDA_TRY(c, cudaMemcpyAsync(host.data(), c->d_records, host.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < c->m.size(); ++i)
+        for (int r = 0; r < nrec; ++r) {
+            const double *x = &host[(i * kRecCap + r) * kRecLen];
+            c->m[i].hist.insert(c->m[i].hist.end(), {x[0], x[1], x[2], x[3]});
+        }
+    return TDSE_OK;
+}
+
+tdse_status check_status(tdse_ctx *c)
+{
+    int st = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (st & 1) return fail(c, TDSE_ETIMEOUT, "a bounded wait in the step kernel expired");
+    if (st & 2) return fail(c, TDSE_EUNSTABLE, "non-finite values or growth of Q detected");
+    return TDSE_OK;
+}
+
+tdse_status next_event(tdse_ctx *c, int *idx)
+{
+    if (c->events_used == c->event_pool.size()) {
+        cudaEvent_t e;
+        CUDA_TRY(c, cudaEventCreate(&e));
+        c->event_pool.push_back(e);
+    }
+    *idx = static_cast<int>(c->events_used++);
+    return TDSE_OK;
+}
+
+// Open a timed interval on the stream (profiling only); returns the start index.
+tdse_status timer_start(tdse_ctx *c, int *start)
+{
+    *start = -1;
+    if (!c->profiling) return TDSE_OK;
+    TRY(next_event(c, start));
+    CUDA_TRY(c, cudaEventRecord(c->event_pool[*start], c->stream));
+    return TDSE_OK;
+}
+
+tdse_status timer_stop(tdse_ctx *c, int start, int kind)
+{
+    if (start < 0) return TDSE_OK;
+    int stop;
+    TRY(next_event(c, &stop));
+    CUDA_TRY(c, cudaEventRecord(c->event_pool[stop], c->stream));
+    c->pending.push_back({start, stop});
+    c->pending_kind.push_back(kind);
+    return TDSE_OK;
+}
+
+// Accumulate the recorded intervals (call after the stream has been synchronised).
+tdse_status resolve_timers(tdse_ctx *c)
+{
+    for (size_t i = 0; i < c->pending.size(); ++i) {
+        float ms = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&ms, c->event_pool[c->pending[i].first],
+                                         c->event_pool[c->pending[i].second]));
+        if (c->pending_kind[i] == 0) {
+            c->prof.step_launches += 1;
+            c->prof.step_ms += ms;
+        } else {
+            c->prof.reduce_launches += 2 * static_cast<long long>(c->m.size());
+            c->prof.reduce_ms += ms;
+        }
+    }
+    c->pending.clear();
+    c->pending_kind.clear();
+    c->events_used = 0;
+    return TDSE_OK;
+}
+
+tdse_status launch_fused(tdse_ctx *c, int T)
+{
+    StepPlan &pl = c->plans[T];
+    StepLaunch L;
+    L.members = pl.d_members;
+    L.work = pl.d_work;
+    L.counter = c->d_counter;
+    L.status = c->d_status;
+    L.in_buf = c->cur;
+    L.grid = pl.grid;
+    L.block = pl.cfg.threads;
+    L.smem = pl.cfg.smem;
+    L.stream = c->stream;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream));
+    int t0;
+    TRY(timer_start(c, &t0));
+    CUDA_TRY(c, launch_step(c->precision, T, L));
+    TRY(timer_stop(c, t0, 0));
+    if (c->profiling) {
+        long long cells = 0;
+        for (const Member &mb : c->m) cells += static_cast<long long>(mb.dev.nx) * mb.dev.ny * mb.dev.nz;
+        c->prof.cells_per_launch = cells;
+        c->prof.steps_per_launch = T;
+    }
+    c->cur ^= 1;
+    c->step += T;
+    return TDSE_OK;
+}
+
+tdse_status observe_all(tdse_ctx *c, int slot)
+{
+    int t0;
+    TRY(timer_start(c, &t0));
+    for (size_t i = 0; i < c->m.size(); ++i) TRY(observe(c, static_cast<int>(i), slot, c->m[i].q0));
+    TRY(timer_stop(c, t0, 1));
+    return TDSE_OK;
+}
+
+// Observation of member i right now (synchronous) into rec[kRecLen].
+tdse_status current_obs(tdse_ctx *c, int i, double *rec)
+{
+    TRY(observe(c, i, kRecCap - 1, 0.0));
+    CUDA_TRY(c, cudaMemcpyAsync(rec, c->d_records + (static_cast<size_t>(i) * kRecCap + kRecCap - 1) * kRecLen,
+                                kRecLen * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return TDSE_OK;
+}
+
+tdse_status reset_run(tdse_ctx *c, int i)
+{
+    Member &mb = c->m[i];
+    const size_t pix = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * sizeof(double);
+    CUDA_TRY(c, cudaMemsetAsync(mb.dev.flux, 0, pix, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(mb.dev.jlast, 0, pix, c->stream));
+    mb.hist.clear();
+    mb.have_state = true;
+    double rec[kRecLen];
+    TRY(current_obs(c, i, rec));
+    mb.q0 = rec[1];
+    mb.hist.insert(mb.hist.end(), {static_cast<double>(c->step), rec[1], rec[2], rec[3]});
+    return TDSE_OK;
+}
+
+tdse_status potential_to_d(tdse_ctx *c, Member &mb, const double *V_dev)
+{
+    const int es = static_cast<int>(elem_size(c->precision));
+    CUDA_TRY(c, launch_build_d(mb.dev, es, V_dev, mb.V64, c->stream));
+    CUDA_TRY(c, launch_fill_ghosts(mb.dev, mb.dev.d, es, c->stream));
+    mb.have_potential = true;
+    return TDSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tdse_version(void) { return kVersion; }
+
+const char *tdse_last_error(const tdse_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : "NULL context";
+}
+
+tdse_status tdse_create(const tdse_params *p, int batch, tdse_ctx **out)
+{
+    if (!p || !out || batch < 1 || batch > 256) return TDSE_EINVAL;
+    *out = nullptr;
+    tdse_ctx *c = new tdse_ctx;
+    c->precision = p[0].precision;
+    if (c->precision < TDSE_FP64 || c->precision > TDSE_FP32_KAHAN) {
+        delete c;
+        return TDSE_EINVAL;
+    }
+    int tb = p[0].tblock;
+    if (tb <= 0) tb = (c->precision == TDSE_FP64) ? 1 : 2;
+    if (tb > kMaxTblock || (c->precision == TDSE_FP64 && tb != 1)) {
+        delete c;
+        return TDSE_EINVAL;
+    }
+    c->tblock = tb;
+    c->obs_every = p[0].obs_every > 0 ? p[0].obs_every : 20;
+    c->ckpt_every = std::max(0, p[0].ckpt_every);
+    for (int i = 0; i < batch; ++i) {
+        Member mb;
+        mb.p = p[i];
+        tdse_params &q = mb.p;
+        if (q.precision != p[0].precision || q.tblock != p[0].tblock ||
+            q.obs_every != p[0].obs_every || q.ckpt_every != p[0].ckpt_every) {
+            delete c;
+            return TDSE_EINVAL;
+        }
+        if (q.hbar <= 0) q.hbar = 1.0;
+        if (q.mass <= 0) q.mass = 1.0;
+        if (q.dt <= 0) {
+            const double h = std::min(q.hx, std::min(q.hy, q.hz));
+            q.dt = q.mass / (5.0 * q.hbar) * h * h;   // Eq. 11
+        }
+        tdse_status st = validate(c, q, i);
+        if (st != TDSE_OK) {
+            delete c;
+            return st;
+        }
+        MemberDev &d = mb.dev;
+        memset(&d, 0, sizeof d);
+        d.nx = q.nx;
+        d.ny = q.ny;
+        d.nz = q.nz;
+        d.G = kGhost;
+        d.pitch = ((q.nx + 2 * kGhost) + 31) / 32 * 32;
+        d.prow = q.ny + 2 * kGhost;
+        d.plane = static_cast<long long>(d.pitch) * d.prow;
+        d.per_x = q.bc[0] == TDSE_BC_PERIODIC;
+        d.per_y = q.bc[1] == TDSE_BC_PERIODIC;
+        d.per_z = q.bc[2] == TDSE_BC_PERIODIC;
+        d.det_k = q.det_k;
+        d.cx = q.hbar * q.dt / (2.0 * q.mass * q.hx * q.hx);
+        d.cy = q.hbar * q.dt / (2.0 * q.mass * q.hy * q.hy);
+        d.cz = q.hbar * q.dt / (2.0 * q.mass * q.hz * q.hz);
+        d.cv = q.dt / q.hbar;
+        d.cj = q.hbar / (q.mass * q.hz);
+        d.dt = q.dt;
+        d.hx = q.hx;
+        d.hy = q.hy;
+        d.hz = q.hz;
+        d.hbar = q.hbar;
+        c->m.push_back(mb);
+    }
+    *out = c;
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_allocator(tdse_ctx *c, tdse_alloc_fn alloc, tdse_free_fn free_fn, void *user)
+{
+    if (!c) return TDSE_EINVAL;
+    if (c->device_ready) return fail(c, TDSE_ESTATE, "allocator must be set before the first allocation");
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(c, TDSE_EINVAL, "alloc and free callbacks must both be set or both NULL");
+    c->alloc_fn = alloc;
+    c->free_fn = free_fn;
+    c->alloc_user = user;
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_stream(tdse_ctx *c, void *stream)
+{
+    if (!c) return TDSE_EINVAL;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_potential(tdse_ctx *c, int member, const double *V, int on_device)
+{
+    TRY(check_member(c, member));
+    if (!V) return fail(c, TDSE_EINVAL, "V is NULL");
+    TRY(ensure_device(c));
+    Member &mb = c->m[member];
+    const size_t bytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz * sizeof(double);
+    const double *Vd = V;
+    void *tmp = nullptr;
+    if (!on_device) {
+        TRY(dalloc(c, bytes, &tmp));
+        CUDA_TRY(c, cudaMemcpyAsync(tmp, V, bytes, cudaMemcpyHostToDevice, c->stream));
+        Vd = static_cast<const double *>(tmp);
+    }
+    tdse_status st = potential_to_d(c, mb, Vd);
+    if (tmp) {
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        dfree(c, tmp);
+    }
+    mb.atoms.clear();
+    return st;
+}
+
+tdse_status tdse_set_atoms(tdse_ctx *c, int member, int n, const double *xyzZ, double soft_a2,
+                           double r_cut)
+{
+    TRY(check_member(c, member));
+    if (n < 0 || (n > 0 && !xyzZ)) return fail(c, TDSE_EINVAL, "bad atom list");
+    if (!(soft_a2 > 0)) return fail(c, TDSE_EINVAL, "soft_a2 must be positive");
+    TRY(ensure_device(c));
+    Member &mb = c->m[member];
+    const MemberDev &d = mb.dev;
+    if (r_cut <= 0) {
+        double rc = 0;
+        bool any = false;
+        const double L[3] = {d.nx * d.hx, d.ny * d.hy, d.nz * d.hz};
+        const int per[3] = {d.per_x, d.per_y, d.per_z};
+        for (int a = 0; a < 3; ++a)
+            if (per[a]) {
+                rc = any ? std::min(rc, 0.5 * L[a]) : 0.5 * L[a];
+                any = true;
+            }
+        r_cut = rc;
+    }
+    const size_t cells = static_cast<size_t>(d.nx) * d.ny * d.nz;
+    void *V = nullptr, *A = nullptr;
+    TRY(dalloc(c, cells * sizeof(double), &V));
+    TRY(dalloc(c, std::max<size_t>(1, 4 * static_cast<size_t>(n)) * sizeof(double), &A));
+    if (n > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(A, xyzZ, 4 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, launch_potential_atoms(d, static_cast<double *>(A), n, soft_a2, r_cut,
+                                       static_cast<double *>(V), c->stream));
+    tdse_status st = potential_to_d(c, mb, static_cast<double *>(V));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    dfree(c, V);
+    dfree(c, A);
+    TRY(st);
+    mb.atoms.assign(xyzZ, xyzZ + 4 * n);
+    mb.soft_a2 = soft_a2;
+    mb.r_cut = r_cut;
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_wavepacket(tdse_ctx *c, int member, const double r0[3], const double sigma[3],
+                                const double k0[3])
+{
+    TRY(check_member(c, member));
+    if (!r0 || !sigma || !k0) return fail(c, TDSE_EINVAL, "NULL packet parameter");
+    TRY(ensure_device(c));
+    Member &mb = c->m[member];
+    if (!mb.have_potential) TRY(potential_to_d(c, mb, nullptr));   // V = 0
+    const size_t cells = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz;
+    void *R = nullptr, *I = nullptr;
+    TRY(dalloc(c, cells * sizeof(double), &R));
+    TRY(dalloc(c, cells * sizeof(double), &I));
+    CUDA_TRY(c, launch_packet(mb.dev, r0, sigma, k0, static_cast<double *>(R),
+                              static_cast<double *>(I), c->d_partials, kObsParts, c->d_scale,
+                              c->stream));
+    CUDA_TRY(c, launch_scale_half(mb.dev, mb.V64, static_cast<double *>(R),
+                                  static_cast<double *>(I), c->d_scale, c->precision, c->cur,
+                                  c->stream));
+    TRY(fill_all_ghosts(c, mb, c->cur));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    dfree(c, R);
+    dfree(c, I);
+    return reset_run(c, member);
+}
+
+tdse_status tdse_set_state(tdse_ctx *c, int member, const double *R, const double *I, int on_device)
+{
+    TRY(check_member(c, member));
+    if (!R || !I) return fail(c, TDSE_EINVAL, "NULL state");
+    TRY(ensure_device(c));
+    Member &mb = c->m[member];
+    if (!mb.have_potential) TRY(potential_to_d(c, mb, nullptr));
+    const size_t bytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz * sizeof(double);
+    const double *Rd = R, *Id = I;
+    void *tR = nullptr, *tI = nullptr;
+    if (!on_device) {
+        TRY(dalloc(c, bytes, &tR));
+        TRY(dalloc(c, bytes, &tI));
+        CUDA_TRY(c, cudaMemcpyAsync(tR, R, bytes, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(tI, I, bytes, cudaMemcpyHostToDevice, c->stream));
+        Rd = static_cast<double *>(tR);
+        Id = static_cast<double *>(tI);
+    }
+    CUDA_TRY(c, launch_set_state(mb.dev, Rd, Id, c->precision, c->cur, c->stream));
+    TRY(fill_all_ghosts(c, mb, c->cur));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    dfree(c, tR);
+    dfree(c, tI);
+    return reset_run(c, member);
+}
+
+tdse_status tdse_step(tdse_ctx *c, long long nsteps)
+{
+    if (!c || nsteps < 0) return TDSE_EINVAL;
+    for (size_t i = 0; i < c->m.size(); ++i)
+        if (!c->m[i].have_state)
+            return fail(c, TDSE_ESTATE, "member %zu has no state (call tdse_set_wavepacket)", i);
+    TRY(ensure_device(c));
+    int nrec = 0;
+    long long left = nsteps;
+    while (left > 0) {
+        const long long to_obs = c->obs_every - (c->step % c->obs_every);
+        long long seg = std::min(left, to_obs);
+        while (seg > 0) {
+            const int T = (seg >= c->tblock) ? c->tblock : 1;
+            TRY(launch_fused(c, T));
+            seg -= T;
+            left -= T;
+        }
+        if (c->step % c->obs_every == 0) {
+            TRY(observe_all(c, nrec));
+            if (++nrec == kRecCap) {
+                TRY(drain_records(c, nrec));
+                nrec = 0;
+            }
+        }
+    }
+    TRY(drain_records(c, nrec));
+    TRY(check_status(c));
+    return resolve_timers(c);
+}
+
+tdse_status tdse_observables(tdse_ctx *c, int member, tdse_obs *out)
+{
+    TRY(check_member(c, member));
+    if (!out) return fail(c, TDSE_EINVAL, "NULL output");
+    Member &mb = c->m[member];
+    if (!mb.have_state) return fail(c, TDSE_ESTATE, "member has no state");
+    double rec[kRecLen];
+    TRY(current_obs(c, member, rec));
+    out->Q = rec[1];
+    out->norm_paper = rec[2];
+    out->energy = rec[3];
+    out->flux = rec[4];
+    out->flux_integrated = rec[5];
+    out->step = c->step;
+    out->t = c->step * mb.p.dt;
+    return TDSE_OK;
+}
+
+tdse_status tdse_get_obs_history(tdse_ctx *c, int member, double *out, int cap, int *count)
+{
+    TRY(check_member(c, member));
+    const std::vector<double> &h = c->m[member].hist;
+    const int n = static_cast<int>(h.size() / 4);
+    if (count) *count = n;
+    if (out && cap > 0) memcpy(out, h.data(), std::min(cap, n) * 4 * sizeof(double));
+    return TDSE_OK;
+}
+
+tdse_status tdse_get_state(tdse_ctx *c, int member, double *R, double *I, int on_device)
+{
+    TRY(check_member(c, member));
+    Member &mb = c->m[member];
+    if (!mb.have_state) return fail(c, TDSE_ESTATE, "member has no state");
+    const size_t bytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz * sizeof(double);
+    if (on_device) {
+        CUDA_TRY(c, launch_get_state(mb.dev, R, I, c->precision, c->cur, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        return TDSE_OK;
+    }
+    void *tR = nullptr, *tI = nullptr;
+    if (R) TRY(dalloc(c, bytes, &tR));
+    if (I) TRY(dalloc(c, bytes, &tI));
+    CUDA_TRY(c, launch_get_state(mb.dev, static_cast<double *>(tR), static_cast<double *>(tI),
+                                 c->precision, c->cur, c->stream));
+    if (R) CUDA_TRY(c, cudaMemcpyAsync(R, tR, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (I) CUDA_TRY(c, cudaMemcpyAsync(I, tI, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    dfree(c, tR);
+    dfree(c, tI);
+    return TDSE_OK;
+}
+
+tdse_status tdse_get_flux_map(tdse_ctx *c, int member, double *F, int on_device)
+{
+    TRY(check_member(c, member));
+    if (!F) return fail(c, TDSE_EINVAL, "NULL output");
+    TRY(ensure_device(c));
+    Member &mb = c->m[member];
+    const size_t bytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * sizeof(double);
+    CUDA_TRY(c, cudaMemcpyAsync(F, mb.dev.flux, bytes,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return TDSE_OK;
+}
+
+tdse_status tdse_get_potential(tdse_ctx *c, int member, double *V, int on_device)
+{
+    TRY(check_member(c, member));
+    if (!V) return fail(c, TDSE_EINVAL, "NULL output");
+    Member &mb = c->m[member];
+    if (!mb.have_potential) return fail(c, TDSE_ESTATE, "member has no potential");
+    const size_t bytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz * sizeof(double);
+    CUDA_TRY(c, cudaMemcpyAsync(V, mb.V64, bytes,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return TDSE_OK;
+}
+
+tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *, double *, double *, int)
+{
+    TRY(check_member(c, member));
+    return fail(c, TDSE_ESTATE, "adjoint not available in this build");
+}
+
+tdse_status tdse_save_state(tdse_ctx *c, const char *path)
+{
+    if (!c || !path) return TDSE_EINVAL;
+    return fail(c, TDSE_ESTATE, "save_state not available in this build");
+}
+
+tdse_status tdse_load_state(tdse_ctx *c, const char *path)
+{
+    if (!c || !path) return TDSE_EINVAL;
+    return fail(c, TDSE_ESTATE, "load_state not available in this build");
+}
+
+tdse_status tdse_set_profiling(tdse_ctx *c, int enable)
+{
+    if (!c) return TDSE_EINVAL;
+    c->profiling = enable != 0;
+    c->prof = tdse_profile{};
+    return TDSE_OK;
+}
+
+tdse_status tdse_get_profile(tdse_ctx *c, tdse_profile *out)
+{
+    if (!c || !out) return TDSE_EINVAL;
+    *out = c->prof;
+    return TDSE_OK;
+}
+
+tdse_status tdse_destroy(tdse_ctx *c)
+{
+    if (!c) return TDSE_OK;
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    std::vector<void *> all = c->allocations;
+    for (void *p : all) dfree(c, p);
+    delete c;
+    return TDSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Internal declarations shared by the translation units of libtdse.
+//
+// Device data layout of one member (all fields of the context's precision Real):
+//   padded planes of (nx + 2G) x (ny + 2G) nodes with ghost width G on x and y;
+//   row pitch `pitch` elements (a multiple of 16 bytes), `prow` = ny + 2G rows,
+//   nz planes; element (x, y, z) with unpadded x in [-G, nx+G) lives at
+//   ((z * prow) + (y + G)) * pitch + (x + G).
+//   Periodic axes keep copies of the opposite boundary strips in their ghost
+//   zones (refreshed by every kernel that writes the field); walled axes keep
+//   zeros there.  The fused step reads whole tiles with TMA and never wraps
+//   indices in x or y.
+// Fields: R[2], I[2] (ping-pong: each step launch reads one and writes the other),
+//   cR[2], cI[2] (Kahan compensation, FP32_KAHAN only), d (the diagonal of the
+//   operator A: d = -2 (c_x + c_y + c_z) - c_v V), flux and jlast (FP64 [ny][nx]),
+//   mask[nz] (Real).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tdse {
+
+constexpr int kGhost = 8;          // ghost width on x and y (supports up to 4 fused steps)
+constexpr int kMaxTblock = 2;      // largest number of steps fused per launch
+
+struct alignas(128) MemberDev {
+    CUtensorMap tm_R[2], tm_I[2], tm_cR[2], tm_cI[2], tm_d;
+    void *R[2];
+    void *I[2];
+    void *cR[2];
+    void *cI[2];
+    void *d;
+    void *mask;            // Real[nz]
+    double *flux;          // [ny][nx], time-integrated flux
+    double *jlast;         // [ny][nx], flux of the last step
+    long long plane;       // elements per padded plane = pitch * prow
+    int nx, ny, nz, G, pitch, prow;
+    int per_x, per_y, per_z, det_k;
+    double cx, cy, cz, cv, cj, dt;
+    double hx, hy, hz, hbar;
+};
+
+// Work decomposition of one fused-step launch configuration over all members:
+// member m owns items [item_begin[m], item_begin[m+1]); item i of member m is
+// tile (i % tiles_x, (i / tiles_x) % tiles_y) of z-chunk i / (tiles_x tiles_y).
+struct WorkDev {
+    int nmembers;
+    int total;
+    int item_begin[257];
+    int tiles_x[256];
+    int tiles_y[256];
+    int chunk[256];        // z planes per chunk (last chunk may be shorter)
+};
+
+struct StepLaunch {
+    const MemberDev *members;
+    const WorkDev *work;
+    int *counter;          // dynamic work counter, zeroed before the launch
+    int *status;           // error word (bit 0: barrier timeout)
+    int in_buf;            // ping-pong index read by this launch
+    int grid, block;
+    size_t smem;
+    cudaStream_t stream;
+};
+
+// Launch configuration of a fused step: precision, fused steps and Kahan.
+struct StepConfig {
+    int tile_x, tile_y;    // output tile (x, y)
+    int box_x, box_y;      // TMA box (region) loaded per plane
+    int threads;
+    size_t smem;
+    int ctas_per_sm;
+};
+
+// step_kernels.cu
+bool step_config(int precision, int tsteps, StepConfig *cfg);
+cudaError_t launch_step(int precision, int tsteps, const StepLaunch &L);
+
+// aux_kernels.cu
+cudaError_t launch_fill_ghosts(const MemberDev &m, void *field, int elem, cudaStream_t s);
+cudaError_t launch_potential_atoms(const MemberDev &m, const double *atoms, int n, double a2,
+                                   double rc, double *V, cudaStream_t s);
+// d (padded, Real) from V (unpadded FP64, NULL: V = 0); V copied into V64
+cudaError_t launch_build_d(const MemberDev &m, int elem, const double *V, double *V64,
+                           cudaStream_t s);
+// psi0 of Eq. 3 into R64/I64 (unpadded FP64) and the normalisation factor into *scale
+cudaError_t launch_packet(const MemberDev &m, const double *r0, const double *sigma,
+                          const double *k0, double *R64, double *I64, double *partials,
+                          int nparts, double *scale, cudaStream_t s);
+cudaError_t launch_scale_half(const MemberDev &m, const double *V64, const double *R64,
+                              const double *I64, const double *scale, int precision, int buf,
+                              cudaStream_t s);
+cudaError_t launch_set_state(const MemberDev &m, const double *R64, const double *I64,
+                             int precision, int buf, cudaStream_t s);
+cudaError_t launch_get_state(const MemberDev &m, double *R64, double *I64, int precision,
+                             int buf, cudaStream_t s);
+// record[0..5] = {step, Q, norm_paper, energy, flux_last, flux_integrated}.  Sets status bit 1 if Q is
+// not finite or exceeds (1 + 1e-3) q_ref (q_ref <= 0: no growth check).
+cudaError_t launch_observables(const MemberDev &m, int precision, int buf, double *partials,
+                               double *record, int *status, double q_ref, long long step,
+                               cudaStream_t s);
+constexpr int kObsParts = 1216;     // fixed block count: the reduction order never changes
+
+}  // namespace tdse

@@ -1,0 +1,277 @@
+"""Thin ctypes binding of libtdse (include/tdse.h), function for function.
+
+Only argument marshalling happens here: every computation runs in the CUDA
+kernels of ``libtdse.so``.  Arrays may be numpy arrays (host memory) or torch
+CUDA tensors (device memory, float64, contiguous); the ``on_device`` flag of the
+C call is derived from the argument.  Every non-zero status raises ``TdseError``
+with the library's message.  There is no fallback: if ``libtdse.so`` is missing
+or no GPU is present the calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtdse.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "TDSE_OK", -1: "TDSE_EINVAL", -2: "TDSE_ENOMEM", -3: "TDSE_ECUDA",
+                -4: "TDSE_EUNSTABLE", -5: "TDSE_ETIMEOUT", -6: "TDSE_ESTATE"}
+FP64, FP32, FP32_KAHAN = W.FP64, W.FP32, W.FP32_KAHAN
+
+
+class TdseError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
+                ("dt", ctypes.c_double), ("hbar", ctypes.c_double), ("mass", ctypes.c_double),
+                ("bc", ctypes.c_int * 3), ("mask_lo", ctypes.c_int), ("mask_hi", ctypes.c_int),
+                ("mask_eta", ctypes.c_double), ("det_k", ctypes.c_int),
+                ("obs_every", ctypes.c_int), ("ckpt_every", ctypes.c_int),
+                ("precision", ctypes.c_int), ("tblock", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("Q", ctypes.c_double), ("norm_paper", ctypes.c_double),
+                ("energy", ctypes.c_double), ("flux", ctypes.c_double),
+                ("flux_integrated", ctypes.c_double), ("t", ctypes.c_double),
+                ("step", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("step_launches", ctypes.c_longlong), ("step_ms", ctypes.c_double),
+                ("reduce_launches", ctypes.c_longlong), ("reduce_ms", ctypes.c_double),
+                ("cells_per_launch", ctypes.c_longlong), ("steps_per_launch", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+# C signatures: name -> (restype, argtypes)
+_VP, _I, _D, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+SIGNATURES = {
+    "tdse_create": (_I, [ctypes.POINTER(Params), _I, ctypes.POINTER(_VP)]),
+    "tdse_set_allocator": (_I, [_VP, ALLOC_FN, FREE_FN, _VP]),
+    "tdse_set_stream": (_I, [_VP, _VP]),
+    "tdse_set_potential": (_I, [_VP, _I, _VP, _I]),
+    "tdse_set_atoms": (_I, [_VP, _I, _I, _VP, _D, _D]),
+    "tdse_get_potential": (_I, [_VP, _I, _VP, _I]),
+    "tdse_set_wavepacket": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "tdse_set_state": (_I, [_VP, _I, _VP, _VP, _I]),
+    "tdse_step": (_I, [_VP, _LL]),
+    "tdse_observables": (_I, [_VP, _I, ctypes.POINTER(Obs)]),
+    "tdse_get_obs_history": (_I, [_VP, _I, _VP, _I, ctypes.POINTER(_I)]),
+    "tdse_get_state": (_I, [_VP, _I, _VP, _VP, _I]),
+    "tdse_get_flux_map": (_I, [_VP, _I, _VP, _I]),
+    "tdse_adjoint": (_I, [_VP, _I, _VP, _VP, _VP, _I]),
+    "tdse_save_state": (_I, [_VP, ctypes.c_char_p]),
+    "tdse_load_state": (_I, [_VP, ctypes.c_char_p]),
+    "tdse_set_profiling": (_I, [_VP, _I]),
+    "tdse_get_profile": (_I, [_VP, ctypes.POINTER(Profile)]),
+    "tdse_last_error": (ctypes.c_char_p, [_VP]),
+    "tdse_version": (ctypes.c_char_p, []),
+    "tdse_destroy": (_I, [_VP]),
+}
+
+_lib = None
+
+
+def lib():
+    """Open libtdse.so (built by ``paper_2401_07416_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2401_07416_gb300.build` (needs nvcc)")
+        _lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(_lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _lib
+
+
+def _check(ctx, status: int):
+    if status != OK:
+        msg = lib().tdse_last_error(ctx)
+        raise TdseError(status, msg.decode() if msg else "")
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _arg(a, writable=False):
+    """(pointer, on_device, keepalive) for a numpy array or a torch CUDA tensor."""
+    if a is None:
+        return None, 0, None
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("torch tensors passed to libtdse must be contiguous float64")
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0, a
+    arr = np.asarray(a)
+    if arr.dtype != np.float64 or not arr.flags.c_contiguous or (writable and not arr.flags.writeable):
+        if writable:
+            raise TypeError("output arrays must be writable C-contiguous float64")
+        arr = np.ascontiguousarray(arr, dtype=np.float64)
+    return arr.ctypes.data_as(ctypes.c_void_p), 0, arr
+
+
+def params_from_grid(g: W.Grid, precision: int = FP64, tblock: int = 0,
+                     ckpt_every: int = 0) -> Params:
+    p = Params()
+    p.nx, p.ny, p.nz = g.nx, g.ny, g.nz
+    p.hx, p.hy, p.hz = g.hx, g.hy, g.hz
+    p.dt, p.hbar, p.mass = g.dt, g.hbar, g.mass
+    p.bc[:] = list(g.bc)
+    p.mask_lo, p.mask_hi, p.mask_eta = g.mask_lo, g.mask_hi, g.mask_eta
+    p.det_k = g.det_k
+    p.obs_every = g.obs_every
+    p.ckpt_every = ckpt_every
+    p.precision = precision
+    p.tblock = tblock
+    return p
+
+
+# ------------------------------------------------------------------ C calls, same names
+
+def tdse_version() -> str:
+    return lib().tdse_version().decode()
+
+
+def tdse_create(params: Sequence[Params]):
+    arr = (Params * len(params))(*params)
+    ctx = ctypes.c_void_p()
+    st = lib().tdse_create(arr, len(params), ctypes.byref(ctx))
+    if st != OK:
+        raise TdseError(st, "tdse_create rejected the parameters")
+    return ctx
+
+
+def tdse_set_allocator(ctx, alloc_fn, free_fn, user=None):
+    _check(ctx, lib().tdse_set_allocator(ctx, alloc_fn, free_fn, user))
+
+
+def tdse_set_stream(ctx, stream_ptr: int):
+    _check(ctx, lib().tdse_set_stream(ctx, ctypes.c_void_p(stream_ptr)))
+
+
+def tdse_set_potential(ctx, member: int, V):
+    p, dev, keep = _arg(V)
+    _check(ctx, lib().tdse_set_potential(ctx, member, p, dev))
+
+
+def tdse_set_atoms(ctx, member: int, atoms, soft_a2: float = 0.25, r_cut: float = 0.0):
+    a = np.ascontiguousarray(atoms, dtype=np.float64).reshape(-1, 4)
+    _check(ctx, lib().tdse_set_atoms(ctx, member, a.shape[0], a.ctypes.data_as(ctypes.c_void_p),
+                                     soft_a2, r_cut))
+
+
+def tdse_get_potential(ctx, member: int, V):
+    p, dev, _ = _arg(V, writable=True)
+    _check(ctx, lib().tdse_get_potential(ctx, member, p, dev))
+    return V
+
+
+def tdse_set_wavepacket(ctx, member: int, r0, sigma, k0):
+    r0, sigma, k0 = (np.ascontiguousarray(v, dtype=np.float64) for v in (r0, sigma, k0))
+    _check(ctx, lib().tdse_set_wavepacket(ctx, member, r0.ctypes.data_as(ctypes.c_void_p),
+                                          sigma.ctypes.data_as(ctypes.c_void_p),
+                                          k0.ctypes.data_as(ctypes.c_void_p)))
+
+
+def tdse_set_state(ctx, member: int, R, I):
+    pr, dr, kr = _arg(R)
+    pi, di, ki = _arg(I)
+    if dr != di:
+        raise TypeError("R and I must both be host or both be device arrays")
+    _check(ctx, lib().tdse_set_state(ctx, member, pr, pi, dr))
+
+
+def tdse_step(ctx, nsteps: int):
+    _check(ctx, lib().tdse_step(ctx, int(nsteps)))
+
+
+def tdse_observables(ctx, member: int) -> dict:
+    o = Obs()
+    _check(ctx, lib().tdse_observables(ctx, member, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def tdse_get_obs_history(ctx, member: int) -> np.ndarray:
+    n = ctypes.c_int()
+    _check(ctx, lib().tdse_get_obs_history(ctx, member, None, 0, ctypes.byref(n)))
+    out = np.zeros((n.value, 4))
+    _check(ctx, lib().tdse_get_obs_history(ctx, member, out.ctypes.data_as(ctypes.c_void_p),
+                                           n.value, ctypes.byref(n)))
+    return out
+
+
+def tdse_get_state(ctx, member: int, R=None, I=None):
+    """Fill R and I (numpy or torch float64 of shape (nz, ny, nx)); returns them."""
+    pr, dr, _ = _arg(R, writable=True)
+    pi, di, _ = _arg(I, writable=True)
+    dev = dr if R is not None else di
+    _check(ctx, lib().tdse_get_state(ctx, member, pr, pi, dev))
+    return R, I
+
+
+def tdse_get_flux_map(ctx, member: int, F):
+    p, dev, _ = _arg(F, writable=True)
+    _check(ctx, lib().tdse_get_flux_map(ctx, member, p, dev))
+    return F
+
+
+def tdse_adjoint(ctx, member: int, dL_dF, dL_dV=None, dL_datoms=None):
+    pf, df, kf = _arg(dL_dF)
+    pv, dv, _ = _arg(dL_dV, writable=True)
+    pa, da, _ = _arg(dL_datoms, writable=True)
+    devs = {d for d, a in ((df, dL_dF), (dv, dL_dV), (da, dL_datoms)) if a is not None}
+    if len(devs) > 1:
+        raise TypeError("adjoint arrays must all be host or all be device arrays")
+    _check(ctx, lib().tdse_adjoint(ctx, member, pf, pv, pa, devs.pop() if devs else 0))
+
+
+def tdse_save_state(ctx, path: str):
+    _check(ctx, lib().tdse_save_state(ctx, os.fsencode(path)))
+
+
+def tdse_load_state(ctx, path: str):
+    _check(ctx, lib().tdse_load_state(ctx, os.fsencode(path)))
+
+
+def tdse_set_profiling(ctx, enable: bool):
+    _check(ctx, lib().tdse_set_profiling(ctx, int(bool(enable))))
+
+
+def tdse_get_profile(ctx) -> dict:
+    p = Profile()
+    _check(ctx, lib().tdse_get_profile(ctx, ctypes.byref(p)))
+    return {k: getattr(p, k) for k, _ in p._fields_ if k != "reserved"}
+
+
+def tdse_last_error(ctx) -> str:
+    m = lib().tdse_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def tdse_destroy(ctx):
+    if ctx:
+        lib().tdse_destroy(ctx)

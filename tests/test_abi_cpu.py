@@ -1,0 +1,120 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads and
+exports every function declared in include/tdse.h; the ctypes structures match
+the C layout; parameter validation and call-order errors come back as status
+codes; with no GPU the library fails loudly instead of falling back to the CPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2401_07416_gb300 import build as B
+from paper_2401_07416_gb300 import tdse as T
+from paper_2401_07416_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tdse.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return T.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"TDSE_API\s+[\w\s\*]+?\b(tdse_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    out = subprocess.run(["nm", "-D", "--defined-only", T.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(tdse_\w+)", out))
+    assert set(names) <= exported, set(names) - exported
+    for n in names:
+        assert hasattr(lib, n)
+    assert set(names) == set(T.SIGNATURES)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "tdse.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(tdse_params), offsetof(tdse_params, hx),
+         offsetof(tdse_params, bc), offsetof(tdse_params, mask_eta), offsetof(tdse_params, det_k),
+         offsetof(tdse_params, tblock), sizeof(tdse_obs), sizeof(tdse_profile));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    P = T.Params
+    assert vals == [ctypes.sizeof(P), P.hx.offset, P.bc.offset, P.mask_eta.offset,
+                    P.det_k.offset, P.tblock.offset, ctypes.sizeof(T.Obs), ctypes.sizeof(T.Profile)]
+
+
+def _params(**kw):
+    g = W.small_grid(16, 12, 20, bc=(0, 0, 1))
+    p = T.params_from_grid(g, precision=kw.pop("precision", T.FP32))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nx", 18),            # not a multiple of 4
+    ("nz", 2),
+    ("hx", 0.0),
+    ("dt", 10.0),          # far above the leapfrog stability bound
+    ("det_k", 19),         # needs det_k <= nz-2
+    ("mask_lo", 30),
+    ("precision", 7),
+    ("tblock", 5),
+])
+def test_create_rejects_bad_parameters(lib, field, value):
+    with pytest.raises(T.TdseError) as e:
+        T.tdse_create([_params(**{field: value})])
+    assert e.value.status == T.EINVAL
+
+
+def test_create_rejects_mixed_precision_batch(lib):
+    with pytest.raises(T.TdseError):
+        T.tdse_create([_params(), _params(precision=T.FP64)])
+
+
+def test_default_dt_is_eq11(lib):
+    p = _params(dt=0.0)
+    ctx = T.tdse_create([p])
+    T.tdse_destroy(ctx)   # accepted: dt <= 0 selects m min(h)^2 / (5 hbar)
+
+
+def test_call_order_and_no_gpu_errors(lib):
+    ctx = T.tdse_create([_params()])
+    try:
+        with pytest.raises(T.TdseError) as e:
+            T.tdse_step(ctx, 1)
+        assert e.value.status == T.ESTATE
+        with pytest.raises(T.TdseError) as e:
+            T.tdse_observables(ctx, 3)
+        assert e.value.status == T.EINVAL
+        import torch
+        if not torch.cuda.is_available():
+            # no CPU fallback: device work fails with a CUDA status
+            with pytest.raises(T.TdseError) as e:
+                T.tdse_set_wavepacket(ctx, 0, (1, 1, 1), (0.5, 0.5, 0.5), (0, 0, 1))
+            assert e.value.status in (T.ECUDA, T.ENOMEM)
+    finally:
+        T.tdse_destroy(ctx)
+
+
+def test_version_string(lib):
+    assert "sm_103a" in T.tdse_version()

@@ -1,0 +1,226 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (written here, used by every case):
+  FP64 GPU:        max |gpu - oracle| / max |oracle| <= 1e-11 for R, I, the flux map
+                   and the observables;
+  FP32 / Kahan:    ||psi_gpu - psi_oracle||_2 / ||psi_oracle||_2 <= 1e-4 and
+                   |Q_gpu - Q_oracle| / Q_oracle <= 1e-5;
+  fused vs unfused and batched vs solo: bitwise equal (same arithmetic, same order).
+Small grids span several tiles with ragged tails in x, y and z (tiles are 56 x 28
+in FP32 T=1, 56 x 24 in T=2, 60 x 20 in FP64; z-chunks are chosen per launch).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_07416_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+TOL32_L2 = 1e-4
+TOL32_Q = 1e-5
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_07416_gb300 import build
+    build.build()
+    from paper_2401_07416_gb300 import tdse
+    return tdse
+
+
+def make_sim(grids, precision, tblock=0, ckpt_every=0):
+    from paper_2401_07416_gb300.sim import Sim
+    return Sim(grids, precision=precision, tblock=tblock, ckpt_every=ckpt_every)
+
+
+def maxrel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def l2rel(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2)) / np.sqrt(np.sum(b ** 2)))
+
+
+CASES = {
+    # name: (nx, ny, nz, bc, mask, det_k)
+    "walls": (20, 37, 41, (1, 1, 1), 5, 12),
+    "slab": (132, 44, 50, (0, 0, 1), 6, 20),
+    "periodic": (24, 24, 30, (0, 0, 0), 0, 5),
+    "mixed": (36, 28, 33, (0, 1, 0), 4, 9),
+}
+
+
+def case(name, seed=0):
+    nx, ny, nz, bc, mask, det = CASES[name]
+    g = W.small_grid(nx, ny, nz, h=(0.21, 0.19, 0.23), dt=0.004, bc=bc, mask=mask, det_k=det,
+                     eta=0.5)
+    V = W.random_potential(g, 100 + seed, 2.0)
+    L = g.lengths
+    p = W.Packet((0.5 * L[0], 0.45 * L[1], 0.55 * L[2]), (0.9, 1.1, 0.8), (0.4, -0.3, -1.8))
+    return g, V, p
+
+
+def oracle_run(g, V, p, nsteps):
+    R0, I0 = oracle.initial_state(g, p, V)
+    R, I, F, jl = oracle.run(g, V, R0, I0, nsteps, use_mask=True, flux=g.det_k >= 0)
+    return (R0, I0), (R, I, F, jl), oracle.observables(g, V, R, I)
+
+
+def gpu_run(g, V, p, nsteps, precision, tblock=0):
+    s = make_sim(g, precision, tblock)
+    s.set_potential(0, V)
+    s.set_packet(0, p)
+    init = s.state(0)
+    s.step(nsteps)
+    R, I = s.state(0)
+    F = s.flux_map(0)
+    obs = s.observables(0)
+    s.close()
+    return init, (R, I, F), obs
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_matches_oracle(T, name):
+    g, V, p = case(name)
+    n = 23
+    (R0, I0), (Ro, Io, Fo, _), oo = oracle_run(g, V, p, n)
+    (Rg0, Ig0), (Rg, Ig, Fg), og = gpu_run(g, V, p, n, T.FP64)
+    assert maxrel(Rg0, R0) < 1e-13 and maxrel(Ig0, I0) < 1e-13
+    scale = max(np.abs(Ro).max(), np.abs(Io).max())
+    assert np.abs(Rg - Ro).max() / scale < TOL64
+    assert np.abs(Ig - Io).max() / scale < TOL64
+    if g.det_k >= 0:
+        assert maxrel(Fg, Fo) < TOL64
+    assert og["Q"] == pytest.approx(oo["Q"], rel=TOL64)
+    assert og["energy"] == pytest.approx(oo["energy"], rel=TOL64)
+    assert og["norm_paper"] == pytest.approx(oo["norm_paper"], rel=TOL64)
+
+
+@pytest.mark.parametrize("precision", ["FP32", "FP32_KAHAN"])
+@pytest.mark.parametrize("tblock", [1, 2])
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp32_matches_oracle(T, name, precision, tblock):
+    g, V, p = case(name, seed=1)
+    n = 23
+    _, (Ro, Io, Fo, _), oo = oracle_run(g, V, p, n)
+    _, (Rg, Ig, Fg), og = gpu_run(g, V, p, n, getattr(T, precision), tblock)
+    psi_err = math.sqrt(np.sum((Rg - Ro) ** 2 + (Ig - Io) ** 2) / np.sum(Ro ** 2 + Io ** 2))
+    assert psi_err < TOL32_L2
+    assert abs(og["Q"] - oo["Q"]) / oo["Q"] < TOL32_Q
+    if g.det_k >= 0 and np.abs(Fo).max() > 0:
+        assert l2rel(Fg, Fo) < 1e-3
+
+
+@pytest.mark.parametrize("precision", ["FP32", "FP32_KAHAN"])
+@pytest.mark.parametrize("name", ["slab", "mixed"])
+def test_fused_two_steps_bitwise_equal_to_one_step_launches(T, name, precision):
+    g, V, p = case(name, seed=2)
+    a = gpu_run(g, V, p, 18, getattr(T, precision), tblock=2)
+    b = gpu_run(g, V, p, 18, getattr(T, precision), tblock=1)
+    for x, y in zip(a[1], b[1]):
+        assert np.array_equal(x, y)
+
+
+def test_potential_from_atoms_matches_oracle(T):
+    g = W.small_grid(40, 36, 30, h=(0.2, 0.22, 0.25), bc=(0, 0, 1))
+    rng = np.random.default_rng(5)
+    atoms = np.column_stack([rng.uniform(0, 8, 12), rng.uniform(0, 7.9, 12),
+                             rng.uniform(1, 6, 12), rng.choice([1.0, 6.0, 8.0], 12)])
+    s = make_sim(g, T.FP64)
+    s.set_atoms(0, atoms)
+    Vg = s.potential(0)
+    s.close()
+    Vo = oracle.potential_atoms(g, atoms)
+    assert maxrel(Vg, Vo) < 1e-14
+
+
+def test_set_state_roundtrip_and_kahan_exactness(T):
+    g, V, p = case("slab")
+    R = W.random_field((g.nz, g.ny, g.nx), 7)
+    I = W.random_field((g.nz, g.ny, g.nx), 8)
+    for prec in (T.FP64, T.FP32_KAHAN):
+        s = make_sim(g, prec)
+        s.set_potential(0, V)
+        s.set_state(0, R, I)
+        Rg, Ig = s.state(0)
+        s.close()
+        # FP64 exact; Kahan stores value + compensation, recovering ~48 bits
+        tol = 0.0 if prec == T.FP64 else 1e-13
+        assert np.abs(Rg - R).max() <= tol * np.abs(R).max()
+        assert np.abs(Ig - I).max() <= tol * np.abs(I).max()
+
+
+def test_batched_members_equal_solo_runs(T):
+    names = ["walls", "slab", "mixed"]
+    cs = [case(n, seed=3) for n in names]
+    # the same precision and depth for the batch and the solo runs; walls/mixed
+    # differ in shape so the work list interleaves uneven members
+    for prec in (T.FP32_KAHAN, T.FP64):
+        s = make_sim([c[0] for c in cs], prec)
+        for i, (g, V, p) in enumerate(cs):
+            s.set_potential(i, V)
+            s.set_packet(i, p)
+        s.step(14)
+        batch = [(s.state(i), s.flux_map(i)) for i in range(len(cs))]
+        s.close()
+        for i, (g, V, p) in enumerate(cs):
+            _, (R, I, F), _ = gpu_run(g, V, p, 14, prec)
+            assert np.array_equal(batch[i][0][0], R)
+            assert np.array_equal(batch[i][0][1], I)
+            assert np.array_equal(batch[i][1], F)
+
+
+def test_config1_free_packet_full_size(T):
+    """64^3 FP64, 500 steps: GPU = oracle to 1e-11, and the oracle-pinned closed-form
+    drift of the centroid holds for the GPU result too."""
+    wl = W.config1()
+    g = wl.grid
+    (R0, I0), (Ro, Io, _, _), oo = oracle_run(g, None, wl.packet, wl.steps)
+    s = make_sim(g, T.FP64)
+    s.set_packet(0, wl.packet)
+    s.step(wl.steps)
+    Rg, Ig = s.state(0)
+    og = s.observables(0)
+    hist = s.history(0)
+    s.close()
+    scale = np.abs(Ro).max()
+    assert np.abs(Rg - Ro).max() / scale < TOL64
+    assert np.abs(Ig - Io).max() / scale < TOL64
+    assert og["Q"] == pytest.approx(oo["Q"], rel=TOL64)
+    # Q conserved along the run (no absorbing layer), every 20 steps
+    assert hist.shape[0] == wl.steps // g.obs_every + 1
+    assert np.abs(hist[:, 1] / hist[0, 1] - 1).max() < 1e-12
+
+
+def test_observation_history_and_eq11_default_dt(T):
+    g = W.small_grid(16, 16, 16, h=(0.2, 0.2, 0.2), dt=0.0, bc=(1, 1, 1))
+    s = make_sim(g, T.FP64)
+    s.set_packet(0, W.Packet((1.5, 1.5, 1.5), (0.5, 0.5, 0.5), (0, 0, 1)))
+    s.step(45)
+    h = s.history(0)
+    o = s.observables(0)
+    s.close()
+    assert list(h[:, 0]) == [0, 20, 40]
+    assert o["step"] == 45
+    assert o["t"] == pytest.approx(45 * 0.2 ** 2 / 5)
+
+
+def test_unstable_run_reports_status(T):
+    """A potential that makes the scheme unstable (dt |V| far above 2) grows the
+    invariant; tdse_step must report TDSE_EUNSTABLE instead of returning garbage."""
+    g = W.small_grid(16, 16, 16, h=(0.2, 0.2, 0.2), dt=0.004, bc=(1, 1, 1))
+    V = np.full((16, 16, 16), 3000.0)   # dt * V = 12 >> 2
+    s = make_sim(g, T.FP64)
+    s.set_potential(0, V)
+    s.set_packet(0, W.Packet((1.5, 1.5, 1.5), (0.5, 0.5, 0.5), (0, 0, 1)))
+    with pytest.raises(T.TdseError) as e:
+        s.step(200)
+    s.close()
+    assert e.value.status == T.EUNSTABLE
