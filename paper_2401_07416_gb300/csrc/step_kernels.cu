@@ -129,6 +129,12 @@ __device__ __forceinline__ void st_vec<double>(double *p, const double (&v)[2])
     *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
 }
 
+// Rounded product that the compiler may not fuse into a following add: the
+// absorbing factor must round identically whether its product is stored
+// (one step per launch) or consumed in registers (several steps per launch).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Compile-time shape of one fused-step kernel.
 template <typename Real_, int H_, int TPX_, int ROWS_, bool KAHAN_, int PF_>
 struct Cfg {
@@ -348,8 +354,8 @@ __global__ void __launch_bounds__(C::NT, 1)
                     if (odd) {   // I of the previous step still carries its absorbing factor
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
-                            acc[v] *= mq;
-                            cacc[v] *= mq;
+                            acc[v] = mul_rn(acc[v], mq);
+                            cacc[v] = mul_rn(cacc[v], mq);
                         }
                     }
                 }
@@ -374,8 +380,8 @@ __global__ void __launch_bounds__(C::NT, 1)
                         cout[v] = Real(0);
                     }
                     if (!odd) {          // Eq. 8 step complete: absorbing factor on R
-                        out[v] *= mq;
-                        cout[v] *= mq;
+                        out[v] = mul_rn(out[v], mq);
+                        cout[v] = mul_rn(cout[v], mq);
                     }
                     if (walls) {
                         out[v] *= keep[v];
@@ -414,8 +420,8 @@ __global__ void __launch_bounds__(C::NT, 1)
                     Real vi[VEC], vci[VEC];
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
-                        vi[v] = w[H - 1][1][v] * mq;
-                        vci[v] = cw[H - 1][1][v] * mq;
+                        vi[v] = mul_rn(w[H - 1][1][v], mq);
+                        vci[v] = mul_rn(cw[H - 1][1][v], mq);
                     }
                     // primary location plus the ghost copies of periodic axes
                     int xo[2] = {xs, xs};
