@@ -136,73 +136,85 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 // Compile-time shape of one fused-step kernel.
-template <typename Real_, int H_, int TPX_, int ROWS_, bool KAHAN_, int PF_>
+//   H     half-step stages per launch (2T)
+//   TPX   threads across a region row (VEC cells each)
+//   ROWS  region rows; each thread owns RPT consecutive rows
+//   PF    planes loaded ahead of use
+template <typename Real_, int H_, int TPX_, int ROWS_, int RPT_, bool KAHAN_, int PF_, int MINB_ = 1>
 struct Cfg {
     typedef Real_ Real;
-    static constexpr int H = H_;          // half-step stages per launch (2T)
-    static constexpr int TPX = TPX_;      // threads per region row
-    static constexpr int ROWS = ROWS_;    // region rows (one per thread row)
+    static constexpr int H = H_, TPX = TPX_, ROWS = ROWS_, RPT = RPT_, PF = PF_;
+    static constexpr int MINB = MINB_;                  // CTAs resident per SM
     static constexpr bool KAHAN = KAHAN_;
-    static constexpr int PF = PF_;        // planes loaded ahead
     static constexpr int VEC = VecOf<Real>::N;
-    static constexpr int W = VEC * TPX;   // region width (elements)
+    static constexpr int W = VEC * TPX;                 // region width (elements)
     static constexpr int AX = 16 / static_cast<int>(sizeof(Real));
     static constexpr int HX = (H + AX - 1) / AX * AX;   // x halo, TMA-aligned
     static constexpr int TX = W - 2 * HX;
     static constexpr int TY = ROWS - 2 * H;
-    static constexpr int NT = TPX * ROWS;
-    static constexpr int RW = 32 / TPX;   // rows per warp
-    static constexpr int NR = PF + 2, NI = PF + 2, ND = PF + H + 1;
-    static constexpr int NCR = KAHAN ? PF + 3 : 0, NCI = KAHAN ? PF + 2 : 0;
-    static constexpr int NCRm = KAHAN ? NCR : 1, NCIm = KAHAN ? NCI : 1;   // modulus-safe
-    static constexpr int NB = PF + 1;
+    static constexpr int NT = TPX * ROWS / RPT;
+    static constexpr int RW = 32 / TPX * RPT;           // rows per warp
     static constexpr int PLANE = W * ROWS;
     static constexpr int PLANE_BYTES = PLANE * static_cast<int>(sizeof(Real));
-    static constexpr int NSB = 2 * (H - 1);
-    static constexpr int NPLANES = NR + NI + ND + NCR + NCI + NSB;
+    static constexpr int NFA = KAHAN ? 4 : 2;           // R, I (, cR, cI) per ring slot
+    static constexpr int NA = PF + 3;                   // R is read two planes back
+    static constexpr int ND = PF + H + 1;               // d is read H planes back
+    static constexpr int NB = PF + 1;
+    static constexpr int NSB = 2 * (H - 1);             // stage planes, double-buffered
+    static constexpr int NPLANES = NA * NFA + ND + NSB;
     static constexpr size_t SMEM = static_cast<size_t>(NPLANES) * PLANE_BYTES + 8 * NB + 128;
-    static constexpr uint32_t TX_BYTES = PLANE_BYTES * (KAHAN ? 5 : 3);
+    static constexpr uint32_t TX_BYTES = PLANE_BYTES * (NFA + 1);
     static_assert(TPX <= 32 && 32 % TPX == 0, "a region row must sit inside one warp");
+    static_assert(ROWS % RPT == 0, "rows per thread must divide the region");
     static_assert(TX > 0 && TY > 0, "halo larger than region");
     static_assert(W <= 256 && ROWS <= 256, "TMA box dimension limit");
     static_assert(H % 2 == 0, "whole time steps only");
+    static_assert(SMEM <= 232448, "more than 227 KB of shared memory per CTA");
+    static_assert(MINB * (SMEM + 1024) <= 233472, "CTAs per SM exceed the shared memory");
 };
 
 template <class C>
-__global__ void __launch_bounds__(C::NT, 1)
+__global__ void __launch_bounds__(C::NT, C::MINB)
     fused_step_kernel(const MemberDev *__restrict__ members, const WorkDev *__restrict__ work,
                       int *counter, int *status, int in_buf)
 {
     typedef typename C::Real Real;
     constexpr int H = C::H, VEC = C::VEC, W = C::W, ROWS = C::ROWS, PLANE = C::PLANE;
-    constexpr int NB = C::NB, PF = C::PF;
+    constexpr int RPT = C::RPT, NB = C::NB, PF = C::PF, NA = C::NA, ND = C::ND;
+    constexpr int NF = H > 1 ? H - 1 : 1;   // register windows for F_1 .. F_{H-1}
+    constexpr int SLOT = C::NFA * PLANE;    // one ring slot: R, I (, cR, cI) of a plane
+    constexpr int OFF_I = PLANE, OFF_CR = 2 * PLANE, OFF_CI = 3 * PLANE;
+    // A f = cx sx + cy sy + cz sz + d f (s_a: neighbour sums).  FP64 (ALU-bound)
+    // folds the accumulator into the FMA chain; FP32 keeps the increment separate
+    // so that its rounding happens at the increment's scale.
+    constexpr bool CHAIN = sizeof(Real) == 8 && !C::KAHAN;
 
     extern __shared__ unsigned char smem_raw[];
-    Real *base = reinterpret_cast<Real *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
-                                          ~static_cast<uintptr_t>(127));
-    Real *ringR = base;
-    Real *ringI = ringR + C::NR * PLANE;
-    Real *ringD = ringI + C::NI * PLANE;
-    Real *ringCR = ringD + C::ND * PLANE;
-    Real *ringCI = ringCR + C::NCR * PLANE;
-    Real *sbuf = ringCI + C::NCI * PLANE;
+    Real *ringA = reinterpret_cast<Real *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                           ~static_cast<uintptr_t>(127));
+    Real *ringD = ringA + NA * SLOT;
+    Real *sbuf = ringD + ND * PLANE;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sbuf + C::NSB * PLANE);
     __shared__ int s_item;
+    __shared__ int s_abort;
 
     const int tid = threadIdx.x;
-    const int row = tid / C::TPX;
     const int qx = tid % C::TPX;
-    const int warp_row0 = (tid & ~31) / C::TPX;
+    const int r0 = (tid / C::TPX) * RPT;                 // first region row of this thread
+    const int warp_row0 = (tid >> 5) * C::RW;
+    const int own = r0 * W + qx * VEC;                   // row r of this thread: own + r * W
+    const int off_ym = (r0 > 0 ? r0 - 1 : r0) * W + qx * VEC;
+    const int off_yp = (r0 + RPT < ROWS ? r0 + RPT : r0 + RPT - 1) * W + qx * VEC;
 
     if (tid == 0) {
         for (int b = 0; b < NB; ++b) mbar_init(&bars[b], 1);
+        s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
 
     long long gbase = 0;   // loads issued by this CTA before the current item
-    bool aborted = false;
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -223,239 +235,331 @@ __global__ void __launch_bounds__(C::NT, 1)
         const int G = M.G, nx = M.nx, ny = M.ny, nz = M.nz;
         const int bx = G + tile_x * C::TX - C::HX;   // padded coordinates of the box
         const int by = G + tile_y * C::TY - H;
-        const int xs = tile_x * C::TX - C::HX + qx * VEC;  // unpadded x of this thread's first cell
-        const int ys = tile_y * C::TY - H + row;
+        const int xs = tile_x * C::TX - C::HX + qx * VEC;   // unpadded x of the first cell
+        const int ys0 = tile_y * C::TY - H + r0;             // unpadded y of row 0
         const bool zper = M.per_z != 0;
+        const int mlo = M.mask_lo, mhi = nz - M.mask_hi;    // planes outside [mlo, mhi) absorb
         const Real cx = static_cast<Real>(M.cx), cy = static_cast<Real>(M.cy),
                    cz = static_cast<Real>(M.cz);
         const Real *maskz = reinterpret_cast<const Real *>(M.mask);
+        const int kd = M.det_k;
+        const bool flux_owner = kd >= kz0 && kd < kz1;
+
+        // Cells outside the domain on a walled axis are kept at zero after every stage.
+        bool walls = false;
+        Real keep[RPT][VEC];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const bool in_x = M.per_x || (xs + v >= 0 && xs + v < nx);
+                const bool in_y = M.per_y || (ys0 + r >= 0 && ys0 + r < ny);
+                keep[r][v] = (in_x && in_y) ? Real(1) : Real(0);
+                walls |= !(in_x && in_y);
+            }
+        const bool col_in = qx * VEC >= C::HX && qx * VEC < C::HX + C::TX && xs < nx;
+        bool store_row[RPT];
+        bool any_store = false;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            store_row[r] = col_in && r0 + r >= H && r0 + r < H + C::TY && ys0 + r < ny;
+            any_store |= store_row[r];
+        }
+        // output offsets within a plane (primary location; ghost copies of periodic axes
+        // are added only on tiles that touch a seam)
+        const long long pitch = M.pitch;
+        const bool seam = (M.per_x && (xs < G || xs >= nx - G)) ||
+                          (M.per_y && (ys0 < G || ys0 + RPT - 1 >= ny - G));
         Real *outR = reinterpret_cast<Real *>(M.R[1 - in_buf]);
         Real *outI = reinterpret_cast<Real *>(M.I[1 - in_buf]);
         Real *outCR = reinterpret_cast<Real *>(M.cR[1 - in_buf]);
         Real *outCI = reinterpret_cast<Real *>(M.cI[1 - in_buf]);
+        const long long out0 = static_cast<long long>(ys0 + G) * pitch + (xs + G);
 
-        // Cells outside the domain on a walled axis are kept at zero after every stage.
-        const bool walls = (!M.per_x && (xs < 0 || xs + VEC > nx)) || (!M.per_y && (ys < 0 || ys >= ny));
-        Real keep[VEC];
+        // register windows of F_1 .. F_{H-1}: [0] old (q-1), [1] center (q), [2] new (q+1)
+        Real w[NF][3][RPT][VEC];
+        Real cw[C::KAHAN ? NF : 1][3][RPT][VEC];
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            const bool in_x = M.per_x || (xs + v >= 0 && xs + v < nx);
-            const bool in_y = M.per_y || (ys >= 0 && ys < ny);
-            keep[v] = (in_x && in_y) ? Real(1) : Real(0);
-        }
-        const bool store_cell = row >= H && row < H + C::TY && qx * VEC >= C::HX &&
-                                qx * VEC < C::HX + C::TX && ys < ny && xs < nx;
-        const int kd = M.det_k;
-        const bool flux_owner = kd >= kz0 && kd < kz1;
-
-        // Register windows of the stage outputs F_0 .. F_{H-1}: [0] old (q-1),
-        // [1] center (q), [2] new (q+1); Kahan compensation windows alongside.
-        Real w[H][3][VEC];
-        Real cw[H][3][VEC];
-#pragma unroll
-        for (int f = 0; f < H; ++f)
+        for (int f = 0; f < NF; ++f)
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    w[f][k][v] = Real(0);
-                    cw[f][k][v] = Real(0);
-                }
+                for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        w[f][k][r][v] = Real(0);
+                        if constexpr (C::KAHAN) cw[f][k][r][v] = Real(0);
+                    }
 
-        auto issue = [&](int l) {
+        int headA = 0, headD = 0;
+        int headB = static_cast<int>(gbase % NB);
+        uint32_t phase = static_cast<uint32_t>((gbase / NB) & 1);
+
+        auto issue = [&](int l, int ahead) {
             const int L = L0 + l;
             const int zc = zper ? ((L % nz) + nz) % nz : L;
-            uint64_t *bar = &bars[(gbase + l) % NB];
+            int b = headB + ahead; if (b >= NB) b -= NB;
+            int a = headA + ahead; if (a >= NA) a -= NA;
+            int d = headD + ahead; if (d >= ND) d -= ND;
+            uint64_t *bar = &bars[b];
+            Real *slot = ringA + a * SLOT;
             mbar_arrive_expect_tx(bar, C::TX_BYTES);
-            tma_load_3d(ringR + (l % C::NR) * PLANE, &M.tm_R[in_buf], bx, by, zc, bar);
-            tma_load_3d(ringI + (l % C::NI) * PLANE, &M.tm_I[in_buf], bx, by, zc, bar);
-            tma_load_3d(ringD + (l % C::ND) * PLANE, &M.tm_d, bx, by, zc, bar);
-            if (C::KAHAN) {
-                tma_load_3d(ringCR + (l % C::NCRm) * PLANE, &M.tm_cR[in_buf], bx, by, zc, bar);
-                tma_load_3d(ringCI + (l % C::NCIm) * PLANE, &M.tm_cI[in_buf], bx, by, zc, bar);
+            tma_load_3d(slot, &M.tm_R[in_buf], bx, by, zc, bar);
+            tma_load_3d(slot + OFF_I, &M.tm_I[in_buf], bx, by, zc, bar);
+            if constexpr (C::KAHAN) {
+                tma_load_3d(slot + OFF_CR, &M.tm_cR[in_buf], bx, by, zc, bar);
+                tma_load_3d(slot + OFF_CI, &M.tm_cI[in_buf], bx, by, zc, bar);
             }
+            tma_load_3d(ringD + d * PLANE, &M.tm_d, bx, by, zc, bar);
         };
 
         if (tid == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            for (int l = 0; l < PF && l < nit; ++l) issue(l);
+            for (int l = 0; l < PF && l < nit; ++l) issue(l, l);
         }
-
         int issued = min(PF, nit);
-        int waited = 0;   // loads consumed by this thread
+        int waited = 0;
+
         for (int it = 0; it < nit; ++it) {
             const int p = L0 + it;
-            if (__syncthreads_or(aborted ? 1 : 0)) {
-                aborted = true;
-                break;
-            }
-            if (tid == 0 && it + PF < nit) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(it + PF);
-            }
-            if (it + PF < nit) issued = it + PF + 1;
-            if (!mbar_wait_bounded(&bars[(gbase + it) % NB],
-                                   static_cast<uint32_t>(((gbase + it) / NB) & 1))) {
-                atomicOr(status, 1);
-                aborted = true;
-                continue;
-            }
-            waited = it + 1;
-
-            // stage 0: R of plane p enters the window of F_0
-            {
-                Real nr[VEC];
-                ld_vec<Real>(ringR + (it % C::NR) * PLANE + row * W + qx * VEC, nr);
-                const bool oob = !zper && (p < 0 || p >= nz);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    w[0][0][v] = w[0][1][v];
-                    w[0][1][v] = w[0][2][v];
-                    w[0][2][v] = oob ? Real(0) : nr[v];
+            if (tid == 0) {
+                if (mbar_wait_bounded(&bars[headB], phase)) {
+                    waited = it + 1;
+                } else {
+                    atomicOr(status, 1);
+                    s_abort = 1;
                 }
             }
+            __syncthreads();   // plane p has landed; the previous iteration's reads are done
+            if (s_abort) break;
+            if (it + PF < nit) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(it + PF, PF);
+                }
+                issued = it + PF + 1;
+            }
+            // ring slots of planes p, p-1, p-2 and of d at p-s
+            const Real *A0 = ringA + headA * SLOT;
+            const Real *A1 = ringA + (headA >= 1 ? headA - 1 : headA - 1 + NA) * SLOT;
+            const Real *A2 = ringA + (headA >= 2 ? headA - 2 : headA - 2 + NA) * SLOT;
+            const Real *sb_prev = sbuf + ((it - 1) & 1) * PLANE;   // + 2 (f) PLANE for F_{f+1}
+            Real *sb_cur = sbuf + (it & 1) * PLANE;
+            const bool p_out = !zper && (p < 0 || p >= nz);
 
+            Real zmR[RPT][VEC];   // R at plane p-2: stage 1's z- neighbour, stage 2's accumulator
 #pragma unroll
             for (int s = 1; s <= H; ++s) {
-                const int q = p - s;
                 if (it < 2 * s) continue;                                     // pipeline filling
                 if (warp_row0 + C::RW <= s || warp_row0 >= ROWS - s) continue;  // rows outside the cone
+                const int q = p - s;
                 const bool odd = (s & 1) != 0;
                 const bool q_out = !zper && (q < 0 || q >= nz);
-                const int qm = zper ? ((q % nz) + nz) % nz : q;
-                const Real mq = q_out ? Real(0) : maskz[qm];
+                int qm = q;                      // plane index inside [0, nz) (periodic z wraps)
+                if (zper) {
+                    qm = q % nz;
+                    if (qm < 0) qm += nz;
+                }
+                const bool absorb = !q_out && (qm < mlo || qm >= mhi);
+                const Real mq = absorb ? maskz[qm] : Real(1);
+                int dslot = headD - s;
+                if (dslot < 0) dslot += ND;
+                const Real *Dp = ringD + dslot * PLANE;
 
-                // stencil input F_{s-1}: center plane in shared memory for the y-neighbours
-                const Real *S = (s == 1) ? ringR + ((it - 1) % C::NR) * PLANE
-                                         : sbuf + ((s - 2) * 2 + ((it - 1) & 1)) * PLANE;
-                const int rm = row > 0 ? row - 1 : row;
-                const int rp = row < ROWS - 1 ? row + 1 : row;
-                Real ym[VEC], yp[VEC], dd[VEC];
-                ld_vec<Real>(S + rm * W + qx * VEC, ym);
-                ld_vec<Real>(S + rp * W + qx * VEC, yp);
-                ld_vec<Real>(ringD + ((it - s) % C::ND) * PLANE + row * W + qx * VEC, dd);
-                const Real xl = __shfl_up_sync(kFull, w[s - 1][1][VEC - 1], 1);
-                const Real xr = __shfl_down_sync(kFull, w[s - 1][1][0], 1);
-
-                // accumulator: the field of stage s-2 at plane q
-                Real acc[VEC], cacc[VEC];
+                Real zm[RPT][VEC], c[RPT][VEC], zp[RPT][VEC], ym[VEC], yp[VEC], dd[RPT][VEC];
                 if (s == 1) {
-                    ld_vec<Real>(ringI + ((it - 1) % C::NI) * PLANE + row * W + qx * VEC, acc);
-                    if (C::KAHAN)
-                        ld_vec<Real>(ringCI + ((it - 1) % C::NCIm) * PLANE + row * W + qx * VEC, cacc);
-                } else {
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        acc[v] = w[s - 2][0][v];
-                        cacc[v] = cw[s - 2][0][v];
-                    }
-                    if (s == 2 && C::KAHAN)
-                        ld_vec<Real>(ringCR + ((it - 2) % C::NCRm) * PLANE + row * W + qx * VEC, cacc);
-                    if (odd) {   // I of the previous step still carries its absorbing factor
+                    for (int r = 0; r < RPT; ++r) {
+                        ld_vec<Real>(A2 + own + r * W, zmR[r]);
+                        ld_vec<Real>(A1 + own + r * W, c[r]);
+                        ld_vec<Real>(A0 + own + r * W, zp[r]);
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
-                            acc[v] = mul_rn(acc[v], mq);
-                            cacc[v] = mul_rn(cacc[v], mq);
+                            zm[r][v] = zmR[r][v];
+                            if (p_out) zp[r][v] = Real(0);
+                        }
+                    }
+                    ld_vec<Real>(A1 + off_ym, ym);
+                    ld_vec<Real>(A1 + off_yp, yp);
+                } else {
+                    const Real *S = sb_prev + (s - 2) * 2 * PLANE;
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            zm[r][v] = w[s - 2][0][r][v];
+                            c[r][v] = w[s - 2][1][r][v];
+                            zp[r][v] = w[s - 2][2][r][v];
+                        }
+                    ld_vec<Real>(S + off_ym, ym);
+                    ld_vec<Real>(S + off_yp, yp);
+                }
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) ld_vec<Real>(Dp + own + r * W, dd[r]);
+
+                // accumulator: the field two stages back at plane q
+                Real acc[RPT][VEC], cacc[RPT][VEC];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    if (s == 1) {
+                        ld_vec<Real>(A1 + OFF_I + own + r * W, acc[r]);
+                        if constexpr (C::KAHAN) ld_vec<Real>(A1 + OFF_CI + own + r * W, cacc[r]);
+                    } else if (s == 2) {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[r][v] = zmR[r][v];
+                        if constexpr (C::KAHAN) ld_vec<Real>(A2 + OFF_CR + own + r * W, cacc[r]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            acc[r][v] = w[s - 3][0][r][v];
+                            if constexpr (C::KAHAN) cacc[r][v] = cw[s - 3][0][r][v];
                         }
                     }
                 }
-
-                Real out[VEC], cout[VEC];
+                if (s >= 3 && odd && absorb) {   // I of the previous step carries its absorbing factor
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    const Real c0 = w[s - 1][1][v];
-                    const Real sx = (v == 0 ? xl : w[s - 1][1][v - 1]) +
-                                    (v == VEC - 1 ? xr : w[s - 1][1][v + 1]);
-                    const Real sy = ym[v] + yp[v];
-                    const Real sz = w[s - 1][0][v] + w[s - 1][2][v];
-                    const Real delta = fma(cx, sx, fma(cy, sy, fma(cz, sz, dd[v] * c0)));
-                    const Real inc = odd ? delta : -delta;
-                    if (C::KAHAN) {
-                        const Real y = inc - cacc[v];
-                        const Real t = acc[v] + y;
-                        cout[v] = (t - acc[v]) - y;
-                        out[v] = t;
-                    } else {
-                        out[v] = acc[v] + inc;
-                        cout[v] = Real(0);
-                    }
-                    if (!odd) {          // Eq. 8 step complete: absorbing factor on R
-                        out[v] = mul_rn(out[v], mq);
-                        cout[v] = mul_rn(cout[v], mq);
-                    }
-                    if (walls) {
-                        out[v] *= keep[v];
-                        cout[v] *= keep[v];
-                    }
-                    if (q_out) {
-                        out[v] = Real(0);
-                        cout[v] = Real(0);
-                    }
+                    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            acc[r][v] = mul_rn(acc[r][v], mq);
+                            if constexpr (C::KAHAN) cacc[r][v] = mul_rn(cacc[r][v], mq);
+                        }
                 }
 
-                // detector flux of step (s+1)/2: R at planes kd, kd+1 and the new I
-                if (odd && flux_owner && q == kd + 1 && store_cell) {
-                    const int pix = ys * nx + xs;
+                Real out[RPT][VEC], cout[RPT][VEC];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const Real xl = __shfl_up_sync(kFull, c[r][VEC - 1], 1);
+                    const Real xr = __shfl_down_sync(kFull, c[r][0], 1);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
-                        const double j = M.cj * (static_cast<double>(w[s - 1][0][v]) * out[v] -
-                                                 static_cast<double>(w[s - 1][1][v]) * w[s][2][v]);
-                        M.flux[pix + v] += j * M.dt;
-                        if (s == H - 1) M.jlast[pix + v] = j;
+                        const Real sx = (v == 0 ? xl : c[r][v - 1]) + (v == VEC - 1 ? xr : c[r][v + 1]);
+                        const Real sy = (r == 0 ? ym[v] : c[r - 1][v]) + (r == RPT - 1 ? yp[v] : c[r + 1][v]);
+                        const Real sz = zm[r][v] + zp[r][v];
+                        if constexpr (CHAIN) {
+                            const Real sg = odd ? Real(1) : Real(-1);
+                            out[r][v] = fma(sg * cx, sx, fma(sg * cy, sy,
+                                            fma(sg * cz, sz, fma(sg * dd[r][v], c[r][v], acc[r][v]))));
+                        } else {
+                            const Real delta = fma(cx, sx, fma(cy, sy, fma(cz, sz, dd[r][v] * c[r][v])));
+                            const Real inc = odd ? delta : -delta;
+                            if constexpr (C::KAHAN) {
+                                const Real y = inc - cacc[r][v];
+                                const Real t = acc[r][v] + y;
+                                cout[r][v] = (t - acc[r][v]) - y;
+                                out[r][v] = t;
+                            } else {
+                                out[r][v] = acc[r][v] + inc;
+                            }
+                        }
+                    }
+                }
+                if (!odd && absorb) {   // Eq. 8 step complete: absorbing factor on R
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            out[r][v] = mul_rn(out[r][v], mq);
+                            if constexpr (C::KAHAN) cout[r][v] = mul_rn(cout[r][v], mq);
+                        }
+                }
+                if (walls || q_out) {
+                    const Real zq = q_out ? Real(0) : Real(1);
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            out[r][v] *= keep[r][v] * zq;
+                            if constexpr (C::KAHAN) cout[r][v] *= keep[r][v] * zq;
+                        }
+                }
+
+                // detector flux of step (s+1)/2: R^n at planes kd, kd+1 and the new I
+                if (odd && flux_owner && q == kd + 1 && any_store) {
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        if (!store_row[r]) continue;
+                        const int pix = (ys0 + r) * nx + xs;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            // I at plane kd is the previous output of stage s
+                            const Real ilo = s < H ? w[s - 1][2][r][v] : Real(0);
+                            const double j = M.cj * (static_cast<double>(zm[r][v]) * out[r][v] -
+                                                     static_cast<double>(c[r][v]) * ilo);
+                            M.flux[pix + v] += j * M.dt;
+                            if (s == H - 1) M.jlast[pix + v] = j;
+                        }
                     }
                 }
 
                 if (s < H) {
+                    Real *So = sb_cur + (s - 1) * 2 * PLANE;
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        w[s][0][v] = w[s][1][v];
-                        w[s][1][v] = w[s][2][v];
-                        w[s][2][v] = out[v];
-                        cw[s][0][v] = cw[s][1][v];
-                        cw[s][1][v] = cw[s][2][v];
-                        cw[s][2][v] = cout[v];
-                    }
-                    st_vec<Real>(sbuf + ((s - 1) * 2 + (it & 1)) * PLANE + row * W + qx * VEC, out);
-                } else if (store_cell && q >= kz0 && q < kz1) {
-                    Real vi[VEC], vci[VEC];
+                    for (int r = 0; r < RPT; ++r) {
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        vi[v] = mul_rn(w[H - 1][1][v], mq);
-                        vci[v] = mul_rn(cw[H - 1][1][v], mq);
-                    }
-                    // primary location plus the ghost copies of periodic axes
-                    int xo[2] = {xs, xs};
-                    int yo[2] = {ys, ys};
-                    int nxo = 1, nyo = 1;
-                    if (M.per_x) {
-                        if (xs < G) xo[nxo++] = xs + nx;
-                        else if (xs >= nx - G) xo[nxo++] = xs - nx;
-                    }
-                    if (M.per_y) {
-                        if (ys < G) yo[nyo++] = ys + ny;
-                        else if (ys >= ny - G) yo[nyo++] = ys - ny;
-                    }
-                    const long long zoff = static_cast<long long>(q) * M.plane;
-                    for (int a = 0; a < nyo; ++a)
-                        for (int b = 0; b < nxo; ++b) {
-                            const long long o = zoff + static_cast<long long>(yo[a] + G) * M.pitch + (xo[b] + G);
-                            st_vec<Real>(outR + o, out);
-                            st_vec<Real>(outI + o, vi);
-                            if (C::KAHAN) {
-                                st_vec<Real>(outCR + o, cout);
-                                st_vec<Real>(outCI + o, vci);
+                        for (int v = 0; v < VEC; ++v) {
+                            w[s - 1][0][r][v] = w[s - 1][1][r][v];
+                            w[s - 1][1][r][v] = w[s - 1][2][r][v];
+                            w[s - 1][2][r][v] = out[r][v];
+                            if constexpr (C::KAHAN) {
+                                cw[s - 1][0][r][v] = cw[s - 1][1][r][v];
+                                cw[s - 1][1][r][v] = cw[s - 1][2][r][v];
+                                cw[s - 1][2][r][v] = cout[r][v];
                             }
                         }
+                        if (r == 0 || r == RPT - 1) st_vec<Real>(So + own + r * W, out[r]);
+                    }
+                } else if (any_store && q >= kz0 && q < kz1) {
+                    const long long zoff = static_cast<long long>(q) * M.plane;
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        if (!store_row[r]) continue;
+                        Real vi[VEC], vci[VEC];
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            vi[v] = absorb ? mul_rn(w[H - 2][1][r][v], mq) : w[H - 2][1][r][v];
+                            if constexpr (C::KAHAN)
+                                vci[v] = absorb ? mul_rn(cw[H - 2][1][r][v], mq) : cw[H - 2][1][r][v];
+                        }
+                        const long long o = zoff + out0 + r * pitch;
+                        st_vec<Real>(outR + o, out[r]);
+                        st_vec<Real>(outI + o, vi);
+                        if constexpr (C::KAHAN) {
+                            st_vec<Real>(outCR + o, cout[r]);
+                            st_vec<Real>(outCI + o, vci);
+                        }
+                        if (seam) {   // ghost copies of periodic axes
+                            const int y = ys0 + r;
+                            const int gx = !M.per_x ? 0 : (xs < G ? nx : (xs >= nx - G ? -nx : 0));
+                            const int gy = !M.per_y ? 0 : (y < G ? ny : (y >= ny - G ? -ny : 0));
+                            for (int k = 1; k < 4; ++k) {
+                                const int dx = (k & 1) ? gx : 0, dy = (k & 2) ? gy : 0;
+                                if ((k & 1 && !gx) || (k & 2 && !gy)) continue;
+                                const long long og = o + dy * pitch + dx;
+                                st_vec<Real>(outR + og, out[r]);
+                                st_vec<Real>(outI + og, vi);
+                                if constexpr (C::KAHAN) {
+                                    st_vec<Real>(outCR + og, cout[r]);
+                                    st_vec<Real>(outCI + og, vci);
+                                }
+                            }
+                        }
+                    }
                 }
             }
+            headA = headA + 1 == NA ? 0 : headA + 1;
+            headD = headD + 1 == ND ? 0 : headD + 1;
+            headB = headB + 1 == NB ? 0 : headB + 1;
+            if (headB == 0) phase ^= 1u;
         }
 
-        if (__syncthreads_or(aborted ? 1 : 0)) {
+        if (s_abort) {
             // wait (bounded) for the loads still in flight, then leave
             if (tid == 0) {
-                for (int l = waited; l < issued; ++l)
-                    mbar_wait_bounded(&bars[(gbase + l) % NB],
-                                      static_cast<uint32_t>(((gbase + l) / NB) & 1));
+                for (int l = waited; l < issued; ++l) {
+                    const long long g = gbase + l;
+                    mbar_wait_bounded(&bars[g % NB], static_cast<uint32_t>((g / NB) & 1));
+                }
             }
             __syncthreads();
             return;
@@ -490,36 +594,75 @@ void fill_config(StepConfig *cfg)
     cfg->box_y = C::ROWS;
     cfg->threads = C::NT;
     cfg->smem = C::SMEM;
-    cfg->ctas_per_sm = 1;
+    cfg->ctas_per_sm = C::MINB;
 }
 
-// The kernel configurations of the library.
-typedef Cfg<float, 2, 16, 32, false, 2> F32T1;
-typedef Cfg<float, 2, 16, 32, true, 2> K32T1;
-typedef Cfg<float, 4, 16, 32, false, 2> F32T2;
-typedef Cfg<float, 4, 16, 28, true, 2> K32T2;
-typedef Cfg<double, 2, 32, 24, false, 1> F64T1;
+struct Variant {
+    int precision, tsteps;
+    const char *name;
+    void (*fill)(StepConfig *);
+    cudaError_t (*launch)(const StepLaunch &);
+};
+
+#define TDSE_VARIANT(P, T, NAME, ...)                                                      \
+    Variant{P, T, NAME, &fill_config<Cfg<__VA_ARGS__>>, &launch_cfg<Cfg<__VA_ARGS__>>}
+
+// Kernel variants per (precision, fused steps); the first of each pair is the default.
+// Cfg<Real, 2T, threads per row, rows, Kahan, planes prefetched>
+// Measured on GB300 (512x512x1024 slab): the first entry of each (precision, steps)
+// group is the fastest and the default; the others remain for the autotuner.
+const Variant kVariants[] = {
+    TDSE_VARIANT(1, 1, "f32_t1_w64_r24x2_pf2_b2", float, 2, 16, 24, 2, false, 2, 2),
+    TDSE_VARIANT(1, 1, "f32_t1_w64_r32x2_pf1_b2", float, 2, 16, 32, 2, false, 1, 2),
+    TDSE_VARIANT(1, 1, "f32_t1_w64_r48x2_pf2", float, 2, 16, 48, 2, false, 2),
+    TDSE_VARIANT(1, 1, "f32_t1_w128_r24x2_pf2", float, 2, 32, 24, 2, false, 2),
+    TDSE_VARIANT(1, 1, "f32_t1_w64_r32x2_pf2", float, 2, 16, 32, 2, false, 2),
+    TDSE_VARIANT(1, 2, "f32_t2_w64_r32x1_pf2", float, 4, 16, 32, 1, false, 2),
+    TDSE_VARIANT(1, 2, "f32_t2_w64_r32x2_pf2", float, 4, 16, 32, 2, false, 2),
+    TDSE_VARIANT(2, 1, "k32_t1_w64_r32x1_pf2", float, 2, 16, 32, 1, true, 2),
+    TDSE_VARIANT(2, 1, "k32_t1_w64_r32x2_pf2", float, 2, 16, 32, 2, true, 2),
+    TDSE_VARIANT(2, 2, "k32_t2_w64_r28x2_pf1", float, 4, 16, 28, 2, true, 1),
+    TDSE_VARIANT(2, 2, "k32_t2_w64_r24x2_pf2", float, 4, 16, 24, 2, true, 2),
+    TDSE_VARIANT(0, 1, "f64_t1_w64_r16x2_pf1_b2", double, 2, 32, 16, 2, false, 1, 2),
+    TDSE_VARIANT(0, 1, "f64_t1_w64_r32x2_pf1", double, 2, 32, 32, 2, false, 1),
+    TDSE_VARIANT(0, 1, "f64_t1_w64_r16x1_pf2", double, 2, 32, 16, 1, false, 2),
+};
+
+const Variant *find_variant(int precision, int tsteps, int variant)
+{
+    int k = 0;
+    for (const Variant &v : kVariants)
+        if (v.precision == precision && v.tsteps == tsteps && k++ == variant) return &v;
+    return nullptr;
+}
 
 }  // namespace
 
-bool step_config(int precision, int tsteps, StepConfig *cfg)
+int step_variant_count(int precision, int tsteps)
 {
-    if (precision == 0 && tsteps == 1) { fill_config<F64T1>(cfg); return true; }
-    if (precision == 1 && tsteps == 1) { fill_config<F32T1>(cfg); return true; }
-    if (precision == 1 && tsteps == 2) { fill_config<F32T2>(cfg); return true; }
-    if (precision == 2 && tsteps == 1) { fill_config<K32T1>(cfg); return true; }
-    if (precision == 2 && tsteps == 2) { fill_config<K32T2>(cfg); return true; }
-    return false;
+    int k = 0;
+    for (const Variant &v : kVariants) k += (v.precision == precision && v.tsteps == tsteps);
+    return k;
 }
 
-cudaError_t launch_step(int precision, int tsteps, const StepLaunch &L)
+const char *step_variant_name(int precision, int tsteps, int variant)
 {
-    if (precision == 0 && tsteps == 1) return launch_cfg<F64T1>(L);
-    if (precision == 1 && tsteps == 1) return launch_cfg<F32T1>(L);
-    if (precision == 1 && tsteps == 2) return launch_cfg<F32T2>(L);
-    if (precision == 2 && tsteps == 1) return launch_cfg<K32T1>(L);
-    if (precision == 2 && tsteps == 2) return launch_cfg<K32T2>(L);
-    return cudaErrorInvalidValue;
+    const Variant *v = find_variant(precision, tsteps, variant);
+    return v ? v->name : nullptr;
+}
+
+bool step_config(int precision, int tsteps, int variant, StepConfig *cfg)
+{
+    const Variant *v = find_variant(precision, tsteps, variant);
+    if (!v) return false;
+    v->fill(cfg);
+    return true;
+}
+
+cudaError_t launch_step(int precision, int tsteps, int variant, const StepLaunch &L)
+{
+    const Variant *v = find_variant(precision, tsteps, variant);
+    return v ? v->launch(L) : cudaErrorInvalidValue;
 }
 
 }  // namespace tdse

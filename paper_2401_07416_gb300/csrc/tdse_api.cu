@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -34,6 +35,7 @@ struct Member {
 
 struct StepPlan {
     int tsteps = 0;
+    int variant = 0;
     StepConfig cfg{};
     MemberDev *d_members = nullptr; // members with tensor maps for this config's box
     WorkDev *d_work = nullptr;
@@ -225,7 +227,11 @@ tdse_status build_plans(tdse_ctx *c)
         if (T != 1 && T != c->tblock) continue;
         StepPlan &pl = c->plans[T];
         pl.tsteps = T;
-        if (!step_config(c->precision, T, &pl.cfg))
+        pl.variant = 0;
+        char env[64];
+        snprintf(env, sizeof env, "TDSE_STEP_VARIANT_P%d_T%d", c->precision, T);
+        if (const char *v = getenv(env)) pl.variant = atoi(v);
+        if (!step_config(c->precision, T, pl.variant, &pl.cfg))
             return fail(c, TDSE_EINVAL, "no kernel for precision %d with %d fused steps", c->precision, T);
         std::vector<MemberDev> hm(B);
         WorkDev w{};
@@ -451,7 +457,7 @@ tdse_status launch_fused(tdse_ctx *c, int T)
     CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream));
     int t0;
     TRY(timer_start(c, &t0));
-    CUDA_TRY(c, launch_step(c->precision, T, L));
+    CUDA_TRY(c, launch_step(c->precision, T, pl.variant, L));
     TRY(timer_stop(c, t0, 0));
     if (c->profiling) {
         long long cells = 0;
@@ -570,6 +576,8 @@ tdse_status tdse_create(const tdse_params *p, int batch, tdse_ctx **out)
         d.per_y = q.bc[1] == TDSE_BC_PERIODIC;
         d.per_z = q.bc[2] == TDSE_BC_PERIODIC;
         d.det_k = q.det_k;
+        d.mask_lo = q.mask_lo;
+        d.mask_hi = q.mask_hi;
         d.cx = q.hbar * q.dt / (2.0 * q.mass * q.hx * q.hx);
         d.cy = q.hbar * q.dt / (2.0 * q.mass * q.hy * q.hy);
         d.cz = q.hbar * q.dt / (2.0 * q.mass * q.hz * q.hz);

@@ -37,6 +37,7 @@ struct alignas(128) MemberDev {
     long long plane;       // elements per padded plane = pitch * prow
     int nx, ny, nz, G, pitch, prow;
     int per_x, per_y, per_z, det_k;
+    int mask_lo, mask_hi;     // absorbing planes at the z ends
     double cx, cy, cz, cv, cj, dt;
     double hx, hy, hz, hbar;
 };
@@ -73,9 +74,12 @@ struct StepConfig {
     int ctas_per_sm;
 };
 
-// step_kernels.cu
-bool step_config(int precision, int tsteps, StepConfig *cfg);
-cudaError_t launch_step(int precision, int tsteps, const StepLaunch &L);
+// step_kernels.cu: kernel variants (tile shape, prefetch depth) per precision
+// and number of fused steps; variant 0 is the default.
+int step_variant_count(int precision, int tsteps);
+const char *step_variant_name(int precision, int tsteps, int variant);
+bool step_config(int precision, int tsteps, int variant, StepConfig *cfg);
+cudaError_t launch_step(int precision, int tsteps, int variant, const StepLaunch &L);
 
 // aux_kernels.cu
 cudaError_t launch_fill_ghosts(const MemberDev &m, void *field, int elem, cudaStream_t s);
