@@ -206,6 +206,28 @@ TDSE_API tdse_status tdse_get_profile(tdse_ctx *ctx, tdse_profile *out);
 /* Description of the last error on this context (static storage, never NULL). */
 TDSE_API const char *tdse_last_error(const tdse_ctx *ctx);
 
+/* Q, paper norm and energy (out[0..2], as in tdse_obs) of an FP64 state
+ * R = psi_R^n, I = psi_I^{n-1/2} and potential V (each [nz][ny][nx], device memory;
+ * V may be NULL for V = 0) on the grid described by *p (spacings, dt, hbar, mass,
+ * boundaries; precision, absorbing layers and detector are ignored), without
+ * allocating any device memory.  The paper has no counterpart: this exists for
+ * callers that cannot allocate, such as a host program whose device memory is
+ * owned by another allocator (a framework pool or a fixed arena it must not
+ * bypass), or code where a cudaMalloc would implicitly synchronise the device.
+ * The reduction's scratch is a static device array of 8193 x 4 doubles
+ * (256 KiB) that every GPU loading this library keeps until the process exits;
+ * the first call on a device looks up its address, so make that first call
+ * before any stream capture.  Each call overwrites the nz per-plane sums it
+ * reads and the result slot, so nothing has to be cleared between calls, but
+ * calls on the same device share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race.  Work runs on `stream` (a
+ * cudaStream_t; NULL: legacy default stream), which is synchronised before the
+ * host results are written to out.  EINVAL: NULL pointer, bad spacing, or nz
+ * above 8192 (one scratch slot per z plane); ECUDA: a CUDA call failed. */
+TDSE_API tdse_status tdse_observables_static(const tdse_params *p, const double *R,
+                                             const double *I, const double *V, double out[3],
+                                             void *stream);
+
 /* Library version string. */
 TDSE_API const char *tdse_version(void);
 

@@ -84,6 +84,7 @@ SIGNATURES = {
     "tdse_load_state": (_I, [_VP, ctypes.c_char_p]),
     "tdse_set_profiling": (_I, [_VP, _I]),
     "tdse_get_profile": (_I, [_VP, ctypes.POINTER(Profile)]),
+    "tdse_observables_static": (_I, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP]),
     "tdse_last_error": (ctypes.c_char_p, [_VP]),
     "tdse_version": (ctypes.c_char_p, []),
     "tdse_destroy": (_I, [_VP]),
@@ -265,6 +266,23 @@ def tdse_get_profile(ctx) -> dict:
     p = Profile()
     _check(ctx, lib().tdse_get_profile(ctx, ctypes.byref(p)))
     return {k: getattr(p, k) for k, _ in p._fields_ if k != "reserved"}
+
+
+def tdse_observables_static(params: Params, R, I, V=None, stream_ptr: int = 0) -> dict:
+    """Q, paper norm and energy of a device-resident FP64 state, computed without
+    any device allocation (for callers that cannot allocate)."""
+    pr, dr, _ = _arg(R)
+    pi, di, _ = _arg(I)
+    pv, dv, _ = _arg(V)
+    if not (dr and di and (V is None or dv)):
+        raise TypeError("R, I and V must be CUDA tensors")
+    out = np.zeros(3)
+    st = lib().tdse_observables_static(ctypes.byref(params), pr, pi, pv,
+                                       out.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.c_void_p(stream_ptr))
+    if st != OK:
+        raise TdseError(st, "tdse_observables_static failed (nz > 8192, bad geometry or CUDA error)")
+    return {"Q": out[0], "norm_paper": out[1], "energy": out[2]}
 
 
 def tdse_last_error(ctx) -> str:
