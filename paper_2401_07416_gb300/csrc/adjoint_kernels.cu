@@ -1,0 +1,371 @@
+// Reverse-time kernels of the adjoint (gradient of a loss of the time-integrated
+// detector flux) and the chain rule from dL/dV to the atom parameters.
+//
+// Forward step n -> n+1 (Sec. 2.1, Eqs. 8-9, with the absorbing factor M and the
+// detector flux j): It = I + A R; j = cj (R_kd It_kd+1 - R_kd+1 It_kd);
+// Rt = R - A It; R' = M Rt; I' = M It.  A is symmetric, so one backward step,
+// with (P, Q) the adjoints of (R', I') and w = dL/dF * dt * cj per pixel, is
+//   a. It = I'/M, Rt = R'/M, Pt = M P                         (pointwise)
+//   b. R = Rt + A It,  Qt = M Q - A Pt                        (undo Eq. 8; adjoint of Eq. 8)
+//   c. Qt[kd+1] += w R[kd],  Qt[kd] -= w R[kd+1]              (flux w.r.t. It)
+//   d. gV -= cv (Qt R - Pt It);  P = Pt + A Qt + dj/dR        (adjoint of Eq. 9, V terms)
+//   e. I = It - A R,  Q = Qt                                  (undo Eq. 9)
+// after which (R, I) = (R^n, I^{n-1/2}) and (P, Q) their adjoints.  Arrays are
+// unpadded [nz][ny][nx]; neighbours wrap on periodic axes and read zero on walls.
+#include <cmath>
+
+#include "tdse_internal.cuh"
+
+namespace tdse {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Geo {
+    int nx, ny, nz;
+    int per[3];
+    double cx, cy, cz, cv, c0;   // c0 = -2 (cx + cy + cz)
+};
+
+__device__ __forceinline__ long long cell(const Geo &g, int x, int y, int z)
+{
+    return (static_cast<long long>(z) * g.ny + y) * g.nx + x;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real nb(const Real *f, const Geo &g, int x, int y, int z)
+{
+    if (x < 0 || x >= g.nx) {
+        if (!g.per[0]) return Real(0);
+        x = (x % g.nx + g.nx) % g.nx;
+    }
+    if (y < 0 || y >= g.ny) {
+        if (!g.per[1]) return Real(0);
+        y = (y % g.ny + g.ny) % g.ny;
+    }
+    if (z < 0 || z >= g.nz) {
+        if (!g.per[2]) return Real(0);
+        z = (z % g.nz + g.nz) % g.nz;
+    }
+    return f[cell(g, x, y, z)];
+}
+
+// (A f)(x, y, z) with d = -2 (cx + cy + cz) - cv V rounded to Real like the forward step.
+template <typename Real>
+__device__ __forceinline__ Real apply_A(const Real *f, const double *V, const Geo &g, int x, int y,
+                                        int z, long long o)
+{
+    const Real d = static_cast<Real>(g.c0 - g.cv * V[o]);
+    const Real sx = nb(f, g, x + 1, y, z) + nb(f, g, x - 1, y, z);
+    const Real sy = nb(f, g, x, y + 1, z) + nb(f, g, x, y - 1, z);
+    const Real sz = nb(f, g, x, y, z + 1) + nb(f, g, x, y, z - 1);
+    return fma(static_cast<Real>(g.cx), sx,
+               fma(static_cast<Real>(g.cy), sy, fma(static_cast<Real>(g.cz), sz, d * f[o])));
+}
+
+#define GRID_STRIDE(t, n)                                                                     \
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < (n); \
+         t += static_cast<long long>(gridDim.x) * blockDim.x)
+
+template <typename Real>
+__global__ void adj_unmask_kernel(Geo g, const double *__restrict__ M, Real *R, Real *I, Real *P)
+{
+    const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+    const long long plane = static_cast<long long>(g.nx) * g.ny;
+    GRID_STRIDE(t, n)
+    {
+        const double m = M[t / plane];
+        if (m != 1.0) {
+            R[t] = static_cast<Real>(R[t] / m);
+            I[t] = static_cast<Real>(I[t] / m);
+            P[t] = static_cast<Real>(P[t] * m);
+        }
+    }
+}
+
+template <typename Real>
+__global__ void adj_b_kernel(Geo g, const double *__restrict__ M, const double *__restrict__ V,
+                             Real *R, const Real *__restrict__ I, const Real *__restrict__ P, Real *Q)
+{
+    const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+    GRID_STRIDE(t, n)
+    {
+        const int x = static_cast<int>(t % g.nx);
+        const int y = static_cast<int>((t / g.nx) % g.ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(g.nx) * g.ny));
+        R[t] = R[t] + apply_A(I, V, g, x, y, z, t);
+        Q[t] = static_cast<Real>(M[z] * Q[t]) - apply_A(P, V, g, x, y, z, t);
+    }
+}
+
+template <typename Real>
+__global__ void adj_flux_q_kernel(Geo g, int kd, const double *__restrict__ w, const Real *R, Real *Q)
+{
+    const long long plane = static_cast<long long>(g.nx) * g.ny;
+    GRID_STRIDE(p, plane)
+    {
+        const Real wp = static_cast<Real>(w[p]);
+        Q[(kd + 1) * plane + p] += wp * R[kd * plane + p];
+        Q[kd * plane + p] -= wp * R[(kd + 1) * plane + p];
+    }
+}
+
+template <typename Real>
+__global__ void adj_d_kernel(Geo g, const double *__restrict__ V, int kd,
+                             const double *__restrict__ w, const Real *__restrict__ R,
+                             const Real *__restrict__ I, Real *P, const Real *__restrict__ Q,
+                             double *gV)
+{
+    const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+    const long long plane = static_cast<long long>(g.nx) * g.ny;
+    GRID_STRIDE(t, n)
+    {
+        const int x = static_cast<int>(t % g.nx);
+        const int y = static_cast<int>((t / g.nx) % g.ny);
+        const int z = static_cast<int>(t / plane);
+        const Real pt = P[t];
+        gV[t] -= g.cv * (static_cast<double>(Q[t]) * R[t] - static_cast<double>(pt) * I[t]);
+        Real pn = pt + apply_A(Q, V, g, x, y, z, t);
+        if (kd >= 0) {
+            const long long p = t % plane;
+            if (z == kd) pn += static_cast<Real>(w[p]) * I[t + plane];
+            else if (z == kd + 1) pn -= static_cast<Real>(w[p]) * I[t - plane];
+        }
+        P[t] = pn;
+    }
+}
+
+template <typename Real>
+__global__ void adj_e_kernel(Geo g, const double *__restrict__ V, const Real *__restrict__ R, Real *I)
+{
+    const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+    GRID_STRIDE(t, n)
+    {
+        const int x = static_cast<int>(t % g.nx);
+        const int y = static_cast<int>((t / g.nx) % g.ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(g.nx) * g.ny));
+        I[t] = I[t] - apply_A(R, V, g, x, y, z, t);
+    }
+}
+
+// I^{-1/2} = Im psi0 - A R^0 / 2 makes L depend on V through the start: gV += (cv/2) Q R^0.
+template <typename Real>
+__global__ void adj_start_kernel(Geo g, const double *__restrict__ R0, const Real *__restrict__ Q,
+                                 double *gV)
+{
+    const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+    GRID_STRIDE(t, n) gV[t] += 0.5 * g.cv * static_cast<double>(Q[t]) * R0[t];
+}
+
+template <typename Real>
+__global__ void convert_kernel(long long n, const double *__restrict__ src, Real *dst)
+{
+    GRID_STRIDE(t, n) dst[t] = static_cast<Real>(src[t]);
+}
+
+// w = dL/dF * dt * cj per pixel
+__global__ void flux_weight_kernel(long long npix, const double *__restrict__ gF, double scale,
+                                   double *w)
+{
+    GRID_STRIDE(t, npix) w[t] = gF[t] * scale;
+}
+
+// ---------------------------------------------------------------- atom chain rule
+
+// d phi / d(r^2) of the atom profile (see the potential kernel).
+__device__ __forceinline__ void atom_profile(double r2, double a2, double rc, double *phi,
+                                             double *dphi)
+{
+    const double rho = sqrt(r2 + a2);
+    const double ir = 1.0 / rho, ir3 = ir * ir * ir;
+    if (rc <= 0.0) {
+        *phi = ir;
+        *dphi = -0.5 * ir3;
+        return;
+    }
+    const double uc = rc * rc;
+    if (r2 >= uc) {
+        *phi = 0.0;
+        *dphi = 0.0;
+        return;
+    }
+    const double ic = 1.0 / sqrt(uc + a2), ic3 = ic * ic * ic, ic5 = ic3 * ic * ic;
+    const double du = r2 - uc;
+    *phi = ir - (ic - 0.5 * du * ic3 + 0.375 * du * du * ic5);
+    *dphi = -0.5 * ir3 - (-0.5 * ic3 + 0.75 * du * ic5);
+}
+
+struct AtomGeo {
+    int nx, ny, nz;
+    int per[3];
+    double h[3], L[3];
+    double a2, rc;
+};
+
+__device__ __forceinline__ double mimg(double d, double L, int per)
+{
+    return per ? d - L * floor(d / L + 0.5) : d;
+}
+
+// block (a, c): atom a, cells c, c + nchunk, ...; partial[(a * nchunk + c) * 4 + k]
+__global__ void atom_grad_kernel(AtomGeo g, const double *__restrict__ atoms,
+                                 const double *__restrict__ gV, int nchunk, double *partial)
+{
+    __shared__ double sh[4][kThreads / 32];
+    const int a = blockIdx.x / nchunk, c = blockIdx.x % nchunk;
+    const double ax = atoms[4 * a], ay = atoms[4 * a + 1], az = atoms[4 * a + 2], Z = atoms[4 * a + 3];
+    const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+    double acc[4] = {0, 0, 0, 0};
+    for (long long t = static_cast<long long>(c) * blockDim.x + threadIdx.x; t < n;
+         t += static_cast<long long>(nchunk) * blockDim.x) {
+        const int x = static_cast<int>(t % g.nx);
+        const int y = static_cast<int>((t / g.nx) % g.ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(g.nx) * g.ny));
+        const double dx = mimg(x * g.h[0] - ax, g.L[0], g.per[0]);
+        const double dy = mimg(y * g.h[1] - ay, g.L[1], g.per[1]);
+        const double dz = mimg(z * g.h[2] - az, g.L[2], g.per[2]);
+        double phi, dphi;
+        atom_profile(dx * dx + dy * dy + dz * dz, g.a2, g.rc, &phi, &dphi);
+        const double wv = gV[t];
+        // V_a = -Z phi(r^2), d(r^2)/d(x_a) = -2 (x - x_a)
+        acc[0] += wv * 2.0 * Z * dphi * dx;
+        acc[1] += wv * 2.0 * Z * dphi * dy;
+        acc[2] += wv * 2.0 * Z * dphi * dz;
+        acc[3] += wv * (-phi);
+    }
+    for (int k = 0; k < 4; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += sh[threadIdx.x][w];
+        partial[(static_cast<long long>(a) * nchunk + c) * 4 + threadIdx.x] = s;
+    }
+}
+
+__global__ void atom_grad_finalize(int natoms, int nchunk, const double *__restrict__ partial,
+                                   double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= natoms * 4) return;
+    const int a = i / 4, k = i % 4;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += partial[(static_cast<long long>(a) * nchunk + c) * 4 + k];
+    out[i] = s;
+}
+
+int grid_for(long long n)
+{
+    long long g = (n + kThreads - 1) / kThreads;
+    if (g > 152LL * 64) g = 152LL * 64;
+    return static_cast<int>(g < 1 ? 1 : g);
+}
+
+Geo make_geo(const MemberDev &m)
+{
+    Geo g;
+    g.nx = m.nx;
+    g.ny = m.ny;
+    g.nz = m.nz;
+    g.per[0] = m.per_x;
+    g.per[1] = m.per_y;
+    g.per[2] = m.per_z;
+    g.cx = m.cx;
+    g.cy = m.cy;
+    g.cz = m.cz;
+    g.cv = m.cv;
+    g.c0 = -2.0 * (m.cx + m.cy + m.cz);
+    return g;
+}
+
+template <typename Real>
+cudaError_t backward_step_t(const MemberDev &m, const AdjointBuffers &b, cudaStream_t s)
+{
+    const Geo g = make_geo(m);
+    const long long n = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const long long plane = static_cast<long long>(m.nx) * m.ny;
+    const int grid = grid_for(n);
+    Real *R = static_cast<Real *>(b.R), *I = static_cast<Real *>(b.I);
+    Real *P = static_cast<Real *>(b.P), *Q = static_cast<Real *>(b.Q);
+    adj_unmask_kernel<Real><<<grid, kThreads, 0, s>>>(g, b.M, R, I, P);
+    adj_b_kernel<Real><<<grid, kThreads, 0, s>>>(g, b.M, b.V, R, I, P, Q);
+    const int kd = m.det_k;
+    if (kd >= 0) adj_flux_q_kernel<Real><<<grid_for(plane), kThreads, 0, s>>>(g, kd, b.w, R, Q);
+    adj_d_kernel<Real><<<grid, kThreads, 0, s>>>(g, b.V, kd, b.w, R, I, P, Q, b.gV);
+    adj_e_kernel<Real><<<grid, kThreads, 0, s>>>(g, b.V, R, I);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t adjoint_backward_step(const MemberDev &m, int elem, const AdjointBuffers &b,
+                                  cudaStream_t s)
+{
+    return elem == 8 ? backward_step_t<double>(m, b, s) : backward_step_t<float>(m, b, s);
+}
+
+cudaError_t adjoint_start_term(const MemberDev &m, int elem, const AdjointBuffers &b,
+                               const double *R0, cudaStream_t s)
+{
+    const Geo g = make_geo(m);
+    const long long n = static_cast<long long>(m.nx) * m.ny * m.nz;
+    if (elem == 8)
+        adj_start_kernel<double><<<grid_for(n), kThreads, 0, s>>>(g, R0, static_cast<double *>(b.Q), b.gV);
+    else
+        adj_start_kernel<float><<<grid_for(n), kThreads, 0, s>>>(g, R0, static_cast<float *>(b.Q), b.gV);
+    return cudaGetLastError();
+}
+
+cudaError_t adjoint_load_state(const MemberDev &m, int elem, const AdjointBuffers &b,
+                               const double *R64, const double *I64, cudaStream_t s)
+{
+    const long long n = static_cast<long long>(m.nx) * m.ny * m.nz;
+    if (elem == 8) {
+        cudaMemcpyAsync(b.R, R64, n * 8, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(b.I, I64, n * 8, cudaMemcpyDeviceToDevice, s);
+    } else {
+        convert_kernel<float><<<grid_for(n), kThreads, 0, s>>>(n, R64, static_cast<float *>(b.R));
+        convert_kernel<float><<<grid_for(n), kThreads, 0, s>>>(n, I64, static_cast<float *>(b.I));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t adjoint_flux_weights(const MemberDev &m, const double *gF, double *w, cudaStream_t s)
+{
+    const long long npix = static_cast<long long>(m.nx) * m.ny;
+    flux_weight_kernel<<<grid_for(npix), kThreads, 0, s>>>(npix, gF, m.dt * m.cj, w);
+    return cudaGetLastError();
+}
+
+int atom_grad_chunks() { return 256; }
+
+cudaError_t launch_atom_gradient(const MemberDev &m, const double *atoms, int natoms, double a2,
+                                 double rc, const double *gV, double *partial, double *out,
+                                 cudaStream_t s)
+{
+    if (natoms <= 0) return cudaSuccess;
+    AtomGeo g;
+    g.nx = m.nx;
+    g.ny = m.ny;
+    g.nz = m.nz;
+    g.per[0] = m.per_x;
+    g.per[1] = m.per_y;
+    g.per[2] = m.per_z;
+    g.h[0] = m.hx;
+    g.h[1] = m.hy;
+    g.h[2] = m.hz;
+    g.L[0] = m.nx * m.hx;
+    g.L[1] = m.ny * m.hy;
+    g.L[2] = m.nz * m.hz;
+    g.a2 = a2;
+    g.rc = rc;
+    const int nchunk = atom_grad_chunks();
+    atom_grad_kernel<<<natoms * nchunk, kThreads, 0, s>>>(g, atoms, gV, nchunk, partial);
+    atom_grad_finalize<<<(natoms * 4 + 127) / 128, 128, 0, s>>>(natoms, nchunk, partial, out);
+    return cudaGetLastError();
+}
+
+}  // namespace tdse

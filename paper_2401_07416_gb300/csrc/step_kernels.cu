@@ -528,21 +528,29 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                             st_vec<Real>(outCR + o, cout[r]);
                             st_vec<Real>(outCI + o, vci);
                         }
-                        if (seam) {   // ghost copies of periodic axes
+                        if (seam) {   // ghost copies of periodic axes (both sides if n < 2G)
                             const int y = ys0 + r;
-                            const int gx = !M.per_x ? 0 : (xs < G ? nx : (xs >= nx - G ? -nx : 0));
-                            const int gy = !M.per_y ? 0 : (y < G ? ny : (y >= ny - G ? -ny : 0));
-                            for (int k = 1; k < 4; ++k) {
-                                const int dx = (k & 1) ? gx : 0, dy = (k & 2) ? gy : 0;
-                                if ((k & 1 && !gx) || (k & 2 && !gy)) continue;
-                                const long long og = o + dy * pitch + dx;
-                                st_vec<Real>(outR + og, out[r]);
-                                st_vec<Real>(outI + og, vi);
-                                if constexpr (C::KAHAN) {
-                                    st_vec<Real>(outCR + og, cout[r]);
-                                    st_vec<Real>(outCI + og, vci);
-                                }
+                            int dxs[3] = {0, 0, 0}, dys[3] = {0, 0, 0};
+                            int ndx = 1, ndy = 1;
+                            if (M.per_x) {
+                                if (xs < G) dxs[ndx++] = nx;
+                                if (xs >= nx - G) dxs[ndx++] = -nx;
                             }
+                            if (M.per_y) {
+                                if (y < G) dys[ndy++] = ny;
+                                if (y >= ny - G) dys[ndy++] = -ny;
+                            }
+                            for (int a = 0; a < ndy; ++a)
+                                for (int b = 0; b < ndx; ++b) {
+                                    if (a == 0 && b == 0) continue;
+                                    const long long og = o + dys[a] * pitch + dxs[b];
+                                    st_vec<Real>(outR + og, out[r]);
+                                    st_vec<Real>(outI + og, vi);
+                                    if constexpr (C::KAHAN) {
+                                        st_vec<Real>(outCR + og, cout[r]);
+                                        st_vec<Real>(outCI + og, vci);
+                                    }
+                                }
                         }
                     }
                 }

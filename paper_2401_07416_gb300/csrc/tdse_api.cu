@@ -31,6 +31,9 @@ struct Member {
     double soft_a2 = 0.25, r_cut = 0.0;
     double q0 = 0.0;                // Q at the last set_wavepacket / set_state
     std::vector<double> hist;       // 4 per record: step, Q, norm_paper, energy
+    double *mask64 = nullptr;       // absorbing factor per plane, FP64 (adjoint)
+    bool from_packet = false;       // the run started with tdse_set_wavepacket
+    std::vector<std::pair<long long, double *>> ckpts;   // (step, FP64 R then I)
 };
 
 struct StepPlan {
@@ -322,6 +325,9 @@ tdse_status ensure_device(tdse_ctx *c)
                 M[k] = s * s;
             }
         }
+        TRY(dalloc(c, d.nz * sizeof(double), &p)); mb.mask64 = static_cast<double *>(p);
+        CUDA_TRY(c, cudaMemcpyAsync(mb.mask64, M.data(), d.nz * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream));
         TRY(dalloc(c, d.nz * es, &p)); d.mask = p;
         std::vector<float> Mf(M.begin(), M.end());
         CUDA_TRY(c, cudaMemcpyAsync(d.mask, es == 8 ? static_cast<const void *>(M.data()) : Mf.data(),
@@ -479,6 +485,24 @@ tdse_status observe_all(tdse_ctx *c, int slot)
     return TDSE_OK;
 }
 
+void clear_checkpoints(tdse_ctx *c, Member &mb)
+{
+    for (auto &ck : mb.ckpts) dfree(c, ck.second);
+    mb.ckpts.clear();
+}
+
+// FP64 copy of member i's state at the current step (value - compensation in Kahan mode).
+tdse_status save_checkpoint(tdse_ctx *c, Member &mb)
+{
+    const size_t cells = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz;
+    void *p = nullptr;
+    TRY(dalloc(c, 2 * cells * sizeof(double), &p));
+    double *buf = static_cast<double *>(p);
+    CUDA_TRY(c, launch_get_state(mb.dev, buf, buf + cells, c->precision, c->cur, c->stream));
+    mb.ckpts.push_back({c->step, buf});
+    return TDSE_OK;
+}
+
 // Observation of member i right now (synchronous) into rec[kRecLen].
 tdse_status current_obs(tdse_ctx *c, int i, double *rec)
 {
@@ -497,6 +521,8 @@ tdse_status reset_run(tdse_ctx *c, int i)
     CUDA_TRY(c, cudaMemsetAsync(mb.dev.jlast, 0, pix, c->stream));
     mb.hist.clear();
     mb.have_state = true;
+    clear_checkpoints(c, mb);
+    if (c->ckpt_every > 0) TRY(save_checkpoint(c, mb));
     double rec[kRecLen];
     TRY(current_obs(c, i, rec));
     mb.q0 = rec[1];
@@ -698,6 +724,7 @@ tdse_status tdse_set_wavepacket(tdse_ctx *c, int member, const double r0[3], con
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     dfree(c, R);
     dfree(c, I);
+    mb.from_packet = true;
     return reset_run(c, member);
 }
 
@@ -724,6 +751,7 @@ tdse_status tdse_set_state(tdse_ctx *c, int member, const double *R, const doubl
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     dfree(c, tR);
     dfree(c, tI);
+    mb.from_packet = false;
     return reset_run(c, member);
 }
 
@@ -737,8 +765,8 @@ tdse_status tdse_step(tdse_ctx *c, long long nsteps)
     int nrec = 0;
     long long left = nsteps;
     while (left > 0) {
-        const long long to_obs = c->obs_every - (c->step % c->obs_every);
-        long long seg = std::min(left, to_obs);
+        long long seg = std::min(left, c->obs_every - (c->step % c->obs_every));
+        if (c->ckpt_every > 0) seg = std::min(seg, c->ckpt_every - (c->step % c->ckpt_every));
         while (seg > 0) {
             const int T = (seg >= c->tblock) ? c->tblock : 1;
             TRY(launch_fused(c, T));
@@ -752,6 +780,8 @@ tdse_status tdse_step(tdse_ctx *c, long long nsteps)
                 nrec = 0;
             }
         }
+        if (c->ckpt_every > 0 && c->step % c->ckpt_every == 0)
+            for (Member &mb : c->m) TRY(save_checkpoint(c, mb));
     }
     TRY(drain_records(c, nrec));
     TRY(check_status(c));
@@ -836,10 +866,86 @@ tdse_status tdse_get_potential(tdse_ctx *c, int member, double *V, int on_device
     return TDSE_OK;
 }
 
-tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *, double *, double *, int)
+tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *dL_dV,
+                         double *dL_datoms, int on_device)
 {
     TRY(check_member(c, member));
-    return fail(c, TDSE_ESTATE, "adjoint not available in this build");
+    if (!dL_dF) return fail(c, TDSE_EINVAL, "dL_dF is NULL");
+    Member &mb = c->m[member];
+    if (!mb.have_state) return fail(c, TDSE_ESTATE, "member has no state");
+    if (c->ckpt_every <= 0 || mb.ckpts.empty())
+        return fail(c, TDSE_ESTATE, "no checkpoints: create the context with ckpt_every > 0");
+    if (dL_datoms && mb.atoms.empty())
+        return fail(c, TDSE_ESTATE, "dL_datoms requested but the potential did not come from atoms");
+    const MemberDev &d = mb.dev;
+    const size_t cells = static_cast<size_t>(d.nx) * d.ny * d.nz;
+    const size_t npix = static_cast<size_t>(d.nx) * d.ny;
+    const int elem = c->precision == TDSE_FP64 ? 8 : 4;
+    std::vector<void *> tmp;
+    auto alloc = [&](size_t bytes, void **p) -> tdse_status {
+        tdse_status st = dalloc(c, bytes, p);
+        if (st == TDSE_OK) tmp.push_back(*p);
+        return st;
+    };
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(c->stream);
+        for (void *p : tmp) dfree(c, p);
+    };
+    void *R, *I, *P, *Q, *gV, *w, *gF, *cur;
+    tdse_status st = TDSE_OK;
+    if ((st = alloc(cells * elem, &R)) || (st = alloc(cells * elem, &I)) ||
+        (st = alloc(cells * elem, &P)) || (st = alloc(cells * elem, &Q)) ||
+        (st = alloc(cells * 8, &gV)) || (st = alloc(npix * 8, &w)) || (st = alloc(npix * 8, &gF)) ||
+        (st = alloc(2 * cells * 8, &cur))) {
+        cleanup();
+        return st;
+    }
+    AdjointBuffers b{R, I, P, Q, static_cast<double *>(gV), static_cast<double *>(w), mb.mask64,
+                     mb.V64};
+    auto run = [&]() -> tdse_status {
+        CUDA_TRY(c, cudaMemcpyAsync(gF, dL_dF, npix * 8,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    c->stream));
+        CUDA_TRY(c, adjoint_flux_weights(d, static_cast<double *>(gF), b.w, c->stream));
+        // start from the latest state, then walk the checkpoints backwards
+        double *cur64 = static_cast<double *>(cur);
+        CUDA_TRY(c, launch_get_state(d, cur64, cur64 + cells, c->precision, c->cur, c->stream));
+        CUDA_TRY(c, adjoint_load_state(d, elem, b, cur64, cur64 + cells, c->stream));
+        long long n = c->step;
+        for (int k = static_cast<int>(mb.ckpts.size()) - 1; k >= 0; --k) {
+            const long long n0 = mb.ckpts[k].first;
+            for (; n > n0; --n) CUDA_TRY(c, adjoint_backward_step(d, elem, b, c->stream));
+            // re-anchor the reconstructed forward state on the FP64 checkpoint
+            const double *ck = mb.ckpts[k].second;
+            CUDA_TRY(c, adjoint_load_state(d, elem, b, ck, ck + cells, c->stream));
+        }
+        if (mb.from_packet)
+            CUDA_TRY(c, adjoint_start_term(d, elem, b, mb.ckpts[0].second, c->stream));
+        if (dL_dV)
+            CUDA_TRY(c, cudaMemcpyAsync(dL_dV, gV, cells * 8,
+                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                        c->stream));
+        if (dL_datoms) {
+            const int na = static_cast<int>(mb.atoms.size() / 4);
+            void *A, *part, *outA;
+            TRY(alloc(mb.atoms.size() * 8, &A));
+            TRY(alloc(static_cast<size_t>(na) * atom_grad_chunks() * 4 * 8, &part));
+            TRY(alloc(mb.atoms.size() * 8, &outA));
+            CUDA_TRY(c, cudaMemcpyAsync(A, mb.atoms.data(), mb.atoms.size() * 8,
+                                        cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(c, launch_atom_gradient(d, static_cast<double *>(A), na, mb.soft_a2, mb.r_cut,
+                                             static_cast<double *>(gV), static_cast<double *>(part),
+                                             static_cast<double *>(outA), c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(dL_datoms, outA, mb.atoms.size() * 8,
+                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                        c->stream));
+        }
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        return TDSE_OK;
+    };
+    st = run();
+    cleanup();
+    return st;
 }
 
 tdse_status tdse_save_state(tdse_ctx *c, const char *path)

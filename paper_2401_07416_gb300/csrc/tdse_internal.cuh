@@ -106,4 +106,26 @@ cudaError_t launch_observables(const MemberDev &m, int precision, int buf, doubl
                                cudaStream_t s);
 constexpr int kObsParts = 1216;     // fixed block count: the reduction order never changes
 
+// adjoint_kernels.cu: working arrays of one backward sweep (unpadded, Real of the
+// context for R, I, P, Q; FP64 for the rest).
+struct AdjointBuffers {
+    void *R, *I;          // forward state being reconstructed: R^n, I^{n-1/2}
+    void *P, *Q;          // their adjoints
+    double *gV;           // dL/dV accumulator
+    double *w;            // dL/dF * dt * cj per detector pixel
+    const double *M;      // absorbing factor per plane (FP64)
+    const double *V;      // potential (FP64)
+};
+cudaError_t adjoint_backward_step(const MemberDev &m, int elem, const AdjointBuffers &b,
+                                  cudaStream_t s);
+cudaError_t adjoint_start_term(const MemberDev &m, int elem, const AdjointBuffers &b,
+                               const double *R0, cudaStream_t s);
+cudaError_t adjoint_load_state(const MemberDev &m, int elem, const AdjointBuffers &b,
+                               const double *R64, const double *I64, cudaStream_t s);
+cudaError_t adjoint_flux_weights(const MemberDev &m, const double *gF, double *w, cudaStream_t s);
+int atom_grad_chunks();
+cudaError_t launch_atom_gradient(const MemberDev &m, const double *atoms, int natoms, double a2,
+                                 double rc, const double *gV, double *partial, double *out,
+                                 cudaStream_t s);
+
 }  // namespace tdse

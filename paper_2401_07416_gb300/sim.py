@@ -100,3 +100,59 @@ class Sim:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def flux_from_atoms(atoms, sim: "Sim", member: int, packet: W.Packet, nsteps: int,
+                    soft_a2: float = 0.25, r_cut: float = 0.0):
+    """Differentiable map atoms [n, 4] (x, y, z, Z) -> time-integrated detector flux
+    F [ny, nx].  forward builds V from the atoms, sets the packet and runs `nsteps`
+    (every member of `sim` advances: use a one-member Sim); backward calls
+    tdse_adjoint.  `sim` must have been created with ckpt_every > 0."""
+    torch = _torch()
+
+    class Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, a):
+            sim.set_atoms(member, a.detach().cpu().double().numpy(), soft_a2, r_cut)
+            sim.set_packet(member, packet)
+            sim.step(nsteps)
+            return torch.from_numpy(sim.flux_map(member)).to(a.device)
+
+        @staticmethod
+        def backward(ctx, gF):
+            g = np.zeros(tuple(atoms.shape))
+            T.tdse_adjoint(sim.ctx, member, gF.detach().cpu().double().numpy(), None, g)
+            return torch.from_numpy(g).to(gF.device)
+
+    return Fn.apply(atoms)
+
+
+def flux_from_potential(V, sim: "Sim", member: int, packet: W.Packet, nsteps: int):
+    """Differentiable map V [nz, ny, nx] -> F [ny, nx] (same contract as flux_from_atoms)."""
+    torch = _torch()
+
+    class Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, v):
+            sim.set_potential(member, v.detach().double().contiguous())
+            sim.set_packet(member, packet)
+            sim.step(nsteps)
+            return torch.from_numpy(sim.flux_map(member)).to(v.device)
+
+        @staticmethod
+        def backward(ctx, gF):
+            g = np.zeros(tuple(V.shape))
+            T.tdse_adjoint(sim.ctx, member, gF.detach().cpu().double().numpy(), g, None)
+            return torch.from_numpy(g).to(gF.device)
+
+    return Fn.apply(V)
+
+
+def diffraction_loss(F, F_target):
+    """L = sum over detector pixels of (F - F*)^2 (no area weight)."""
+    return ((F - F_target) ** 2).sum()

@@ -54,6 +54,8 @@ CASES = {
     "slab": (132, 44, 50, (0, 0, 1), 6, 20),
     "periodic": (24, 24, 30, (0, 0, 0), 0, 5),
     "mixed": (36, 28, 33, (0, 1, 0), 4, 9),
+    # periodic axes shorter than twice the ghost width: both ghost zones are copies
+    "short": (12, 9, 26, (0, 0, 1), 3, 8),
 }
 
 
