@@ -178,7 +178,7 @@ def oracle_sample_state():
     wl, sub, z0 = cpu_sample_workload()
     g = wl.grid
     origin = (0.0, 0.0, z0 * g.hz)
-    period = g.lengths
+    period = [l if b == W.PERIODIC else 0.0 for l, b in zip(g.lengths, g.bc)]
     V = oracle.potential_atoms_window(sub, origin, period, wl.atoms, rc=0.5 * min(period[:2]))
     R0, I0 = oracle.wavepacket_window(sub, origin, wl.packet.r0, wl.packet.sigma, wl.packet.k0)
     return sub, V, R0, oracle.init_half(sub, V, R0, I0)

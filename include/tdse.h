@@ -203,6 +203,27 @@ typedef struct tdse_profile {
 TDSE_API tdse_status tdse_set_profiling(tdse_ctx *ctx, int enable);
 TDSE_API tdse_status tdse_get_profile(tdse_ctx *ctx, tdse_profile *out);
 
+/* Kernel variants and fused depth.  The fused step exists in several variants
+ * (tile shape, planes loaded ahead, CTAs per SM) for each precision and number
+ * of steps per launch (1 or 2; FP64 fuses 1).  tdse_autotune times every variant
+ * on this context's own grids (`launches` launches each, after one warm-up),
+ * keeps the fastest for each depth and, if the context was created with
+ * tblock = 0, the depth with the lower time per step.  The state, flux integral
+ * and step counter are saved before and restored after the trials.  Step
+ * sequences between two reductions are replayed from captured CUDA graphs
+ * unless profiling is on or tdse_set_graphs(ctx, 0) was called. */
+typedef struct tdse_tuning {
+    int tblock;                 /* steps fused per launch in use */
+    int variant[3];             /* variant index for 1 and 2 fused steps (index 0 unused) */
+    double ms_per_step[3];      /* measured by tdse_autotune, 0 if not measured */
+    char name[3][48];           /* variant names */
+} tdse_tuning;
+TDSE_API int tdse_variant_count(int precision, int tsteps);
+TDSE_API tdse_status tdse_set_variant(tdse_ctx *ctx, int tsteps, int variant);
+TDSE_API tdse_status tdse_autotune(tdse_ctx *ctx, int launches);
+TDSE_API tdse_status tdse_get_tuning(tdse_ctx *ctx, tdse_tuning *out);
+TDSE_API tdse_status tdse_set_graphs(tdse_ctx *ctx, int enable);
+
 /* Description of the last error on this context (static storage, never NULL). */
 TDSE_API const char *tdse_last_error(const tdse_ctx *ctx);
 

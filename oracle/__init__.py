@@ -141,7 +141,8 @@ def potential_atoms(g, atoms, a2=0.25, rc=None) -> np.ndarray:
 
 def potential_atoms_window(g, origin, period, atoms, a2=0.25, rc=0.0) -> np.ndarray:
     """Potential on the window grid g whose node (0,0,0) sits at `origin` of a larger
-    grid with periods `period` (rc must be given: the larger grid's cut-off)."""
+    grid; period[a] > 0 gives the larger grid's period along a (minimum image),
+    period[a] <= 0 no images.  rc must be given: the larger grid's cut-off."""
     atoms = _f64(atoms)
     V = np.empty(shape(g))
     lib().orc_potential_atoms_at(ctypes.byref(_grid(g)), _ptr(_f64(origin)), _ptr(_f64(period)),

@@ -44,6 +44,25 @@ typedef struct {
 
 static size_t ncells(const orc_grid *g) { return (size_t)g->nx * g->ny * g->nz; }
 
+/* Neumaier's compensated sum: sums over millions of nodes must stay accurate far
+ * below the 1e-11 parity bound, which a plain running sum (error up to N eps / 2)
+ * does not. */
+typedef struct {
+    double s, c;
+} csum;
+
+static void cadd(csum *a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x))
+        a->c += (a->s - t) + x;
+    else
+        a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static double cval(const csum *a) { return a->s + a->c; }
+
 static size_t at3(const orc_grid *g, int i, int j, int k)
 {
     return ((size_t)k * g->ny + j) * g->nx + i;
@@ -171,9 +190,10 @@ static void profile(double r2, double a2, double rc, double *phi, double *dphi_d
 }
 
 /* V(r) = sum over atoms of -Z phi(|r - r_a|) at the nodes r = origin + (i hx, j hy, k hz)
- * of grid g, with minimum-image distances of period `period[a]` along periodic
- * axes.  atoms: [n][4] rows (x, y, z, Z).  With origin 0 and period n h this is
- * the potential of the whole grid; other values evaluate a window of a larger grid. */
+ * of grid g, with minimum-image distances along every axis whose period[a] is
+ * positive (period[a] <= 0: no periodic images).  atoms: [n][4] rows (x, y, z, Z).
+ * With origin 0 and period n h on the periodic axes of g this is the potential of
+ * the whole grid; other values evaluate a window of a larger grid. */
 void orc_potential_atoms_at(const orc_grid *g, const double origin[3], const double period[3],
                             int n, const double *atoms, double a2, double rc, double *V)
 {
@@ -186,7 +206,7 @@ void orc_potential_atoms_at(const orc_grid *g, const double origin[3], const dou
                 for (int a = 0; a < n; ++a) {
                     double r2 = 0.0;
                     for (int ax = 0; ax < 3; ++ax) {
-                        double d = min_image(r[ax] - atoms[4 * a + ax], period[ax], g->bc[ax] == 0);
+                        double d = min_image(r[ax] - atoms[4 * a + ax], period[ax], period[ax] > 0.0);
                         r2 += d * d;
                     }
                     double phi, dphi;
@@ -201,7 +221,9 @@ void orc_potential_atoms(const orc_grid *g, int n, const double *atoms, double a
                          double *V)
 {
     const double origin[3] = {0.0, 0.0, 0.0};
-    const double period[3] = {g->nx * g->hx, g->ny * g->hy, g->nz * g->hz};
+    const double period[3] = {g->bc[0] == 0 ? g->nx * g->hx : 0.0,
+                              g->bc[1] == 0 ? g->ny * g->hy : 0.0,
+                              g->bc[2] == 0 ? g->nz * g->hz : 0.0};
     orc_potential_atoms_at(g, origin, period, n, atoms, a2, rc, V);
 }
 
@@ -247,7 +269,7 @@ void orc_atom_gradient(const orc_grid *g, int n, const double *atoms, double a2,
 void orc_wavepacket_at(const orc_grid *g, const double origin[3], const double r0[3],
                        const double sigma[3], const double k0[3], double *R, double *I)
 {
-    double sum = 0.0;
+    csum sum = {0.0, 0.0};
     for (int k = 0; k < g->nz; ++k)
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i < g->nx; ++i) {
@@ -261,9 +283,9 @@ void orc_wavepacket_at(const orc_grid *g, const double origin[3], const double r
                 size_t c = at3(g, i, j, k);
                 R[c] = amp * cos(phase);
                 I[c] = amp * sin(phase);
-                sum += R[c] * R[c] + I[c] * I[c];
+                cadd(&sum, R[c] * R[c] + I[c] * I[c]);
             }
-    double s = 1.0 / sqrt(sum * g->hx * g->hy * g->hz);
+    double s = 1.0 / sqrt(cval(&sum) * g->hx * g->hy * g->hz);
     for (size_t c = 0; c < ncells(g); ++c) {
         R[c] *= s;
         I[c] *= s;
@@ -368,7 +390,8 @@ void orc_observables(const orc_grid *g, const double *V, const double *R, const 
     double *AI = (double *)malloc(n * sizeof(double));
     orc_apply_A(g, V, R, AR);
     orc_apply_A(g, V, I, AI);
-    double q = 0.0, pn = 0.0, e = 0.0, mom[6] = {0, 0, 0, 0, 0, 0};
+    csum q = {0, 0}, pn = {0, 0}, e = {0, 0}, mom[6];
+    for (int m = 0; m < 6; ++m) mom[m] = (csum){0, 0};
     for (int k = 0; k < g->nz; ++k)
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i < g->nx; ++i) {
@@ -376,21 +399,21 @@ void orc_observables(const orc_grid *g, const double *V, const double *R, const 
                 double Ip = I[c] + AR[c];
                 double rho = R[c] * R[c] + Ip * I[c];
                 double x = i * g->hx, y = j * g->hy, z = k * g->hz;
-                q += rho;
-                pn += R[c] * R[c] + I[c] * I[c];
-                e += -(g->hbar / g->dt) * (R[c] * AR[c] + Ip * AI[c]);
-                mom[0] += rho * x;
-                mom[1] += rho * y;
-                mom[2] += rho * z;
-                mom[3] += rho * x * x;
-                mom[4] += rho * y * y;
-                mom[5] += rho * z * z;
+                cadd(&q, rho);
+                cadd(&pn, R[c] * R[c] + I[c] * I[c]);
+                cadd(&e, -(g->hbar / g->dt) * (R[c] * AR[c] + Ip * AI[c]));
+                cadd(&mom[0], rho * x);
+                cadd(&mom[1], rho * y);
+                cadd(&mom[2], rho * z);
+                cadd(&mom[3], rho * x * x);
+                cadd(&mom[4], rho * y * y);
+                cadd(&mom[5], rho * z * z);
             }
     double h3 = g->hx * g->hy * g->hz;
-    out[0] = q * h3;
-    out[1] = pn * h3;
-    out[2] = e / q;
-    for (int m = 0; m < 6; ++m) out[3 + m] = mom[m] * h3;
+    out[0] = cval(&q) * h3;
+    out[1] = cval(&pn) * h3;
+    out[2] = cval(&e) / cval(&q);
+    for (int m = 0; m < 6; ++m) out[3 + m] = cval(&mom[m]) * h3;
     free(AR);
     free(AI);
 }

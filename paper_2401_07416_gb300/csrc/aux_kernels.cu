@@ -83,11 +83,6 @@ __device__ __forceinline__ double atom_phi(double r2, double a2, double rc)
     return 1.0 / rho - (ic - 0.5 * du * ic3 + 0.375 * du * du * ic5);
 }
 
-__device__ __forceinline__ double min_image(double d, double L, int periodic)
-{
-    return periodic ? d - L * floor(d / L + 0.5) : d;
-}
-
 __global__ void potential_kernel(MemberDev m, const double *__restrict__ atoms, int n,
                                  double a2, double rc, double *__restrict__ V)
 {
@@ -98,7 +93,10 @@ __global__ void potential_kernel(MemberDev m, const double *__restrict__ atoms, 
     const int y = static_cast<int>((t / m.nx) % m.ny);
     const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
     const double L[3] = {m.nx * m.hx, m.ny * m.hy, m.nz * m.hz};
+    const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
+    const int per[3] = {m.per_x, m.per_y, m.per_z};
     const double r[3] = {x * m.hx, y * m.hy, z * m.hz};
+    const double rc2 = rc > 0.0 ? rc * rc : 1e300;
     double v = 0.0;
     for (int a0 = 0; a0 < n; a0 += 256) {
         const int na = min(256, n - a0);
@@ -107,10 +105,14 @@ __global__ void potential_kernel(MemberDev m, const double *__restrict__ atoms, 
         __syncthreads();
         if (t < cells) {
             for (int a = 0; a < na; ++a) {
-                const double dx = min_image(r[0] - sa[4 * a + 0], L[0], m.per_x);
-                const double dy = min_image(r[1] - sa[4 * a + 1], L[1], m.per_y);
-                const double dz = min_image(r[2] - sa[4 * a + 2], L[2], m.per_z);
-                const double r2 = dx * dx + dy * dy + dz * dz;
+                double r2 = 0.0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    double d = r[k] - sa[4 * a + k];
+                    if (per[k]) d -= L[k] * floor(d * iL[k] + 0.5);   // nearest periodic image
+                    r2 += d * d;
+                }
+                if (r2 >= rc2) continue;   // beyond the cut-off the profile is zero
                 v -= sa[4 * a + 3] * atom_phi(r2, a2, rc);
             }
         }

@@ -50,6 +50,7 @@ struct StepPlan {
 struct tdse_ctx {
     std::vector<Member> m;
     int precision = 0, tblock = 1, obs_every = 20, ckpt_every = 0;
+    bool tblock_auto = false;       // created with tblock = 0: tdse_autotune may change it
     tdse_alloc_fn alloc_fn = nullptr;
     tdse_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
@@ -71,6 +72,15 @@ struct tdse_ctx {
     std::vector<std::pair<int, int>> pending;      // (start, stop) indices into event_pool
     std::vector<int> pending_kind;                 // 0: step launch, 1: reductions
     size_t events_used = 0;
+    bool graphs = true;                            // replay step segments as CUDA graphs
+    cudaStream_t gstream = nullptr;                // capture/replay stream
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    struct GraphEntry {
+        int nsteps, parity, tblock;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graph_cache;
+    double tuned_ms_per_step[kMaxTblock + 1] = {0, 0, 0};
     std::string err;
 };
 
@@ -223,67 +233,80 @@ int choose_chunk(const std::vector<int> &tiles, const std::vector<int> &nz, int 
     return bestL;
 }
 
-tdse_status build_plans(tdse_ctx *c)
+void drop_graphs(tdse_ctx *c)
+{
+    for (auto &g : c->graph_cache) cudaGraphExecDestroy(g.exec);
+    c->graph_cache.clear();
+}
+
+// Build (or rebuild) the launch plan of the fused step with T steps per launch
+// and the given kernel variant: tensor maps with the variant's box, the work list.
+tdse_status build_plan(tdse_ctx *c, int T, int variant)
 {
     const int B = static_cast<int>(c->m.size());
-    for (int T = 1; T <= c->tblock; ++T) {
-        if (T != 1 && T != c->tblock) continue;
-        StepPlan &pl = c->plans[T];
-        pl.tsteps = T;
-        pl.variant = 0;
-        char env[64];
-        snprintf(env, sizeof env, "TDSE_STEP_VARIANT_P%d_T%d", c->precision, T);
-        if (const char *v = getenv(env)) pl.variant = atoi(v);
-        if (!step_config(c->precision, T, pl.variant, &pl.cfg))
-            return fail(c, TDSE_EINVAL, "no kernel for precision %d with %d fused steps", c->precision, T);
-        std::vector<MemberDev> hm(B);
-        WorkDev w{};
-        w.nmembers = B;
-        std::vector<int> tiles(B), nzs(B);
-        for (int i = 0; i < B; ++i) {
-            const Member &mb = c->m[i];
-            hm[i] = mb.dev;
-            MemberDev &d = hm[i];
-            for (int b = 0; b < 2; ++b) {
-                TRY(encode_map(c, &d.tm_R[b], mb, d.R[b], pl.cfg.box_x, pl.cfg.box_y));
-                TRY(encode_map(c, &d.tm_I[b], mb, d.I[b], pl.cfg.box_x, pl.cfg.box_y));
-                if (c->precision == TDSE_FP32_KAHAN) {
-                    TRY(encode_map(c, &d.tm_cR[b], mb, d.cR[b], pl.cfg.box_x, pl.cfg.box_y));
-                    TRY(encode_map(c, &d.tm_cI[b], mb, d.cI[b], pl.cfg.box_x, pl.cfg.box_y));
-                }
+    StepPlan &pl = c->plans[T];
+    StepConfig cfg;
+    if (!step_config(c->precision, T, variant, &cfg))
+        return fail(c, TDSE_EINVAL, "no kernel variant %d for precision %d with %d fused steps",
+                    variant, c->precision, T);
+    std::vector<MemberDev> hm(B);
+    WorkDev w{};
+    w.nmembers = B;
+    std::vector<int> tiles(B), nzs(B);
+    for (int i = 0; i < B; ++i) {
+        const Member &mb = c->m[i];
+        hm[i] = mb.dev;
+        MemberDev &d = hm[i];
+        for (int b = 0; b < 2; ++b) {
+            TRY(encode_map(c, &d.tm_R[b], mb, d.R[b], cfg.box_x, cfg.box_y));
+            TRY(encode_map(c, &d.tm_I[b], mb, d.I[b], cfg.box_x, cfg.box_y));
+            if (c->precision == TDSE_FP32_KAHAN) {
+                TRY(encode_map(c, &d.tm_cR[b], mb, d.cR[b], cfg.box_x, cfg.box_y));
+                TRY(encode_map(c, &d.tm_cI[b], mb, d.cI[b], cfg.box_x, cfg.box_y));
             }
-            TRY(encode_map(c, &d.tm_d, mb, d.d, pl.cfg.box_x, pl.cfg.box_y));
-            w.tiles_x[i] = (d.nx + pl.cfg.tile_x - 1) / pl.cfg.tile_x;
-            w.tiles_y[i] = (d.ny + pl.cfg.tile_y - 1) / pl.cfg.tile_y;
-            tiles[i] = w.tiles_x[i] * w.tiles_y[i];
-            nzs[i] = d.nz;
         }
-        int occ = 1;
-        c->sms = 0;
-        int dev = 0;
-        CUDA_TRY(c, cudaGetDevice(&dev));
-        CUDA_TRY(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
-        occ = std::max(1, pl.cfg.ctas_per_sm);
-        const int P = c->sms * occ;
-        const int L = choose_chunk(tiles, nzs, T, P);
-        int total = 0;
-        for (int i = 0; i < B; ++i) {
-            w.item_begin[i] = total;
-            w.chunk[i] = std::min(L, nzs[i]);
-            total += tiles[i] * ((nzs[i] + w.chunk[i] - 1) / w.chunk[i]);
-        }
-        w.item_begin[B] = total;
-        w.total = total;
-        pl.grid = std::min(total, P);
+        TRY(encode_map(c, &d.tm_d, mb, d.d, cfg.box_x, cfg.box_y));
+        w.tiles_x[i] = (d.nx + cfg.tile_x - 1) / cfg.tile_x;
+        w.tiles_y[i] = (d.ny + cfg.tile_y - 1) / cfg.tile_y;
+        tiles[i] = w.tiles_x[i] * w.tiles_y[i];
+        nzs[i] = d.nz;
+    }
+    int dev = 0;
+    CUDA_TRY(c, cudaGetDevice(&dev));
+    CUDA_TRY(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+    const int P = c->sms * std::max(1, cfg.ctas_per_sm);
+    const int L = choose_chunk(tiles, nzs, T, P);
+    int total = 0;
+    for (int i = 0; i < B; ++i) {
+        w.item_begin[i] = total;
+        w.chunk[i] = std::min(L, nzs[i]);
+        total += tiles[i] * ((nzs[i] + w.chunk[i] - 1) / w.chunk[i]);
+    }
+    w.item_begin[B] = total;
+    w.total = total;
+    if (!pl.d_members) {
         void *p = nullptr;
         TRY(dalloc(c, sizeof(MemberDev) * B, &p));
         pl.d_members = static_cast<MemberDev *>(p);
         TRY(dalloc(c, sizeof(WorkDev), &p));
         pl.d_work = static_cast<WorkDev *>(p);
-        CUDA_TRY(c, cudaMemcpyAsync(pl.d_members, hm.data(), sizeof(MemberDev) * B,
-                                    cudaMemcpyHostToDevice, c->stream));
-        CUDA_TRY(c, cudaMemcpyAsync(pl.d_work, &w, sizeof(WorkDev), cudaMemcpyHostToDevice, c->stream));
     }
+    CUDA_TRY(c, cudaMemcpyAsync(pl.d_members, hm.data(), sizeof(MemberDev) * B,
+                                cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(pl.d_work, &w, sizeof(WorkDev), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    pl.tsteps = T;
+    pl.variant = variant;
+    pl.cfg = cfg;
+    pl.grid = std::min(total, P);
+    drop_graphs(c);
+    return TDSE_OK;
+}
+
+tdse_status build_plans(tdse_ctx *c)
+{
+    TRY(build_plan(c, 1, 0));
+    if (c->precision != TDSE_FP64) TRY(build_plan(c, 2, 0));
     return TDSE_OK;
 }
 
@@ -476,6 +499,66 @@ tdse_status launch_fused(tdse_ctx *c, int T)
     return TDSE_OK;
 }
 
+// Issue the fused launches of `nsteps` steps (no observation in between).
+tdse_status issue_segment(tdse_ctx *c, long long nsteps)
+{
+    while (nsteps > 0) {
+        const int T = (nsteps >= c->tblock) ? c->tblock : 1;
+        TRY(launch_fused(c, T));
+        nsteps -= T;
+    }
+    return TDSE_OK;
+}
+
+// Same launches, replayed from a captured CUDA graph keyed by (steps, ping-pong
+// parity, fused depth).  Captured on a private stream that is ordered after and
+// before the context's stream with events.
+tdse_status run_segment(tdse_ctx *c, long long nsteps)
+{
+    if (!c->graphs || c->profiling || nsteps <= 0) return issue_segment(c, nsteps);
+    if (!c->gstream) {
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming));
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : c->graph_cache)
+        if (g.nsteps == nsteps && g.parity == c->cur && g.tblock == c->tblock) exec = g.exec;
+    const int cur0 = c->cur;
+    const long long step0 = c->step;
+    if (!exec) {
+        cudaStream_t user = c->stream;
+        c->stream = c->gstream;
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+        tdse_status st = issue_segment(c, nsteps);
+        cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
+        c->stream = user;
+        c->cur = cur0;
+        c->step = step0;
+        TRY(st);
+        if (e != cudaSuccess) return fail(c, TDSE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(c, TDSE_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        c->graph_cache.push_back({static_cast<int>(nsteps), cur0, c->tblock, exec});
+    }
+    CUDA_TRY(c, cudaEventRecord(c->gev[0], c->stream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+    CUDA_TRY(c, cudaGraphLaunch(exec, c->gstream));
+    CUDA_TRY(c, cudaEventRecord(c->gev[1], c->gstream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->gev[1], 0));
+    // the replay advanced the state exactly like issue_segment would have
+    long long left = nsteps;
+    while (left > 0) {
+        const int T = (left >= c->tblock) ? c->tblock : 1;
+        c->cur ^= 1;
+        c->step += T;
+        left -= T;
+    }
+    return TDSE_OK;
+}
+
 tdse_status observe_all(tdse_ctx *c, int slot)
 {
     int t0;
@@ -567,6 +650,7 @@ tdse_status tdse_create(const tdse_params *p, int batch, tdse_ctx **out)
         return TDSE_EINVAL;
     }
     c->tblock = tb;
+    c->tblock_auto = p[0].tblock <= 0;
     c->obs_every = p[0].obs_every > 0 ? p[0].obs_every : 20;
     c->ckpt_every = std::max(0, p[0].ckpt_every);
     for (int i = 0; i < batch; ++i) {
@@ -767,12 +851,8 @@ tdse_status tdse_step(tdse_ctx *c, long long nsteps)
     while (left > 0) {
         long long seg = std::min(left, c->obs_every - (c->step % c->obs_every));
         if (c->ckpt_every > 0) seg = std::min(seg, c->ckpt_every - (c->step % c->ckpt_every));
-        while (seg > 0) {
-            const int T = (seg >= c->tblock) ? c->tblock : 1;
-            TRY(launch_fused(c, T));
-            seg -= T;
-            left -= T;
-        }
+        TRY(run_segment(c, seg));
+        left -= seg;
         if (c->step % c->obs_every == 0) {
             TRY(observe_all(c, nrec));
             if (++nrec == kRecCap) {
@@ -960,6 +1040,126 @@ tdse_status tdse_load_state(tdse_ctx *c, const char *path)
     return fail(c, TDSE_ESTATE, "load_state not available in this build");
 }
 
+int tdse_variant_count(int precision, int tsteps) { return step_variant_count(precision, tsteps); }
+
+tdse_status tdse_set_variant(tdse_ctx *c, int tsteps, int variant)
+{
+    if (!c) return TDSE_EINVAL;
+    if (tsteps < 1 || tsteps > kMaxTblock || (c->precision == TDSE_FP64 && tsteps != 1) ||
+        variant < 0 || variant >= step_variant_count(c->precision, tsteps))
+        return fail(c, TDSE_EINVAL, "no variant %d for %d fused steps", variant, tsteps);
+    TRY(ensure_device(c));
+    return build_plan(c, tsteps, variant);
+}
+
+tdse_status tdse_set_graphs(tdse_ctx *c, int enable)
+{
+    if (!c) return TDSE_EINVAL;
+    c->graphs = enable != 0;
+    return TDSE_OK;
+}
+
+tdse_status tdse_get_tuning(tdse_ctx *c, tdse_tuning *out)
+{
+    if (!c || !out) return TDSE_EINVAL;
+    memset(out, 0, sizeof *out);
+    out->tblock = c->tblock;
+    for (int T = 1; T <= kMaxTblock; ++T) {
+        if (c->precision == TDSE_FP64 && T != 1) continue;
+        out->variant[T] = c->plans[T].variant;
+        out->ms_per_step[T] = c->tuned_ms_per_step[T];
+        const char *n = step_variant_name(c->precision, T, c->plans[T].variant);
+        if (n) snprintf(out->name[T], sizeof out->name[T], "%s", n);
+    }
+    return TDSE_OK;
+}
+
+tdse_status tdse_autotune(tdse_ctx *c, int launches)
+{
+    if (!c || launches < 1) return TDSE_EINVAL;
+    TRY(ensure_device(c));
+    // save what the trial launches overwrite
+    const size_t es = elem_size(c->precision);
+    const int nf = c->precision == TDSE_FP32_KAHAN ? 4 : 2;
+    std::vector<void *> saved;
+    auto field = [&](Member &mb, int f, int buf) -> void * {
+        return f == 0 ? mb.dev.R[buf] : f == 1 ? mb.dev.I[buf] : f == 2 ? mb.dev.cR[buf] : mb.dev.cI[buf];
+    };
+    for (Member &mb : c->m) {
+        const size_t fbytes = static_cast<size_t>(mb.dev.plane) * mb.dev.nz * es;
+        const size_t pbytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * sizeof(double);
+        for (int f = 0; f < nf; ++f) {
+            void *p;
+            TRY(dalloc(c, fbytes, &p));
+            CUDA_TRY(c, cudaMemcpyAsync(p, field(mb, f, c->cur), fbytes, cudaMemcpyDeviceToDevice, c->stream));
+            saved.push_back(p);
+        }
+        for (double *src : {mb.dev.flux, mb.dev.jlast}) {
+            void *p;
+            TRY(dalloc(c, pbytes, &p));
+            CUDA_TRY(c, cudaMemcpyAsync(p, src, pbytes, cudaMemcpyDeviceToDevice, c->stream));
+            saved.push_back(p);
+        }
+    }
+    const int cur0 = c->cur;
+    const long long step0 = c->step;
+    const bool prof0 = c->profiling;
+    const int tb0 = c->tblock;
+    c->profiling = false;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    tdse_status st = TDSE_OK;
+    for (int T = 1; T <= kMaxTblock && st == TDSE_OK; ++T) {
+        if (c->precision == TDSE_FP64 && T != 1) continue;
+        c->tblock = T;
+        double best = 1e300;
+        int bestv = 0;
+        for (int v = 0; v < step_variant_count(c->precision, T) && st == TDSE_OK; ++v) {
+            if ((st = build_plan(c, T, v)) != TDSE_OK) break;
+            if ((st = launch_fused(c, T)) != TDSE_OK) break;
+            cudaEventRecord(e0, c->stream);
+            for (int l = 0; l < launches && st == TDSE_OK; ++l) st = launch_fused(c, T);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = fail(c, TDSE_ECUDA, "autotune launch failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per_step = ms / (launches * T);
+            if (per_step < best) {
+                best = per_step;
+                bestv = v;
+            }
+        }
+        if (st == TDSE_OK) st = build_plan(c, T, bestv);
+        c->tuned_ms_per_step[T] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tblock = tb0;
+    if (st == TDSE_OK && c->tblock_auto && c->precision != TDSE_FP64)
+        c->tblock = c->tuned_ms_per_step[2] < c->tuned_ms_per_step[1] ? 2 : 1;
+    // restore the state, the flux integral and the counters
+    size_t k = 0;
+    for (Member &mb : c->m) {
+        const size_t fbytes = static_cast<size_t>(mb.dev.plane) * mb.dev.nz * es;
+        const size_t pbytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * sizeof(double);
+        for (int f = 0; f < nf; ++f)
+            cudaMemcpyAsync(field(mb, f, cur0), saved[k++], fbytes, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(mb.dev.flux, saved[k++], pbytes, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(mb.dev.jlast, saved[k++], pbytes, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (void *p : saved) dfree(c, p);
+    c->cur = cur0;
+    c->step = step0;
+    c->profiling = prof0;
+    c->prof = tdse_profile{};
+    return st;
+}
+
 tdse_status tdse_set_profiling(tdse_ctx *c, int enable)
 {
     if (!c) return TDSE_EINVAL;
@@ -980,6 +1180,13 @@ tdse_status tdse_destroy(tdse_ctx *c)
     if (!c) return TDSE_OK;
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    drop_graphs(c);
+    if (c->gstream) {
+        cudaStreamSynchronize(c->gstream);
+        cudaStreamDestroy(c->gstream);
+        cudaEventDestroy(c->gev[0]);
+        cudaEventDestroy(c->gev[1]);
+    }
     std::vector<void *> all = c->allocations;
     for (void *p : all) dfree(c, p);
     delete c;

@@ -61,6 +61,14 @@ class Sim:
     def set_state(self, member: int, R, I):
         T.tdse_set_state(self.ctx, member, R, I)
 
+    def autotune(self, launches: int = 4) -> dict:
+        """Time every kernel variant on this batch and keep the fastest."""
+        T.tdse_autotune(self.ctx, launches)
+        return T.tdse_get_tuning(self.ctx)
+
+    def tuning(self) -> dict:
+        return T.tdse_get_tuning(self.ctx)
+
     # -- stepping and results
     def step(self, n: int):
         T.tdse_step(self.ctx, n)

@@ -60,6 +60,11 @@ class Profile(ctypes.Structure):
                 ("reserved", ctypes.c_int)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("tblock", ctypes.c_int), ("variant", ctypes.c_int * 3),
+                ("ms_per_step", ctypes.c_double * 3), ("name", (ctypes.c_char * 48) * 3)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -82,6 +87,11 @@ SIGNATURES = {
     "tdse_adjoint": (_I, [_VP, _I, _VP, _VP, _VP, _I]),
     "tdse_save_state": (_I, [_VP, ctypes.c_char_p]),
     "tdse_load_state": (_I, [_VP, ctypes.c_char_p]),
+    "tdse_variant_count": (_I, [_I, _I]),
+    "tdse_set_variant": (_I, [_VP, _I, _I]),
+    "tdse_autotune": (_I, [_VP, _I]),
+    "tdse_get_tuning": (_I, [_VP, ctypes.POINTER(Tuning)]),
+    "tdse_set_graphs": (_I, [_VP, _I]),
     "tdse_set_profiling": (_I, [_VP, _I]),
     "tdse_get_profile": (_I, [_VP, ctypes.POINTER(Profile)]),
     "tdse_observables_static": (_I, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP]),
@@ -256,6 +266,31 @@ def tdse_save_state(ctx, path: str):
 
 def tdse_load_state(ctx, path: str):
     _check(ctx, lib().tdse_load_state(ctx, os.fsencode(path)))
+
+
+def tdse_variant_count(precision: int, tsteps: int) -> int:
+    return lib().tdse_variant_count(precision, tsteps)
+
+
+def tdse_set_variant(ctx, tsteps: int, variant: int):
+    _check(ctx, lib().tdse_set_variant(ctx, tsteps, variant))
+
+
+def tdse_autotune(ctx, launches: int = 4):
+    _check(ctx, lib().tdse_autotune(ctx, launches))
+
+
+def tdse_get_tuning(ctx) -> dict:
+    t = Tuning()
+    _check(ctx, lib().tdse_get_tuning(ctx, ctypes.byref(t)))
+    return {"tblock": t.tblock,
+            "variant": {1: t.variant[1], 2: t.variant[2]},
+            "ms_per_step": {1: t.ms_per_step[1], 2: t.ms_per_step[2]},
+            "name": {1: t.name[1].value.decode(), 2: t.name[2].value.decode()}}
+
+
+def tdse_set_graphs(ctx, enable: bool):
+    _check(ctx, lib().tdse_set_graphs(ctx, int(bool(enable))))
 
 
 def tdse_set_profiling(ctx, enable: bool):

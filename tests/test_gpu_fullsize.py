@@ -1,0 +1,198 @@
+"""Full-size workloads, CUDA graphs and the autotuner, through the C ABI.
+
+* Graph replay and every kernel variant chosen by the autotuner give results
+  bitwise equal to direct launches (the per-node arithmetic never changes).
+* 128x128x256 diffraction run at full size: FP64 GPU vs oracle (1e-11) and FP32 /
+  FP32+Kahan vs oracle (rel L2 <= 1e-4, |dQ|/Q <= 1e-5) over 400 steps; over the
+  full 4000 steps FP32 / FP32+Kahan vs the oracle-pinned FP64 GPU path (same
+  tolerances; the FP64 oracle at this size takes minutes per run).
+* 48-member organic-film batch: one persistent launch per step block, autotuned,
+  members bitwise equal to solo runs, one member vs the oracle.
+* 512x512x1024 throughput run: the state after 4 steps (the launch configuration
+  the benchmark times) is checked node by node against the oracle on light-cone
+  windows: a 40x40 column of the full grid around each sample, periodic images of
+  the full grid's potential, walls at the window edges; after N steps and the
+  half-step start only nodes more than 2N + 1 cells inside a window are exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_07416_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_07416_gb300 import build
+    build.build()
+    from paper_2401_07416_gb300 import tdse
+    return tdse
+
+
+def Sim(*a, **k):
+    from paper_2401_07416_gb300.sim import Sim as S
+    return S(*a, **k)
+
+
+def run(T, wl, precision, steps, tblock=0, graphs=True, autotune=False, V=None):
+    with Sim(wl.grid, precision=precision, tblock=tblock) as s:
+        if not graphs:
+            T.tdse_set_graphs(s.ctx, False)
+        if V is None:
+            s.set_atoms(0, wl.atoms)
+        else:
+            s.set_potential(0, V)
+        if autotune:
+            s.autotune(2)
+        s.set_packet(0, wl.packet)
+        s.step(steps)
+        R, I = s.state(0)
+        return R, I, s.flux_map(0), s.observables(0), s.tuning()
+
+
+def rel_l2(R, I, Ro, Io):
+    return math.sqrt(np.sum((R - Ro) ** 2 + (I - Io) ** 2) / np.sum(Ro ** 2 + Io ** 2))
+
+
+def test_graphs_and_autotuned_variants_bitwise_equal_direct_launches(T):
+    wl = W.config2(W.FP32_KAHAN)
+    ref = run(T, wl, T.FP32_KAHAN, 50, graphs=False)
+    for kw in ({"graphs": True}, {"graphs": True, "autotune": True}):
+        got = run(T, wl, T.FP32_KAHAN, 50, **kw)
+        for a, b in zip(got[:3], ref[:3]):
+            assert np.array_equal(a, b)
+    # every variant of every depth, set explicitly
+    for prec in (T.FP32, T.FP64):
+        base = None
+        for tb in (1, 2):
+            if prec == T.FP64 and tb == 2:
+                continue
+            for v in range(T.tdse_variant_count(prec, tb)):
+                with Sim(wl.grid, precision=prec, tblock=tb) as s:
+                    T.tdse_set_variant(s.ctx, tb, v)
+                    s.set_atoms(0, wl.atoms)
+                    s.set_packet(0, wl.packet)
+                    s.step(10)
+                    R, I = s.state(0)
+                if base is None:
+                    base = (R, I)
+                assert np.array_equal(R, base[0]) and np.array_equal(I, base[1]), (prec, tb, v)
+
+
+@pytest.fixture(scope="module")
+def config2_oracle():
+    wl = W.config2(W.FP64)
+    g = wl.grid
+    V = oracle.potential_atoms(g, wl.atoms)
+    R0, I0 = oracle.initial_state(g, wl.packet, V)
+    R, I, F, _ = oracle.run(g, V, R0, I0, 400)
+    return wl, V, R, I, F, oracle.observables(g, V, R, I)
+
+
+def test_config2_full_size_vs_oracle(T, config2_oracle):
+    wl, V, Ro, Io, Fo, oo = config2_oracle
+    R, I, F, o, _ = run(T, wl, T.FP64, 400)
+    scale = max(np.abs(Ro).max(), np.abs(Io).max())
+    assert max(np.abs(R - Ro).max(), np.abs(I - Io).max()) / scale < TOL64
+    assert np.abs(F - Fo).max() < TOL64 * np.abs(Fo).max()
+    assert o["Q"] == pytest.approx(oo["Q"], rel=TOL64)
+    for prec in (T.FP32, T.FP32_KAHAN):
+        R, I, F, o, _ = run(T, wl, prec, 400)
+        assert rel_l2(R, I, Ro, Io) < 1e-4
+        assert abs(o["Q"] - oo["Q"]) / oo["Q"] < 1e-5
+        assert np.linalg.norm(F - Fo) < 1e-3 * np.linalg.norm(Fo)
+
+
+def test_config2_4000_steps_fp32_vs_fp64(T):
+    wl = W.config2(W.FP64)
+    R64, I64, F64, o64, _ = run(T, wl, T.FP64, wl.steps)
+    errs = {}
+    for prec in (T.FP32, T.FP32_KAHAN):
+        R, I, F, o, _ = run(T, wl, prec, wl.steps)
+        errs[prec] = (rel_l2(R, I, R64, I64), abs(o["Q"] - o64["Q"]) / o64["Q"],
+                      np.linalg.norm(F - F64) / np.linalg.norm(F64))
+        assert errs[prec][0] < 1e-4
+        assert errs[prec][1] < 1e-5
+        assert errs[prec][2] < 1e-3
+    print("config2 4000 steps vs FP64 GPU (rel L2 psi, |dQ|/Q, rel L2 F):", errs)
+
+
+def test_config3_batch_autotuned_equals_solo_and_oracle(T):
+    members = W.config3(48, W.FP32_KAHAN)
+    steps = 40
+    with Sim([m.grid for m in members], precision=T.FP32_KAHAN) as s:
+        for i, m in enumerate(members):
+            s.set_atoms(i, m.atoms)
+        s.autotune(2)
+        for i, m in enumerate(members):
+            s.set_packet(i, m.packet)
+        s.step(steps)
+        picks = [0, 17, 47]
+        got = {i: (s.state(i), s.flux_map(i)) for i in picks}
+    for i in picks:
+        R, I, F, _, _ = run(T, members[i], T.FP32_KAHAN, steps)
+        assert np.array_equal(got[i][0][0], R) and np.array_equal(got[i][0][1], I)
+        assert np.array_equal(got[i][1], F)
+    m = members[17]
+    g = m.grid
+    V = oracle.potential_atoms(g, m.atoms)
+    R0, I0 = oracle.initial_state(g, m.packet, V)
+    Ro, Io, _, _ = oracle.run(g, V, R0, I0, steps)
+    assert rel_l2(got[17][0][0], got[17][0][1], Ro, Io) < 1e-4
+
+
+def window_oracle(wl, x0, y0, width, steps):
+    """Oracle state on a width x width x nz column starting at node (x0, y0)."""
+    g = wl.grid
+    sub = W.Grid(nx=width, ny=width, nz=g.nz, hx=g.hx, hy=g.hy, hz=g.hz, dt=g.dt,
+                 bc=(W.DIRICHLET, W.DIRICHLET, g.bc[2]), mask_lo=g.mask_lo,
+                 mask_hi=g.mask_hi, mask_eta=g.mask_eta, det_k=-1)
+    origin = (x0 * g.hx, y0 * g.hy, 0.0)
+    L = g.lengths
+    period = [l if b == W.PERIODIC else 0.0 for l, b in zip(L, g.bc)]
+    V = oracle.potential_atoms_window(sub, origin, period, wl.atoms, rc=0.5 * min(L[0], L[1]))
+    R0, I0 = oracle.wavepacket_window(sub, origin, wl.packet.r0, wl.packet.sigma, wl.packet.k0)
+    # the packet is a plane wave along x and y: the full grid's normalisation is the
+    # window's times sqrt(window area / grid area)
+    s = math.sqrt((width * width) / (g.nx * g.ny))
+    R0, I0 = R0 * s, I0 * s
+    R, I, _, _ = oracle.run(sub, V, R0, oracle.init_half(sub, V, R0, I0), steps, flux=False)
+    return R, I
+
+
+@pytest.mark.parametrize("precision", ["FP32_KAHAN", "FP64"])
+def test_config5_light_cone_windows(T, precision):
+    import torch
+    prec = getattr(T, precision)
+    wl = W.config5(prec)
+    g = wl.grid
+    steps = 4
+    with Sim(g, precision=prec) as s:
+        s.set_atoms(0, wl.atoms)
+        s.set_packet(0, wl.packet)
+        s.step(steps)
+        Rd = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
+        Id = torch.empty_like(Rd)
+        T.tdse_get_state(s.ctx, 0, Rd, Id)
+    width, margin = 40, 2 * steps + 2
+    for (x0, y0) in [(-20, -20), (200, 130), (492, 300), (100, 480)]:
+        xs = np.arange(x0, x0 + width) % g.nx
+        ys = np.arange(y0, y0 + width) % g.ny
+        Rg = Rd[:, ys][:, :, xs].cpu().numpy()
+        Ig = Id[:, ys][:, :, xs].cpu().numpy()
+        Ro, Io = window_oracle(wl, x0, y0, width, steps)
+        sl = (slice(None), slice(margin, width - margin), slice(margin, width - margin))
+        if prec == T.FP64:
+            scale = max(np.abs(Ro[sl]).max(), np.abs(Io[sl]).max())
+            assert max(np.abs(Rg[sl] - Ro[sl]).max(), np.abs(Ig[sl] - Io[sl]).max()) < TOL64 * scale
+        else:
+            assert rel_l2(Rg[sl], Ig[sl], Ro[sl], Io[sl]) < 1e-4
