@@ -23,13 +23,11 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -56,7 +54,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="kahan", choices=["kahan", "fp32", "fp64"])
-    ap.add_argument("--tblock", type=int, default=2)
+    ap.add_argument("--tblock", type=int, default=0, help="steps fused per launch (0: autotuned)")
+    ap.add_argument("--ncu-case", action="store_true", help="mid-size run of the fused kernel for ncu")
+    ap.add_argument("--variant", type=int, default=0, help="kernel variant for --ncu-case")
     ap.add_argument("--no-extras", action="store_true", help="skip variants, e2e and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -139,13 +139,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key: str, cells: int):
+def ncu_traffic(variant: str, cells: int):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
     scaled to `cells` grid nodes; None if absent or taken on another kernel build."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
-        e = d[kernel_key]
+        e = d[variant]
         if e.get("source_hash") != kernel_source_hash():
             return None
         return e["dram_bytes_per_launch"] * cells / e["cells"]
@@ -239,18 +239,24 @@ def reference_arm(args):
 
 # ------------------------------------------------------------------ GPU arm
 
-def make_ctx(T, wl, precision, tblock, V_dev=None):
+def make_ctx(T, wl, precision, tblock, V_dev=None, autotune=True):
+    """Context for one workload: potential from atoms (or a device V), kernel
+    variants autotuned on this grid, packet set."""
     from paper_2401_07416_gb300.sim import Sim
     s = Sim(wl.grid, precision=precision, tblock=tblock)
     if V_dev is None:
         s.set_atoms(0, wl.atoms)
     else:
         s.set_potential(0, V_dev)
+    if autotune:
+        s.autotune(2)
     s.set_packet(0, wl.packet)
     return s
 
 
 def timed_steps(torch, T, s, steps, warmup, barrier):
+    """W untimed steps, then K steps between CUDA events on the library's stream with
+    per-launch event timing of the fused kernel enabled (events only, no host sync)."""
     s.step(warmup)
     torch.cuda.synchronize()
     barrier()
@@ -270,10 +276,84 @@ def timed_steps(torch, T, s, steps, warmup, barrier):
     return ms, prof
 
 
+def ncu_case(args):
+    """A mid-size (256x256x512, ~1.3 GB) run of the fused kernel for ncu captures:
+    the 512x512x1024 workload's spacing, slab geometry scaled, two warm-up launches
+    then `--steps` steps, kernel variant fixed by --variant."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2401_07416_gb300 import build as B
+    B.build()
+    from paper_2401_07416_gb300 import tdse as T
+    from paper_2401_07416_gb300.sim import Sim
+    prec = {"kahan": W.FP32_KAHAN, "fp32": W.FP32, "fp64": W.FP64}[args.precision]
+    tb = 1 if prec == W.FP64 else max(1, args.tblock)
+    g = W.Grid(nx=256, ny=256, nz=512, hx=0.05, hy=0.05, hz=0.05, dt=5e-4, mask_lo=20,
+               mask_hi=20, det_k=180, obs_every=10 ** 6)
+    atoms = W.square_slab(8, 4, 1.6, 0.4 * 25.6, 12.8, 12.8, W.rng_for(5), 0.05)
+    with Sim(g, precision=prec, tblock=tb) as s:
+        T.tdse_set_variant(s.ctx, tb, args.variant)
+        s.set_atoms(0, atoms)
+        s.set_packet(0, W.Packet((6.4, 6.4, 12.74), (0.0, 0.0, 2.0), (0.0, 0.0, -1.9)))
+        s.step(2 * tb)
+        s.step(args.steps)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": True, "cells": g.cells, "precision": args.precision,
+                          "tblock": tb, "tuning": s.tuning()}))
+
+
+def batch_throughput(torch, T, steps, warmup):
+    """48-member film batch (uneven grids) in one context: aggregate cell-updates/s."""
+    from paper_2401_07416_gb300.sim import Sim
+    members = W.config3(48, W.FP32_KAHAN)
+    with Sim([m.grid for m in members], precision=W.FP32_KAHAN) as s:
+        for i, m in enumerate(members):
+            s.set_atoms(i, m.atoms)
+        s.autotune(2)
+        for i, m in enumerate(members):
+            s.set_packet(i, m.packet)
+        ms, prof = timed_steps(torch, T, s, steps, warmup, lambda: None)
+        tun = s.tuning()
+    cells = sum(m.grid.cells for m in members)
+    return {"value": cells * steps / (ms * 1e-3), "unit": "cell-updates/s", "members": 48,
+            "cells": cells, "steps": steps, "precision": "f32+kahan", "tuning": tun,
+            "graphs": "profiling pass (direct launches)"}
+
+
+def adjoint_cost(torch, T):
+    """96x96x192, 3000 steps: forward with FP64 checkpoints every 100 steps, then the
+    adjoint of the detector-flux loss (dL/dV and the 32 atoms)."""
+    from paper_2401_07416_gb300.sim import Sim
+    out = {}
+    for prec in (W.FP32_KAHAN, W.FP64):
+        wl = W.config4(prec)
+        g = wl.grid
+        with Sim(g, precision=prec, ckpt_every=100) as s:
+            s.set_atoms(0, wl.atoms)
+            s.set_packet(0, wl.packet)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step(wl.steps)
+            torch.cuda.synchronize()
+            t_fwd = time.perf_counter() - t0
+            gF = 2 * s.flux_map(0)
+            gV = np.zeros((g.nz, g.ny, g.nx))
+            ga = np.zeros_like(wl.atoms)
+            t0 = time.perf_counter()
+            T.tdse_adjoint(s.ctx, 0, gF, gV, ga)
+            t_adj = time.perf_counter() - t0
+        out[PREC_NAME[prec]] = {"forward_s": t_fwd, "adjoint_s": t_adj,
+                                "adjoint_over_forward": t_adj / t_fwd,
+                                "adjoint_cell_steps_per_s": g.cells * wl.steps / t_adj}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.ncu_case:
+        return ncu_case(args)
 
     import torch
     rank, world, local = dist_info()
@@ -300,8 +380,9 @@ def main():
     cells = g.cells
     hbm_peak, peak_kind = measured_peaks()
 
-    # headline: the fused step on the full grid
+    # headline: the fused step on the full grid, autotuned on it
     s = make_ctx(T, wl, prec, tblock)
+    tuning = s.tuning()
     V_dev = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
     T.tdse_get_potential(s.ctx, 0, V_dev)
     with ClockSampler(local) as clk:
@@ -318,17 +399,20 @@ def main():
         t_max = float(t.item())
     value = world * cells * args.steps / (t_max * 1e-3)
 
+    tb = prof["steps_per_launch"]
     launch_ms = prof["step_ms"] / max(1, prof["step_launches"])
     bytes_launch = BYTES_PER_NODE[prec] * cells
     achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
-    key = f"{PREC_NAME[prec]}_t{tblock}"
-    traffic = ncu_traffic(key, cells)
+    variant = tuning["name"][tb]
+    traffic = ncu_traffic(variant, cells)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
-                "peak_source": f"{peak_kind} HBM copy bandwidth",
-                "kernel": f"fused_step_kernel ({key})",
+                "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS hbm_gbs)",
+                "kernel": f"fused_step_kernel {variant} ({tb} steps per launch)",
                 "algorithmic_bytes_per_launch": bytes_launch,
+                "bytes_per_node_per_launch": BYTES_PER_NODE[prec],
                 "avg_launch_ms": launch_ms, "launches": prof["step_launches"],
+                "reduce_ms_total": prof["reduce_ms"],
                 "effective_frac_vs_unfused_fp32": value / world * 20 / 1e9 / hbm_peak}
 
     extras = {}
@@ -336,20 +420,22 @@ def main():
     cpu = None
     if not args.no_extras:
         # FP64 unfused step and the FP32 variants on the same grid (same potential)
-        variants = [(W.FP64, 1)] + [(p, t) for p in (W.FP32, W.FP32_KAHAN) for t in (1, 2)
-                                    if (p, t) != (prec, tblock)]
+        variants = [(W.FP64, 1)] + [(p, t) for p in (W.FP32, W.FP32_KAHAN) for t in (1, 2)]
         for vp, vt in variants:
             steps_v = max(10, args.steps // (8 if vp == W.FP64 else 2))
             sv = make_ctx(T, W.config5(vp), vp, vt, V_dev)
+            vname = sv.tuning()["name"][vt]
             vms, vprof = timed_steps(torch, T, sv, steps_v, min(args.warmup, 6), barrier)
             sv.close()
             vlaunch = vprof["step_ms"] / max(1, vprof["step_launches"])
             extras[f"{PREC_NAME[vp]}_t{vt}"] = {
                 "value": cells * steps_v / (vms * 1e-3), "unit": "cell-updates/s",
-                "steps": steps_v, "avg_launch_ms": vlaunch,
-                "hbm_frac": BYTES_PER_NODE[vp] * cells / (vlaunch * 1e-3) / 1e9 / hbm_peak}
-        if "f64_t1" in extras:
-            extras["speedup_vs_fp64_plain"] = value / world / extras["f64_t1"]["value"]
+                "steps": steps_v, "variant": vname, "avg_launch_ms": vlaunch,
+                "hbm_frac_of_algorithmic_bytes": BYTES_PER_NODE[vp] * cells / (vlaunch * 1e-3) / 1e9 / hbm_peak}
+        extras["speedup_vs_fp64_plain"] = value / world / extras["f64_t1"]["value"]
+        extras["batched_48_films"] = batch_throughput(torch, T, max(20, args.steps // 2),
+                                                      min(args.warmup, 6))
+        extras["adjoint_96x96x192_3000"] = adjoint_cost(torch, T)
 
         # end to end through the C ABI from pinned host buffers: potential in,
         # packet set-up, the steps, flux map and observables out
@@ -359,6 +445,7 @@ def main():
         from paper_2401_07416_gb300.sim import Sim
         se = Sim(g, precision=prec, tblock=tblock)
         se.set_potential(0, V_host)       # first call allocates; not timed
+        se.autotune(2)
         se.set_packet(0, wl.packet)
         se.step(4)
         torch.cuda.synchronize()
@@ -377,7 +464,7 @@ def main():
                "h2d_bytes_per_step": V_host.numel() * 8 / args.steps,
                "d2h_bytes_per_step": (F_host.numel() * 8 + 64) / args.steps,
                "includes": "tdse_set_potential (pinned host V, FP64), tdse_set_wavepacket, "
-                           "tdse_step, tdse_get_flux_map, tdse_observables"}
+                           "tdse_step (CUDA-graph replay), tdse_get_flux_map, tdse_observables"}
         del V_host
         if rank == 0 and world == 1:
             cpu = time_oracle(args.cpu_seconds)
@@ -391,7 +478,7 @@ def main():
         "config": {"workload": "512x512x1024 grid, h=0.05, 4x16x16 softened-Coulomb slab, "
                                "cos^2 absorbing layers, detector flux every step, "
                                "Q/E every 20 steps",
-                   "precision": PREC_NAME[prec], "steps_per_launch": tblock,
+                   "precision": PREC_NAME[prec], "steps_per_launch": tb, "variant": variant,
                    "nx": g.nx, "ny": g.ny, "nz": g.nz, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (state ~10 GB), no flush"},
         "roofline": roofline,

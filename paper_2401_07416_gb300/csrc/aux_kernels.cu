@@ -1,5 +1,6 @@
 // Set-up, conversion and reduction kernels of libtdse (everything except the
 // fused step).  All arithmetic that feeds a reduction is FP64.
+#include <algorithm>
 #include <cmath>
 
 #include "tdse_internal.cuh"
@@ -295,37 +296,83 @@ __global__ void get_state_kernel(MemberDev m, double *__restrict__ R, double *__
 // ---------------------------------------------------------------- observables
 
 // Per block: sums of (R.R + I+.I, R^2 + I^2, R.AR + I+.AI) with I+ = I + A R.
+// One thread per (x, y) column marching along z with a register window of R and
+// I at z-1, z, z+1; x/y neighbours come from the ghost zones.  FP64 contexts do
+// everything in FP64.  FP32 contexts evaluate the stencil and the per-node
+// products in FP32 (the arithmetic of the step itself; Kahan compensation terms
+// are below that resolution) and sum each column with compensated FP32
+// additions before adding it to the FP64 accumulators.
 template <typename Real>
-__global__ void observables_kernel(MemberDev m, int kahan, int buf, double *__restrict__ partials)
+struct ColumnSum {
+    Real s = Real(0), c = Real(0);
+    __device__ __forceinline__ void add(Real x)
+    {
+        const Real y = x - c;
+        const Real t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const
+    {
+        return static_cast<double>(s) - static_cast<double>(c);
+    }
+};
+
+// FP64 contexts: the column sums are plain FP64 additions.
+template <>
+struct ColumnSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <typename Real>
+__global__ void observables_kernel(MemberDev m, int buf, double *__restrict__ partials)
 {
     __shared__ double sh[32];
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
-    const Real *R = reinterpret_cast<const Real *>(m.R[buf]);
-    const Real *I = reinterpret_cast<const Real *>(m.I[buf]);
-    const Real *CR = kahan ? reinterpret_cast<const Real *>(m.cR[buf]) : nullptr;
-    const Real *CI = kahan ? reinterpret_cast<const Real *>(m.cI[buf]) : nullptr;
-    const Real *D = reinterpret_cast<const Real *>(m.d);
+    const Real *__restrict__ R = reinterpret_cast<const Real *>(m.R[buf]);
+    const Real *__restrict__ I = reinterpret_cast<const Real *>(m.I[buf]);
+    const Real *__restrict__ D = reinterpret_cast<const Real *>(m.d);
+    const long long ncol = static_cast<long long>(m.nx) * m.ny;
+    const Real cx = static_cast<Real>(m.cx), cy = static_cast<Real>(m.cy),
+               cz = static_cast<Real>(m.cz);
+    const long long plane = m.plane, pitch = m.pitch;
     double q = 0.0, pn = 0.0, e = 0.0;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(t % m.nx);
-        const int y = static_cast<int>((t / m.nx) % m.ny);
-        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
-        const long long o = pidx(m, x, y, z);
-        const double d = static_cast<double>(D[o]);
-        const double r0 = value<Real>(m, R, CR, o), i0 = value<Real>(m, I, CI, o);
-        const double ar = m.cx * (nbr<Real>(m, R, CR, x + 1, y, z) + nbr<Real>(m, R, CR, x - 1, y, z)) +
-                          m.cy * (nbr<Real>(m, R, CR, x, y + 1, z) + nbr<Real>(m, R, CR, x, y - 1, z)) +
-                          m.cz * (nbr<Real>(m, R, CR, x, y, z + 1) + nbr<Real>(m, R, CR, x, y, z - 1)) +
-                          d * r0;
-        const double ai = m.cx * (nbr<Real>(m, I, CI, x + 1, y, z) + nbr<Real>(m, I, CI, x - 1, y, z)) +
-                          m.cy * (nbr<Real>(m, I, CI, x, y + 1, z) + nbr<Real>(m, I, CI, x, y - 1, z)) +
-                          m.cz * (nbr<Real>(m, I, CI, x, y, z + 1) + nbr<Real>(m, I, CI, x, y, z - 1)) +
-                          d * i0;
-        const double ip = i0 + ar;
-        q += r0 * r0 + ip * i0;
-        pn += r0 * r0 + i0 * i0;
-        e += r0 * ar + ip * ai;
+    for (long long col = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; col < ncol;
+         col += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(col % m.nx), y = static_cast<int>(col / m.nx);
+        const long long base = static_cast<long long>(y + m.G) * pitch + (x + m.G);
+        const long long last = base + static_cast<long long>(m.nz - 1) * plane;
+        Real rm = m.per_z ? R[last] : Real(0), im = m.per_z ? I[last] : Real(0);
+        Real rc = R[base], ic = I[base];
+        ColumnSum<Real> sq, sp, se;
+        for (int z = 0; z < m.nz; ++z) {
+            const long long o = base + static_cast<long long>(z) * plane;
+            Real rp, ip;
+            if (z + 1 < m.nz) {
+                rp = R[o + plane];
+                ip = I[o + plane];
+            } else {
+                rp = m.per_z ? R[base] : Real(0);
+                ip = m.per_z ? I[base] : Real(0);
+            }
+            const Real d = D[o];
+            const Real ar = fma(cx, R[o + 1] + R[o - 1],
+                                fma(cy, R[o + pitch] + R[o - pitch], fma(cz, rm + rp, d * rc)));
+            const Real ai = fma(cx, I[o + 1] + I[o - 1],
+                                fma(cy, I[o + pitch] + I[o - pitch], fma(cz, im + ip, d * ic)));
+            const Real ipl = ic + ar;
+            sq.add(rc * rc + ipl * ic);
+            sp.add(rc * rc + ic * ic);
+            se.add(rc * ar + ipl * ai);
+            rm = rc;
+            rc = rp;
+            im = ic;
+            ic = ip;
+        }
+        q += sq.value();
+        pn += sp.value();
+        e += se.value();
     }
     const double sq = block_sum(q, sh);
     const double sp = block_sum(pn, sh);
@@ -469,12 +516,15 @@ cudaError_t launch_observables(const MemberDev &m, int precision, int buf, doubl
                                double *record, int *status, double q_ref, long long step,
                                cudaStream_t s)
 {
+    const long long ncol = static_cast<long long>(m.nx) * m.ny;
+    const int threads = 128;
+    const int nparts = static_cast<int>(std::min<long long>((ncol + threads - 1) / threads, kObsParts));
     if (precision == 0)
-        observables_kernel<double><<<kObsParts, kThreads, 0, s>>>(m, 0, buf, partials);
+        observables_kernel<double><<<nparts, threads, 0, s>>>(m, buf, partials);
     else
-        observables_kernel<float><<<kObsParts, kThreads, 0, s>>>(m, precision == 2, buf, partials);
-    observables_finalize_kernel<<<1, kThreads, 0, s>>>(m, partials, kObsParts, record, status,
-                                                       q_ref, step);
+        observables_kernel<float><<<nparts, threads, 0, s>>>(m, buf, partials);
+    observables_finalize_kernel<<<1, kThreads, 0, s>>>(m, partials, nparts, record, status, q_ref,
+                                                       step);
     return cudaGetLastError();
 }
 
