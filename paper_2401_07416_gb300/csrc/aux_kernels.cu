@@ -84,41 +84,119 @@ __device__ __forceinline__ double atom_phi(double r2, double a2, double rc)
     return 1.0 / rho - (ic - 0.5 * du * ic3 + 0.375 * du * du * ic5);
 }
 
-__global__ void potential_kernel(MemberDev m, const double *__restrict__ atoms, int n,
+// Atom position in grid units: node index i0 and fraction f in [0, 1), so that
+// the distance to node i along the axis is h (i - i0 - f) with the integer part
+// exact (and the periodic minimum image an integer wrap).
+struct AtomCell {
+    int i[3];
+    float f[3];
+    double fd[3];
+    double Z;
+};
+
+__global__ void atom_cells_kernel(MemberDev m, const double *__restrict__ atoms, int n,
+                                  AtomCell *__restrict__ out)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    const double h[3] = {m.hx, m.hy, m.hz};
+    AtomCell c;
+    for (int k = 0; k < 3; ++k) {
+        const double u = atoms[4 * a + k] / h[k];
+        const double fl = floor(u);
+        c.i[k] = static_cast<int>(fl);
+        c.fd[k] = u - fl;
+        c.f[k] = static_cast<float>(c.fd[k]);
+    }
+    c.Z = atoms[4 * a + 3];
+    out[a] = c;
+}
+
+// Integer offset i - i0 along an axis of n nodes, wrapped to the nearest periodic
+// image ([-n/2, n/2]) on a periodic axis.
+__device__ __forceinline__ int wrap_offset(int k, int n, int periodic)
+{
+    if (periodic) {
+        k %= n;
+        if (k > n / 2) k -= n;
+        if (k < -n / 2) k += n;
+    }
+    return k;
+}
+
+// V at every node from the atoms.  FP64 contexts evaluate each term in FP64;
+// FP32 contexts evaluate the profile in FP32 (V is stored in FP32 for the step)
+// from exact integer offsets, accumulating with compensated FP32 additions.
+template <typename Compute>
+__global__ void potential_kernel(MemberDev m, const AtomCell *__restrict__ atoms, int n,
                                  double a2, double rc, double *__restrict__ V)
 {
-    __shared__ double sa[4 * 256];
+    __shared__ AtomCell sa[128];
     const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
     const long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     const int x = static_cast<int>(t % m.nx);
     const int y = static_cast<int>((t / m.nx) % m.ny);
     const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
-    const double L[3] = {m.nx * m.hx, m.ny * m.hy, m.nz * m.hz};
-    const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
-    const int per[3] = {m.per_x, m.per_y, m.per_z};
-    const double r[3] = {x * m.hx, y * m.hy, z * m.hz};
-    const double rc2 = rc > 0.0 ? rc * rc : 1e300;
-    double v = 0.0;
-    for (int a0 = 0; a0 < n; a0 += 256) {
-        const int na = min(256, n - a0);
+    const Compute h[3] = {static_cast<Compute>(m.hx), static_cast<Compute>(m.hy),
+                          static_cast<Compute>(m.hz)};
+    const Compute ca2 = static_cast<Compute>(a2);
+    // profile phi(u) = (u + a^2)^-1/2 - [p0 + p1 (u - uc) + p2 (u - uc)^2] for u < uc
+    const double uc = rc > 0.0 ? rc * rc : 0.0;
+    const double ic = rc > 0.0 ? 1.0 / sqrt(uc + a2) : 0.0;
+    const Compute p0 = static_cast<Compute>(ic), p1 = static_cast<Compute>(-0.5 * ic * ic * ic),
+                  p2 = static_cast<Compute>(0.375 * ic * ic * ic * ic * ic);
+    const Compute cuc = static_cast<Compute>(uc);
+    const bool cut = rc > 0.0;
+    Compute acc = Compute(0), comp = Compute(0);
+    for (int a0 = 0; a0 < n; a0 += 128) {
+        const int na = min(128, n - a0);
         __syncthreads();
-        for (int i = threadIdx.x; i < 4 * na; i += blockDim.x) sa[i] = atoms[4 * a0 + i];
+        if (threadIdx.x < na) sa[threadIdx.x] = atoms[a0 + threadIdx.x];
         __syncthreads();
-        if (t < cells) {
-            for (int a = 0; a < na; ++a) {
-                double r2 = 0.0;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    double d = r[k] - sa[4 * a + k];
-                    if (per[k]) d -= L[k] * floor(d * iL[k] + 0.5);   // nearest periodic image
-                    r2 += d * d;
-                }
-                if (r2 >= rc2) continue;   // beyond the cut-off the profile is zero
-                v -= sa[4 * a + 3] * atom_phi(r2, a2, rc);
+        if (t >= cells) continue;
+        for (int a = 0; a < na; ++a) {
+            const AtomCell &c = sa[a];
+            const int kx = wrap_offset(x - c.i[0], m.nx, m.per_x);
+            const int ky = wrap_offset(y - c.i[1], m.ny, m.per_y);
+            const int kz = wrap_offset(z - c.i[2], m.nz, m.per_z);
+            Compute gx, gy, gz;   // offsets in grid units, nearest image on periodic axes
+            if constexpr (sizeof(Compute) == 8) {
+                gx = kx - c.fd[0];
+                gy = ky - c.fd[1];
+                gz = kz - c.fd[2];
+            } else {
+                gx = static_cast<float>(kx) - c.f[0];
+                gy = static_cast<float>(ky) - c.f[1];
+                gz = static_cast<float>(kz) - c.f[2];
+            }
+            if (m.per_x && gx < Compute(-0.5) * m.nx) gx += m.nx;
+            if (m.per_y && gy < Compute(-0.5) * m.ny) gy += m.ny;
+            if (m.per_z && gz < Compute(-0.5) * m.nz) gz += m.nz;
+            const Compute dx = h[0] * gx, dy = h[1] * gy, dz = h[2] * gz;
+            const Compute u = fma(dx, dx, fma(dy, dy, dz * dz));
+            if (cut && u >= cuc) continue;   // beyond the cut-off the profile is zero
+            Compute phi;
+            if constexpr (sizeof(Compute) == 8) {
+                phi = 1.0 / sqrt(u + ca2);
+            } else {
+                phi = rsqrtf(u + ca2);
+            }
+            if (cut) {
+                const Compute du = u - cuc;
+                phi -= fma(fma(p2, du, p1), du, p0);
+            }
+            const Compute term = -static_cast<Compute>(c.Z) * phi;
+            if constexpr (sizeof(Compute) == 8) {
+                acc += term;
+            } else {
+                const Compute yk = term - comp;
+                const Compute tk = acc + yk;
+                comp = (tk - acc) - yk;
+                acc = tk;
             }
         }
     }
-    if (t < cells) V[t] = v;
+    if (t < cells) V[t] = static_cast<double>(acc) - static_cast<double>(comp);
 }
 
 // d = -2 (cx + cy + cz) - cv V into the padded Real array; V kept in FP64.
@@ -443,13 +521,21 @@ cudaError_t launch_fill_ghosts(const MemberDev &m, void *field, int elem, cudaSt
 }
 
 cudaError_t launch_potential_atoms(const MemberDev &m, const double *atoms, int n, double a2,
-                                   double rc, double *V, cudaStream_t s)
+                                   double rc, double *V, void *scratch, int precision,
+                                   cudaStream_t s)
 {
     const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
-    potential_kernel<<<static_cast<unsigned>((cells + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-        m, atoms, n, a2, rc, V);
+    AtomCell *ac = static_cast<AtomCell *>(scratch);
+    if (n > 0) atom_cells_kernel<<<(n + 127) / 128, 128, 0, s>>>(m, atoms, n, ac);
+    const unsigned blocks = static_cast<unsigned>((cells + 127) / 128);
+    if (precision == 0)
+        potential_kernel<double><<<blocks, 128, 0, s>>>(m, ac, n, a2, rc, V);
+    else
+        potential_kernel<float><<<blocks, 128, 0, s>>>(m, ac, n, a2, rc, V);
     return cudaGetLastError();
 }
+
+size_t atom_cell_bytes(int n) { return static_cast<size_t>(n > 0 ? n : 1) * sizeof(AtomCell); }
 
 cudaError_t launch_build_d(const MemberDev &m, int elem, const double *V, double *V64,
                            cudaStream_t s)

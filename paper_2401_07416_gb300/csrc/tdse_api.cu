@@ -768,17 +768,19 @@ tdse_status tdse_set_atoms(tdse_ctx *c, int member, int n, const double *xyzZ, d
         r_cut = rc;
     }
     const size_t cells = static_cast<size_t>(d.nx) * d.ny * d.nz;
-    void *V = nullptr, *A = nullptr;
+    void *V = nullptr, *A = nullptr, *AC = nullptr;
     TRY(dalloc(c, cells * sizeof(double), &V));
     TRY(dalloc(c, std::max<size_t>(1, 4 * static_cast<size_t>(n)) * sizeof(double), &A));
+    TRY(dalloc(c, atom_cell_bytes(n), &AC));
     if (n > 0)
         CUDA_TRY(c, cudaMemcpyAsync(A, xyzZ, 4 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, launch_potential_atoms(d, static_cast<double *>(A), n, soft_a2, r_cut,
-                                       static_cast<double *>(V), c->stream));
+                                       static_cast<double *>(V), AC, c->precision, c->stream));
     tdse_status st = potential_to_d(c, mb, static_cast<double *>(V));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     dfree(c, V);
     dfree(c, A);
+    dfree(c, AC);
     TRY(st);
     mb.atoms.assign(xyzZ, xyzZ + 4 * n);
     mb.soft_a2 = soft_a2;

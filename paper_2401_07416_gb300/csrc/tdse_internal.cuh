@@ -83,8 +83,12 @@ cudaError_t launch_step(int precision, int tsteps, int variant, const StepLaunch
 
 // aux_kernels.cu
 cudaError_t launch_fill_ghosts(const MemberDev &m, void *field, int elem, cudaStream_t s);
+// V[nz][ny][nx] (FP64) from n atoms [n][4]; `scratch` holds atom_cell_bytes(n).
+// precision 0 evaluates every term in FP64, otherwise the profile in FP32.
 cudaError_t launch_potential_atoms(const MemberDev &m, const double *atoms, int n, double a2,
-                                   double rc, double *V, cudaStream_t s);
+                                   double rc, double *V, void *scratch, int precision,
+                                   cudaStream_t s);
+size_t atom_cell_bytes(int n);
 // d (padded, Real) from V (unpadded FP64, NULL: V = 0); V copied into V64
 cudaError_t launch_build_d(const MemberDev &m, int elem, const double *V, double *V64,
                            cudaStream_t s);
