@@ -131,12 +131,9 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for name in sorted(os.listdir(os.path.join(ROOT, "paper_2401_07416_gb300", "csrc"))):
-        if name.startswith("step_kernels") or name.endswith(".cuh"):
-            with open(os.path.join(ROOT, "paper_2401_07416_gb300", "csrc", name), "rb") as f:
-                h.update(f.read())
-    return h.hexdigest()[:16]
+    """Hash of the fused-step kernel source the traffic figures were taken on."""
+    with open(os.path.join(ROOT, "paper_2401_07416_gb300", "csrc", "step_kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def ncu_traffic(variant: str, cells: int):

@@ -180,9 +180,12 @@ TDSE_API tdse_status tdse_get_flux_map(tdse_ctx *ctx, int member, double *F, int
 TDSE_API tdse_status tdse_adjoint(tdse_ctx *ctx, int member, const double *dL_dF, double *dL_dV,
                          double *dL_datoms, int on_device);
 
-/* Save / restore the whole context state (fields, compensation, flux integral,
- * step counters, observation history) to / from a file; the file records the
- * parameters and load_state rejects a mismatch (EINVAL). */
+/* Save / restore the whole context state to / from a binary file: for every
+ * member its parameters, the raw state fields (R, I and, in Kahan mode, their
+ * compensation terms, each stored exactly as FP64), V, the flux integral and last flux,
+ * the observation history, the atoms and the adjoint checkpoints; plus the step
+ * counter.  load_state needs a context created with the same batch and grid
+ * parameters (EINVAL otherwise) and replaces its potential and state. */
 TDSE_API tdse_status tdse_save_state(tdse_ctx *ctx, const char *path);
 TDSE_API tdse_status tdse_load_state(tdse_ctx *ctx, const char *path);
 

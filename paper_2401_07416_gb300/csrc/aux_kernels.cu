@@ -371,6 +371,25 @@ __global__ void get_state_kernel(MemberDev m, double *__restrict__ R, double *__
     }
 }
 
+// Interior of a padded Real field <-> unpadded FP64 array (exact in both directions
+// for values that are Real).
+template <typename Real>
+__global__ void field_io_kernel(MemberDev m, Real *field, double *host_side, int to_field)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % m.nx);
+        const int y = static_cast<int>((t / m.nx) % m.ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+        const long long o = pidx(m, x, y, z);
+        if (to_field)
+            field[o] = static_cast<Real>(host_side[t]);
+        else
+            host_side[t] = static_cast<double>(field[o]);
+    }
+}
+
 // ---------------------------------------------------------------- observables
 
 // Per block: sums of (R.R + I+.I, R^2 + I^2, R.AR + I+.AI) with I+ = I + A R.
@@ -595,6 +614,17 @@ cudaError_t launch_get_state(const MemberDev &m, double *R64, double *I64, int p
         get_state_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, R64, I64, 0, buf);
     else
         get_state_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, R64, I64, precision == 2, buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_io(const MemberDev &m, void *field, int elem, double *array, int to_field,
+                            cudaStream_t s)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    if (elem == 8)
+        field_io_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, static_cast<double *>(field), array, to_field);
+    else
+        field_io_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, static_cast<float *>(field), array, to_field);
     return cudaGetLastError();
 }
 

@@ -624,6 +624,26 @@ tdse_status potential_to_d(tdse_ctx *c, Member &mb, const double *V_dev)
 
 }  // namespace
 
+namespace {
+
+const char kMagic[8] = {'T', 'D', 'S', 'E', 'S', 'T', '0', '1'};
+
+bool same_grid(const tdse_params &a, const tdse_params &b)
+{
+    return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.hx == b.hx && a.hy == b.hy &&
+           a.hz == b.hz && a.dt == b.dt && a.hbar == b.hbar && a.mass == b.mass &&
+           a.bc[0] == b.bc[0] && a.bc[1] == b.bc[1] && a.bc[2] == b.bc[2] &&
+           a.mask_lo == b.mask_lo && a.mask_hi == b.mask_hi && a.mask_eta == b.mask_eta &&
+           a.det_k == b.det_k && a.precision == b.precision;
+}
+
+template <typename T>
+bool put(FILE *f, const T *p, size_t n) { return fwrite(p, sizeof(T), n, f) == n; }
+template <typename T>
+bool get(FILE *f, T *p, size_t n) { return fread(p, sizeof(T), n, f) == n; }
+
+}  // namespace
+
 extern "C" {
 
 const char *tdse_version(void) { return kVersion; }
@@ -1033,13 +1053,127 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
 tdse_status tdse_save_state(tdse_ctx *c, const char *path)
 {
     if (!c || !path) return TDSE_EINVAL;
-    return fail(c, TDSE_ESTATE, "save_state not available in this build");
+    for (const Member &mb : c->m)
+        if (!mb.have_state) return fail(c, TDSE_ESTATE, "every member needs a state to be saved");
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(c, TDSE_EINVAL, "cannot open %s for writing", path);
+    bool ok = put(f, kMagic, 8);
+    const int B = static_cast<int>(c->m.size());
+    ok = ok && put(f, &B, 1) && put(f, &c->step, 1);
+    std::vector<double> host;
+    for (Member &mb : c->m) {
+        const size_t cells = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz;
+        const size_t pix = static_cast<size_t>(mb.dev.nx) * mb.dev.ny;
+        const int from = mb.from_packet, nh = static_cast<int>(mb.hist.size()),
+                  na = static_cast<int>(mb.atoms.size()), nck = static_cast<int>(mb.ckpts.size());
+        ok = ok && put(f, &mb.p, 1) && put(f, &from, 1) && put(f, &mb.q0, 1) &&
+             put(f, &mb.soft_a2, 1) && put(f, &mb.r_cut, 1);
+        ok = ok && put(f, &nh, 1) && put(f, mb.hist.data(), nh) && put(f, &na, 1) &&
+             put(f, mb.atoms.data(), na);
+        // raw fields: R, I (and the Kahan compensation terms), exact in FP64
+        const int nf = c->precision == TDSE_FP32_KAHAN ? 4 : 2;
+        void *fields[4] = {mb.dev.R[c->cur], mb.dev.I[c->cur], mb.dev.cR[c->cur], mb.dev.cI[c->cur]};
+        void *tmp = nullptr;
+        TRY(dalloc(c, cells * 8, &tmp));
+        host.resize(cells);
+        for (int k = 0; k < nf; ++k) {
+            CUDA_TRY(c, launch_field_io(mb.dev, fields[k], static_cast<int>(elem_size(c->precision)),
+                                        static_cast<double *>(tmp), 0, c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(host.data(), tmp, cells * 8, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            ok = ok && put(f, host.data(), cells);
+        }
+        dfree(c, tmp);
+        host.resize(2 * cells);
+        CUDA_TRY(c, cudaMemcpy(host.data(), mb.V64, cells * 8, cudaMemcpyDeviceToHost));
+        ok = ok && put(f, host.data(), cells);
+        CUDA_TRY(c, cudaMemcpy(host.data(), mb.dev.flux, pix * 8, cudaMemcpyDeviceToHost));
+        CUDA_TRY(c, cudaMemcpy(host.data() + pix, mb.dev.jlast, pix * 8, cudaMemcpyDeviceToHost));
+        ok = ok && put(f, host.data(), 2 * pix) && put(f, &nck, 1);
+        for (auto &ck : mb.ckpts) {
+            CUDA_TRY(c, cudaMemcpy(host.data(), ck.second, 2 * cells * 8, cudaMemcpyDeviceToHost));
+            ok = ok && put(f, &ck.first, 1) && put(f, host.data(), 2 * cells);
+        }
+    }
+    ok = (fclose(f) == 0) && ok;
+    return ok ? TDSE_OK : fail(c, TDSE_EINVAL, "write to %s failed", path);
 }
 
 tdse_status tdse_load_state(tdse_ctx *c, const char *path)
 {
     if (!c || !path) return TDSE_EINVAL;
-    return fail(c, TDSE_ESTATE, "load_state not available in this build");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(c, TDSE_EINVAL, "cannot open %s", path);
+    auto bad = [&](const char *why) {
+        fclose(f);
+        return fail(c, TDSE_EINVAL, "%s: %s", path, why);
+    };
+    char magic[8];
+    int B = 0;
+    long long step = 0;
+    if (!get(f, magic, 8) || memcmp(magic, kMagic, 8) != 0) return bad("not a tdse state file");
+    if (!get(f, &B, 1) || B != static_cast<int>(c->m.size()) || !get(f, &step, 1))
+        return bad("batch size differs");
+    tdse_status st = ensure_device(c);
+    if (st != TDSE_OK) {
+        fclose(f);
+        return st;
+    }
+    std::vector<double> host;
+    for (Member &mb : c->m) {
+        const size_t cells = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz;
+        const size_t pix = static_cast<size_t>(mb.dev.nx) * mb.dev.ny;
+        tdse_params p;
+        int from = 0, nh = 0, na = 0, nck = 0;
+        double q0 = 0, a2 = 0, rc = 0;
+        if (!get(f, &p, 1) || !same_grid(p, mb.p)) return bad("parameters differ from the context's");
+        if (!get(f, &from, 1) || !get(f, &q0, 1) || !get(f, &a2, 1) || !get(f, &rc, 1) ||
+            !get(f, &nh, 1) || nh < 0)
+            return bad("truncated");
+        std::vector<double> hist(nh), atoms;
+        if (!get(f, hist.data(), nh) || !get(f, &na, 1) || na < 0) return bad("truncated");
+        atoms.resize(na);
+        const int nf = c->precision == TDSE_FP32_KAHAN ? 4 : 2;
+        host.resize((nf + 1) * cells);
+        if (!get(f, atoms.data(), na) || !get(f, host.data(), (nf + 1) * cells)) return bad("truncated");
+        // potential, then the raw fields into the current buffer
+        void *tmp = nullptr;
+        TRY(dalloc(c, (nf + 1) * cells * 8, &tmp));
+        double *dv = static_cast<double *>(tmp);
+        CUDA_TRY(c, cudaMemcpy(dv, host.data(), (nf + 1) * cells * 8, cudaMemcpyHostToDevice));
+        TRY(potential_to_d(c, mb, dv + nf * cells));
+        void *fields[4] = {mb.dev.R[c->cur], mb.dev.I[c->cur], mb.dev.cR[c->cur], mb.dev.cI[c->cur]};
+        for (int k = 0; k < nf; ++k)
+            CUDA_TRY(c, launch_field_io(mb.dev, fields[k], static_cast<int>(elem_size(c->precision)),
+                                        dv + k * cells, 1, c->stream));
+        TRY(fill_all_ghosts(c, mb, c->cur));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        dfree(c, tmp);
+        host.resize(2 * pix);
+        if (!get(f, host.data(), 2 * pix) || !get(f, &nck, 1) || nck < 0) return bad("truncated");
+        CUDA_TRY(c, cudaMemcpy(mb.dev.flux, host.data(), pix * 8, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(mb.dev.jlast, host.data() + pix, pix * 8, cudaMemcpyHostToDevice));
+        clear_checkpoints(c, mb);
+        host.resize(2 * cells);
+        for (int k = 0; k < nck; ++k) {
+            long long s = 0;
+            if (!get(f, &s, 1) || !get(f, host.data(), 2 * cells)) return bad("truncated");
+            void *ck = nullptr;
+            TRY(dalloc(c, 2 * cells * 8, &ck));
+            CUDA_TRY(c, cudaMemcpy(ck, host.data(), 2 * cells * 8, cudaMemcpyHostToDevice));
+            mb.ckpts.push_back({s, static_cast<double *>(ck)});
+        }
+        mb.from_packet = from != 0;
+        mb.q0 = q0;
+        mb.hist = hist;
+        mb.atoms = atoms;
+        mb.soft_a2 = a2;
+        mb.r_cut = rc;
+        mb.have_state = true;
+    }
+    fclose(f);
+    c->step = step;
+    return TDSE_OK;
 }
 
 int tdse_variant_count(int precision, int tsteps) { return step_variant_count(precision, tsteps); }

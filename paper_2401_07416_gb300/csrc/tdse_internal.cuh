@@ -103,6 +103,10 @@ cudaError_t launch_set_state(const MemberDev &m, const double *R64, const double
                              int precision, int buf, cudaStream_t s);
 cudaError_t launch_get_state(const MemberDev &m, double *R64, double *I64, int precision,
                              int buf, cudaStream_t s);
+// copy the interior of one padded field out to (to_field = 0) or in from an
+// unpadded FP64 array (exact for values representable in the field's type)
+cudaError_t launch_field_io(const MemberDev &m, void *field, int elem, double *array, int to_field,
+                            cudaStream_t s);
 // record[0..5] = {step, Q, norm_paper, energy, flux_last, flux_integrated}.  Sets status bit 1 if Q is
 // not finite or exceeds (1 + 1e-3) q_ref (q_ref <= 0: no growth check).
 cudaError_t launch_observables(const MemberDev &m, int precision, int buf, double *partials,

@@ -92,6 +92,12 @@ class Sim:
         T.tdse_get_flux_map(self.ctx, member, F)
         return F
 
+    def save(self, path: str):
+        T.tdse_save_state(self.ctx, path)
+
+    def load(self, path: str):
+        T.tdse_load_state(self.ctx, path)
+
     def close(self):
         if self.ctx:
             T.tdse_destroy(self.ctx)
