@@ -21,6 +21,7 @@
 // node (FP32: 20 bytes, FP64: 40 bytes; Kahan adds 16 bytes), i.e. 20/T bytes
 // per node-update in FP32.
 #include <cstdio>
+#include <type_traits>
 
 #include "tdse_internal.cuh"
 
@@ -173,6 +174,16 @@ struct Cfg {
     static_assert(MINB * (SMEM + 1024) <= 233472, "CTAs per SM exceed the shared memory");
 };
 
+// Per-item scalars staged in shared memory by thread 0.
+struct ItemScalars {
+    void *outR, *outI, *outCR, *outCI, *mask;
+    double *flux, *jlast;
+    long long plane, pitch;
+    double cx, cy, cz, cj, dt;
+    int m, tile_x, tile_y, kz0, kz1, nx, ny, nz, G;
+    int per_x, per_y, per_z, det_k, mask_lo, mask_hi;
+};
+
 template <class C>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fused_step_kernel(const MemberDev *__restrict__ members, const WorkDev *__restrict__ work,
@@ -190,13 +201,14 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     constexpr bool CHAIN = sizeof(Real) == 8 && !C::KAHAN;
 
     extern __shared__ unsigned char smem_raw[];
-    Real *ringA = reinterpret_cast<Real *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
-                                           ~static_cast<uintptr_t>(127));
+    // pointer arithmetic on smem_raw keeps the shared address space visible to the compiler
+    Real *ringA = reinterpret_cast<Real *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     Real *ringD = ringA + NA * SLOT;
     Real *sbuf = ringD + ND * PLANE;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sbuf + C::NSB * PLANE);
     __shared__ int s_item;
     __shared__ int s_abort;
+    __shared__ ItemScalars S;
 
     const int tid = threadIdx.x;
     const int qx = tid % C::TPX;
@@ -217,46 +229,62 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     long long gbase = 0;   // loads issued by this CTA before the current item
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(counter, 1);
+        // thread 0 takes the next work item and stages the member's scalars in
+        // shared memory (loop invariants then never come back from global memory)
+        if (tid == 0) {
+            const int it_ = atomicAdd(counter, 1);
+            s_item = it_;
+            if (it_ < work->total) {
+                int mm = 0;
+                while (it_ >= work->item_begin[mm + 1]) ++mm;
+                const MemberDev &Mm = members[mm];
+                const int local = it_ - work->item_begin[mm];
+                const int ntx = work->tiles_x[mm], nty = work->tiles_y[mm];
+                S.m = mm;
+                S.tile_x = local % ntx;
+                S.tile_y = (local / ntx) % nty;
+                S.kz0 = (local / (ntx * nty)) * work->chunk[mm];
+                S.kz1 = min(S.kz0 + work->chunk[mm], Mm.nz);
+                S.nx = Mm.nx; S.ny = Mm.ny; S.nz = Mm.nz; S.G = Mm.G;
+                S.per_x = Mm.per_x; S.per_y = Mm.per_y; S.per_z = Mm.per_z;
+                S.det_k = Mm.det_k; S.mask_lo = Mm.mask_lo; S.mask_hi = Mm.mask_hi;
+                S.pitch = Mm.pitch; S.plane = Mm.plane;
+                S.cx = Mm.cx; S.cy = Mm.cy; S.cz = Mm.cz; S.cj = Mm.cj; S.dt = Mm.dt;
+                S.mask = Mm.mask; S.flux = Mm.flux; S.jlast = Mm.jlast;
+                S.outR = Mm.R[1 - in_buf]; S.outI = Mm.I[1 - in_buf];
+                S.outCR = Mm.cR[1 - in_buf]; S.outCI = Mm.cI[1 - in_buf];
+            }
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= work->total) break;
-        int m = 0;
-        while (item >= work->item_begin[m + 1]) ++m;
-        const MemberDev &M = members[m];
-        const int local = item - work->item_begin[m];
-        const int ntx = work->tiles_x[m], nty = work->tiles_y[m];
-        const int tile_x = local % ntx;
-        const int tile_y = (local / ntx) % nty;
-        const int kz0 = (local / (ntx * nty)) * work->chunk[m];
-        const int kz1 = min(kz0 + work->chunk[m], M.nz);
+        const int m = S.m;
+        const MemberDev &M = members[m];   // tensor maps only (thread 0)
+        const int tile_x = S.tile_x, tile_y = S.tile_y, kz0 = S.kz0, kz1 = S.kz1;
         const int L0 = kz0 - H;                 // first plane loaded
         const int nit = (kz1 - kz0) + 2 * H;    // iterations (planes loaded)
-        const int G = M.G, nx = M.nx, ny = M.ny, nz = M.nz;
+        const int G = S.G, nx = S.nx, ny = S.ny, nz = S.nz;
         const int bx = G + tile_x * C::TX - C::HX;   // padded coordinates of the box
         const int by = G + tile_y * C::TY - H;
         const int xs = tile_x * C::TX - C::HX + qx * VEC;   // unpadded x of the first cell
         const int ys0 = tile_y * C::TY - H + r0;             // unpadded y of row 0
-        const bool zper = M.per_z != 0;
-        const int mlo = M.mask_lo, mhi = nz - M.mask_hi;    // planes outside [mlo, mhi) absorb
-        const Real cx = static_cast<Real>(M.cx), cy = static_cast<Real>(M.cy),
-                   cz = static_cast<Real>(M.cz);
-        const Real *maskz = reinterpret_cast<const Real *>(M.mask);
-        const int kd = M.det_k;
+        const bool zper = S.per_z != 0;
+        const int mlo = S.mask_lo, mhi = nz - S.mask_hi;    // planes outside [mlo, mhi) absorb
+        const Real cx = static_cast<Real>(S.cx), cy = static_cast<Real>(S.cy),
+                   cz = static_cast<Real>(S.cz);
+        const Real *maskz = reinterpret_cast<const Real *>(S.mask);
+        const int kd = S.det_k;
         const bool flux_owner = kd >= kz0 && kd < kz1;
 
         // Cells outside the domain on a walled axis are kept at zero after every stage.
+        auto inside = [&](int r, int v) {
+            return (S.per_x || (xs + v >= 0 && xs + v < nx)) && (S.per_y || (ys0 + r >= 0 && ys0 + r < ny));
+        };
         bool walls = false;
-        Real keep[RPT][VEC];
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                const bool in_x = M.per_x || (xs + v >= 0 && xs + v < nx);
-                const bool in_y = M.per_y || (ys0 + r >= 0 && ys0 + r < ny);
-                keep[r][v] = (in_x && in_y) ? Real(1) : Real(0);
-                walls |= !(in_x && in_y);
-            }
+            for (int v = 0; v < VEC; ++v) walls |= !inside(r, v);
         const bool col_in = qx * VEC >= C::HX && qx * VEC < C::HX + C::TX && xs < nx;
         bool store_row[RPT];
         bool any_store = false;
@@ -267,16 +295,20 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         }
         // output offsets within a plane (primary location; ghost copies of periodic axes
         // are added only on tiles that touch a seam)
-        const long long pitch = M.pitch;
-        const bool seam = (M.per_x && (xs < G || xs >= nx - G)) ||
-                          (M.per_y && (ys0 < G || ys0 + RPT - 1 >= ny - G));
-        Real *outR = reinterpret_cast<Real *>(M.R[1 - in_buf]);
-        Real *outI = reinterpret_cast<Real *>(M.I[1 - in_buf]);
-        Real *outCR = reinterpret_cast<Real *>(M.cR[1 - in_buf]);
-        Real *outCI = reinterpret_cast<Real *>(M.cI[1 - in_buf]);
+        const long long pitch = S.pitch;
+        const bool seam = (S.per_x && (xs < G || xs >= nx - G)) ||
+                          (S.per_y && (ys0 < G || ys0 + RPT - 1 >= ny - G));
+        Real *outR = reinterpret_cast<Real *>(S.outR);
+        Real *outI = reinterpret_cast<Real *>(S.outI);
+        Real *outCR = reinterpret_cast<Real *>(S.outCR);
+        Real *outCI = reinterpret_cast<Real *>(S.outCI);
         const long long out0 = static_cast<long long>(ys0 + G) * pitch + (xs + G);
 
-        // register windows of F_1 .. F_{H-1}: [0] old (q-1), [1] center (q), [2] new (q+1)
+        // Register windows of F_1 .. F_{H-1}.  The z-march is unrolled by three and
+        // the window slots are renamed rather than moved: in iteration `it`, once
+        // stage f+1 has run, slot it % 3 of window f holds F_{f+1} at plane q-1
+        // (old), slot (it+1) % 3 at q (center) and slot (it+2) % 3 at q+1 (new),
+        // where q = p-f-2 is the plane stage f+2 works on.
         Real w[NF][3][RPT][VEC];
         Real cw[C::KAHAN ? NF : 1][3][RPT][VEC];
 #pragma unroll
@@ -290,6 +322,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                         w[f][k][r][v] = Real(0);
                         if constexpr (C::KAHAN) cw[f][k][r][v] = Real(0);
                     }
+
+        // Planes p whose stages all work on interior planes (no wall, absorbing
+        // layer, detector or wrap) take a path without those checks; the
+        // arithmetic is the same on both paths.
+        const bool tile_walls = __syncthreads_or(walls) != 0;
+        const int fast_lo = mlo + H;
+        const int fast_hi = zper ? mhi + 1 : min(mhi + 1, nz);
 
         int headA = 0, headD = 0;
         int headB = static_cast<int>(gbase % NB);
@@ -320,48 +359,34 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         int issued = min(PF, nit);
         int waited = 0;
 
-        for (int it = 0; it < nit; ++it) {
-            const int p = L0 + it;
-            if (tid == 0) {
-                if (mbar_wait_bounded(&bars[headB], phase)) {
-                    waited = it + 1;
-                } else {
-                    atomicOr(status, 1);
-                    s_abort = 1;
-                }
-            }
-            __syncthreads();   // plane p has landed; the previous iteration's reads are done
-            if (s_abort) break;
-            if (it + PF < nit) {
-                if (tid == 0) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue(it + PF, PF);
-                }
-                issued = it + PF + 1;
-            }
-            // ring slots of planes p, p-1, p-2 and of d at p-s
-            const Real *A0 = ringA + headA * SLOT;
-            const Real *A1 = ringA + (headA >= 1 ? headA - 1 : headA - 1 + NA) * SLOT;
-            const Real *A2 = ringA + (headA >= 2 ? headA - 2 : headA - 2 + NA) * SLOT;
-            const Real *sb_prev = sbuf + ((it - 1) & 1) * PLANE;   // + 2 (f) PLANE for F_{f+1}
-            Real *sb_cur = sbuf + (it & 1) * PLANE;
-            const bool p_out = !zper && (p < 0 || p >= nz);
+        // The H stages of one iteration (plane p loaded, stage s on plane p - s).
+        auto stages = [&](const int it, const int p, const Real *A0, const Real *A1,
+                          const Real *A2, const Real *sb_prev, Real *sb_cur, auto PHc,
+                          auto FASTc) {
+            constexpr int PH = decltype(PHc)::value;
+            constexpr bool FAST = decltype(FASTc)::value;
+            constexpr int K0 = PH, K1 = (PH + 1) % 3, K2 = (PH + 2) % 3;   // old, center, new
+            const bool p_out = !FAST && !zper && (p < 0 || p >= nz);
 
             Real zmR[RPT][VEC];   // R at plane p-2: stage 1's z- neighbour, stage 2's accumulator
 #pragma unroll
             for (int s = 1; s <= H; ++s) {
-                if (it < 2 * s) continue;                                     // pipeline filling
+                if (!FAST && it < 2 * s) continue;                            // pipeline filling
                 if (warp_row0 + C::RW <= s || warp_row0 >= ROWS - s) continue;  // rows outside the cone
                 const int q = p - s;
                 const bool odd = (s & 1) != 0;
-                const bool q_out = !zper && (q < 0 || q >= nz);
-                int qm = q;                      // plane index inside [0, nz) (periodic z wraps)
-                if (zper) {
-                    qm = q % nz;
-                    if (qm < 0) qm += nz;
+                bool q_out = false, absorb = false;
+                Real mq = Real(1);
+                if constexpr (!FAST) {
+                    q_out = !zper && (q < 0 || q >= nz);
+                    int qm = q;                      // plane index inside [0, nz) (periodic z wraps)
+                    if (zper) {
+                        qm = q % nz;
+                        if (qm < 0) qm += nz;
+                    }
+                    absorb = !q_out && (qm < mlo || qm >= mhi);
+                    if (absorb) mq = maskz[qm];
                 }
-                const bool absorb = !q_out && (qm < mlo || qm >= mhi);
-                const Real mq = absorb ? maskz[qm] : Real(1);
                 int dslot = headD - s;
                 if (dslot < 0) dslot += ND;
                 const Real *Dp = ringD + dslot * PLANE;
@@ -382,17 +407,17 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     ld_vec<Real>(A1 + off_ym, ym);
                     ld_vec<Real>(A1 + off_yp, yp);
                 } else {
-                    const Real *S = sb_prev + (s - 2) * 2 * PLANE;
+                    const Real *Sp = sb_prev + (s - 2) * 2 * PLANE;
 #pragma unroll
                     for (int r = 0; r < RPT; ++r)
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
-                            zm[r][v] = w[s - 2][0][r][v];
-                            c[r][v] = w[s - 2][1][r][v];
-                            zp[r][v] = w[s - 2][2][r][v];
+                            zm[r][v] = w[s - 2][K0][r][v];
+                            c[r][v] = w[s - 2][K1][r][v];
+                            zp[r][v] = w[s - 2][K2][r][v];
                         }
-                    ld_vec<Real>(S + off_ym, ym);
-                    ld_vec<Real>(S + off_yp, yp);
+                    ld_vec<Real>(Sp + off_ym, ym);
+                    ld_vec<Real>(Sp + off_yp, yp);
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) ld_vec<Real>(Dp + own + r * W, dd[r]);
@@ -411,8 +436,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     } else {
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
-                            acc[r][v] = w[s - 3][0][r][v];
-                            if constexpr (C::KAHAN) cacc[r][v] = cw[s - 3][0][r][v];
+                            acc[r][v] = w[s - 3][K0][r][v];
+                            if constexpr (C::KAHAN) cacc[r][v] = cw[s - 3][K0][r][v];
                         }
                     }
                 }
@@ -463,31 +488,34 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                             if constexpr (C::KAHAN) cout[r][v] = mul_rn(cout[r][v], mq);
                         }
                 }
-                if (walls || q_out) {
-                    const Real zq = q_out ? Real(0) : Real(1);
+                if constexpr (!FAST) {
+                    if (walls || q_out) {
+                        const Real zq = q_out ? Real(0) : Real(1);
 #pragma unroll
-                    for (int r = 0; r < RPT; ++r)
+                        for (int r = 0; r < RPT; ++r)
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            out[r][v] *= keep[r][v] * zq;
-                            if constexpr (C::KAHAN) cout[r][v] *= keep[r][v] * zq;
-                        }
-                }
+                            for (int v = 0; v < VEC; ++v) {
+                                const Real keep = inside(r, v) ? Real(1) : Real(0);
+                                out[r][v] *= keep * zq;
+                                if constexpr (C::KAHAN) cout[r][v] *= keep * zq;
+                            }
+                    }
 
-                // detector flux of step (s+1)/2: R^n at planes kd, kd+1 and the new I
-                if (odd && flux_owner && q == kd + 1 && any_store) {
+                    // detector flux of step (s+1)/2: R^n at planes kd, kd+1 and the new I
+                    if (odd && flux_owner && q == kd + 1 && any_store) {
 #pragma unroll
-                    for (int r = 0; r < RPT; ++r) {
-                        if (!store_row[r]) continue;
-                        const int pix = (ys0 + r) * nx + xs;
+                        for (int r = 0; r < RPT; ++r) {
+                            if (!store_row[r]) continue;
+                            const int pix = (ys0 + r) * nx + xs;
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            // I at plane kd is the previous output of stage s
-                            const Real ilo = s < H ? w[s - 1][2][r][v] : Real(0);
-                            const double j = M.cj * (static_cast<double>(zm[r][v]) * out[r][v] -
-                                                     static_cast<double>(c[r][v]) * ilo);
-                            M.flux[pix + v] += j * M.dt;
-                            if (s == H - 1) M.jlast[pix + v] = j;
+                            for (int v = 0; v < VEC; ++v) {
+                                // I at plane kd: the previous output of stage s
+                                const Real ilo = s < H ? w[s - 1][K1][r][v] : Real(0);
+                                const double j = S.cj * (static_cast<double>(zm[r][v]) * out[r][v] -
+                                                         static_cast<double>(c[r][v]) * ilo);
+                                S.flux[pix + v] += j * S.dt;
+                                if (s == H - 1) S.jlast[pix + v] = j;
+                            }
                         }
                     }
                 }
@@ -498,28 +526,22 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     for (int r = 0; r < RPT; ++r) {
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
-                            w[s - 1][0][r][v] = w[s - 1][1][r][v];
-                            w[s - 1][1][r][v] = w[s - 1][2][r][v];
-                            w[s - 1][2][r][v] = out[r][v];
-                            if constexpr (C::KAHAN) {
-                                cw[s - 1][0][r][v] = cw[s - 1][1][r][v];
-                                cw[s - 1][1][r][v] = cw[s - 1][2][r][v];
-                                cw[s - 1][2][r][v] = cout[r][v];
-                            }
+                            w[s - 1][K2][r][v] = out[r][v];
+                            if constexpr (C::KAHAN) cw[s - 1][K2][r][v] = cout[r][v];
                         }
                         if (r == 0 || r == RPT - 1) st_vec<Real>(So + own + r * W, out[r]);
                     }
-                } else if (any_store && q >= kz0 && q < kz1) {
-                    const long long zoff = static_cast<long long>(q) * M.plane;
+                } else if (any_store && (FAST || (q >= kz0 && q < kz1))) {
+                    const long long zoff = static_cast<long long>(q) * S.plane;
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
                         if (!store_row[r]) continue;
                         Real vi[VEC], vci[VEC];
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
-                            vi[v] = absorb ? mul_rn(w[H - 2][1][r][v], mq) : w[H - 2][1][r][v];
+                            vi[v] = absorb ? mul_rn(w[H - 2][K1][r][v], mq) : w[H - 2][K1][r][v];
                             if constexpr (C::KAHAN)
-                                vci[v] = absorb ? mul_rn(cw[H - 2][1][r][v], mq) : cw[H - 2][1][r][v];
+                                vci[v] = absorb ? mul_rn(cw[H - 2][K1][r][v], mq) : cw[H - 2][K1][r][v];
                         }
                         const long long o = zoff + out0 + r * pitch;
                         st_vec<Real>(outR + o, out[r]);
@@ -532,11 +554,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                             const int y = ys0 + r;
                             int dxs[3] = {0, 0, 0}, dys[3] = {0, 0, 0};
                             int ndx = 1, ndy = 1;
-                            if (M.per_x) {
+                            if (S.per_x) {
                                 if (xs < G) dxs[ndx++] = nx;
                                 if (xs >= nx - G) dxs[ndx++] = -nx;
                             }
-                            if (M.per_y) {
+                            if (S.per_y) {
                                 if (y < G) dys[ndy++] = ny;
                                 if (y >= ny - G) dys[ndy++] = -ny;
                             }
@@ -555,10 +577,51 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     }
                 }
             }
+        };
+
+        // One iteration: wait for plane L0 + it, refill the ring, run the stages.
+        auto plane_step = [&](const int it, auto PHc) -> bool {
+            const int p = L0 + it;
+            if (tid == 0) {
+                if (mbar_wait_bounded(&bars[headB], phase)) {
+                    waited = it + 1;
+                } else {
+                    atomicOr(status, 1);
+                    s_abort = 1;
+                }
+            }
+            __syncthreads();   // plane p has landed; the previous iteration's reads are done
+            if (s_abort) return false;
+            if (it + PF < nit) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(it + PF, PF);
+                }
+                issued = it + PF + 1;
+            }
+            // ring slots of planes p, p-1, p-2
+            const Real *A0 = ringA + headA * SLOT;
+            const Real *A1 = ringA + (headA >= 1 ? headA - 1 : headA - 1 + NA) * SLOT;
+            const Real *A2 = ringA + (headA >= 2 ? headA - 2 : headA - 2 + NA) * SLOT;
+            const Real *sb_prev = sbuf + ((it - 1) & 1) * PLANE;   // + 2 (f) PLANE for F_{f+1}
+            Real *sb_cur = sbuf + (it & 1) * PLANE;
+            const bool fast = !tile_walls && it >= 2 * H && p >= fast_lo && p < fast_hi &&
+                              !(flux_owner && p >= kd + 2 && p <= kd + H);
+            if (fast)
+                stages(it, p, A0, A1, A2, sb_prev, sb_cur, PHc, std::true_type{});
+            else
+                stages(it, p, A0, A1, A2, sb_prev, sb_cur, PHc, std::false_type{});
             headA = headA + 1 == NA ? 0 : headA + 1;
             headD = headD + 1 == ND ? 0 : headD + 1;
             headB = headB + 1 == NB ? 0 : headB + 1;
             if (headB == 0) phase ^= 1u;
+            return true;
+        };
+
+        for (int it0 = 0; it0 < nit; it0 += 3) {
+            if (!plane_step(it0, std::integral_constant<int, 0>{})) break;
+            if (it0 + 1 >= nit || !plane_step(it0 + 1, std::integral_constant<int, 1>{})) break;
+            if (it0 + 2 >= nit || !plane_step(it0 + 2, std::integral_constant<int, 2>{})) break;
         }
 
         if (s_abort) {
@@ -615,25 +678,24 @@ struct Variant {
 #define TDSE_VARIANT(P, T, NAME, ...)                                                      \
     Variant{P, T, NAME, &fill_config<Cfg<__VA_ARGS__>>, &launch_cfg<Cfg<__VA_ARGS__>>}
 
-// Kernel variants per (precision, fused steps); the first of each pair is the default.
-// Cfg<Real, 2T, threads per row, rows, Kahan, planes prefetched>
+// Kernel variants per (precision, fused steps).
+// Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched, CTAs per SM>
 // Measured on GB300 (512x512x1024 slab): the first entry of each (precision, steps)
 // group is the fastest and the default; the others remain for the autotuner.
 const Variant kVariants[] = {
     TDSE_VARIANT(1, 1, "f32_t1_w64_r24x2_pf2_b2", float, 2, 16, 24, 2, false, 2, 2),
-    TDSE_VARIANT(1, 1, "f32_t1_w64_r32x2_pf1_b2", float, 2, 16, 32, 2, false, 1, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w64_r48x2_pf2", float, 2, 16, 48, 2, false, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w128_r24x2_pf2", float, 2, 32, 24, 2, false, 2),
-    TDSE_VARIANT(1, 1, "f32_t1_w64_r32x2_pf2", float, 2, 16, 32, 2, false, 2),
-    TDSE_VARIANT(1, 2, "f32_t2_w64_r32x1_pf2", float, 4, 16, 32, 1, false, 2),
+    TDSE_VARIANT(1, 1, "f32_t1_w64_r64x4_pf1", float, 2, 16, 64, 4, false, 1),
     TDSE_VARIANT(1, 2, "f32_t2_w64_r32x2_pf2", float, 4, 16, 32, 2, false, 2),
-    TDSE_VARIANT(2, 1, "k32_t1_w64_r32x1_pf2", float, 2, 16, 32, 1, true, 2),
+    TDSE_VARIANT(1, 2, "f32_t2_w64_r32x1_pf2", float, 4, 16, 32, 1, false, 2),
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x2_pf2", float, 2, 16, 32, 2, true, 2),
+    TDSE_VARIANT(2, 1, "k32_t1_w64_r32x1_pf2", float, 2, 16, 32, 1, true, 2),
     TDSE_VARIANT(2, 2, "k32_t2_w64_r28x2_pf1", float, 4, 16, 28, 2, true, 1),
-    TDSE_VARIANT(2, 2, "k32_t2_w64_r24x2_pf2", float, 4, 16, 24, 2, true, 2),
+    TDSE_VARIANT(2, 2, "k32_t2_w64_r24x1_pf2", float, 4, 16, 24, 1, true, 2),
     TDSE_VARIANT(0, 1, "f64_t1_w64_r16x2_pf1_b2", double, 2, 32, 16, 2, false, 1, 2),
-    TDSE_VARIANT(0, 1, "f64_t1_w64_r32x2_pf1", double, 2, 32, 32, 2, false, 1),
     TDSE_VARIANT(0, 1, "f64_t1_w64_r16x1_pf2", double, 2, 32, 16, 1, false, 2),
+    TDSE_VARIANT(0, 1, "f64_t1_w64_r32x4_pf1", double, 2, 32, 32, 4, false, 1),
 };
 
 const Variant *find_variant(int precision, int tsteps, int variant)

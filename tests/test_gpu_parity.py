@@ -6,8 +6,9 @@ Tolerances (written here, used by every case):
   FP32 / Kahan:    ||psi_gpu - psi_oracle||_2 / ||psi_oracle||_2 <= 1e-4 and
                    |Q_gpu - Q_oracle| / Q_oracle <= 1e-5;
   fused vs unfused and batched vs solo: bitwise equal (same arithmetic, same order).
-Small grids span several tiles with ragged tails in x, y and z (tiles are 56 x 28
-in FP32 T=1, 56 x 24 in T=2, 60 x 20 in FP64; z-chunks are chosen per launch).
+Small grids span several tiles with ragged tails in x, y and z (default tiles are
+56 x 20 in FP32 T=1, 56 x 28 in FP32 T=2, 56 x 24 in Kahan T=2, 60 x 12 in FP64;
+z-chunks are chosen per launch).
 """
 import math
 
