@@ -136,6 +136,21 @@ __device__ __forceinline__ void st_vec<double>(double *p, const double (&v)[2])
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
+// Paired FP32 arithmetic (one instruction for two lanes, each lane rounded to
+// nearest exactly as the scalar operation).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
 // Compile-time shape of one fused-step kernel.
 //   H     half-step stages per launch (2T)
 //   TPX   threads across a region row (VEC cells each)
@@ -157,14 +172,15 @@ struct Cfg {
     static constexpr int RW = 32 / TPX * RPT;           // rows per warp
     static constexpr int PLANE = W * ROWS;
     static constexpr int PLANE_BYTES = PLANE * static_cast<int>(sizeof(Real));
-    static constexpr int NFA = KAHAN ? 4 : 2;           // R, I (, cR, cI) per ring slot
-    static constexpr int NA = PF + 3;                   // R is read two planes back
+    static constexpr int NFC = KAHAN ? 2 : 1;           // a field (and its compensation) per slot
+    static constexpr int NR = PF + 3;                   // R ring: read up to two planes back
+    static constexpr int NI = PF + 2;                   // I ring: read one plane back
     static constexpr int ND = PF + H + 1;               // d is read H planes back
     static constexpr int NB = PF + 1;
     static constexpr int NSB = 2 * (H - 1);             // stage planes, double-buffered
-    static constexpr int NPLANES = NA * NFA + ND + NSB;
+    static constexpr int NPLANES = (NR + NI) * NFC + ND + NSB;
     static constexpr size_t SMEM = static_cast<size_t>(NPLANES) * PLANE_BYTES + 8 * NB + 128;
-    static constexpr uint32_t TX_BYTES = PLANE_BYTES * (NFA + 1);
+    static constexpr uint32_t TX_BYTES = PLANE_BYTES * (2 * NFC + 1);
     static_assert(TPX <= 32 && 32 % TPX == 0, "a region row must sit inside one warp");
     static_assert(ROWS % RPT == 0, "rows per thread must divide the region");
     static_assert(TX > 0 && TY > 0, "halo larger than region");
@@ -191,19 +207,21 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 {
     typedef typename C::Real Real;
     constexpr int H = C::H, VEC = C::VEC, W = C::W, ROWS = C::ROWS, PLANE = C::PLANE;
-    constexpr int RPT = C::RPT, NB = C::NB, PF = C::PF, NA = C::NA, ND = C::ND;
+    constexpr int RPT = C::RPT, NB = C::NB, PF = C::PF, NR = C::NR, NI = C::NI, ND = C::ND;
     constexpr int NF = H > 1 ? H - 1 : 1;   // register windows for F_1 .. F_{H-1}
-    constexpr int SLOT = C::NFA * PLANE;    // one ring slot: R, I (, cR, cI) of a plane
-    constexpr int OFF_I = PLANE, OFF_CR = 2 * PLANE, OFF_CI = 3 * PLANE;
+    constexpr int SLOT = C::NFC * PLANE;    // one ring slot: a field (and its compensation)
+    constexpr int OFF_C = PLANE;            // compensation term within a slot
     // A f = cx sx + cy sy + cz sz + d f (s_a: neighbour sums).  FP64 (ALU-bound)
     // folds the accumulator into the FMA chain; FP32 keeps the increment separate
     // so that its rounding happens at the increment's scale.
     constexpr bool CHAIN = sizeof(Real) == 8 && !C::KAHAN;
+    constexpr bool PAIRED = sizeof(Real) == 4;   // FP32 node updates in paired instructions
 
     extern __shared__ unsigned char smem_raw[];
     // pointer arithmetic on smem_raw keeps the shared address space visible to the compiler
     Real *ringA = reinterpret_cast<Real *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
-    Real *ringD = ringA + NA * SLOT;
+    Real *ringI = ringA + NR * SLOT;
+    Real *ringD = ringI + NI * SLOT;
     Real *sbuf = ringD + ND * PLANE;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sbuf + C::NSB * PLANE);
     __shared__ int s_item;
@@ -272,6 +290,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const int mlo = S.mask_lo, mhi = nz - S.mask_hi;    // planes outside [mlo, mhi) absorb
         const Real cx = static_cast<Real>(S.cx), cy = static_cast<Real>(S.cy),
                    cz = static_cast<Real>(S.cz);
+        const float2 cx2 = make_float2(float(cx), float(cx)), cy2 = make_float2(float(cy), float(cy)),
+                     cz2 = make_float2(float(cz), float(cz));
         const Real *maskz = reinterpret_cast<const Real *>(S.mask);
         const int kd = S.det_k;
         const bool flux_owner = kd >= kz0 && kd < kz1;
@@ -330,7 +350,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const int fast_lo = mlo + H;
         const int fast_hi = zper ? mhi + 1 : min(mhi + 1, nz);
 
-        int headA = 0, headD = 0;
+        int headA = 0, headI = 0, headD = 0;
         int headB = static_cast<int>(gbase % NB);
         uint32_t phase = static_cast<uint32_t>((gbase / NB) & 1);
 
@@ -338,16 +358,18 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             const int L = L0 + l;
             const int zc = zper ? ((L % nz) + nz) % nz : L;
             int b = headB + ahead; if (b >= NB) b -= NB;
-            int a = headA + ahead; if (a >= NA) a -= NA;
+            int a = headA + ahead; if (a >= NR) a -= NR;
+            int i = headI + ahead; if (i >= NI) i -= NI;
             int d = headD + ahead; if (d >= ND) d -= ND;
             uint64_t *bar = &bars[b];
-            Real *slot = ringA + a * SLOT;
+            Real *slotR = ringA + a * SLOT;
+            Real *slotI = ringI + i * SLOT;
             mbar_arrive_expect_tx(bar, C::TX_BYTES);
-            tma_load_3d(slot, &M.tm_R[in_buf], bx, by, zc, bar);
-            tma_load_3d(slot + OFF_I, &M.tm_I[in_buf], bx, by, zc, bar);
+            tma_load_3d(slotR, &M.tm_R[in_buf], bx, by, zc, bar);
+            tma_load_3d(slotI, &M.tm_I[in_buf], bx, by, zc, bar);
             if constexpr (C::KAHAN) {
-                tma_load_3d(slot + OFF_CR, &M.tm_cR[in_buf], bx, by, zc, bar);
-                tma_load_3d(slot + OFF_CI, &M.tm_cI[in_buf], bx, by, zc, bar);
+                tma_load_3d(slotR + OFF_C, &M.tm_cR[in_buf], bx, by, zc, bar);
+                tma_load_3d(slotI + OFF_C, &M.tm_cI[in_buf], bx, by, zc, bar);
             }
             tma_load_3d(ringD + d * PLANE, &M.tm_d, bx, by, zc, bar);
         };
@@ -361,8 +383,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 
         // The H stages of one iteration (plane p loaded, stage s on plane p - s).
         auto stages = [&](const int it, const int p, const Real *A0, const Real *A1,
-                          const Real *A2, const Real *sb_prev, Real *sb_cur, auto PHc,
-                          auto FASTc) {
+                          const Real *A2, const Real *I1, const Real *sb_prev, Real *sb_cur,
+                          auto PHc, auto FASTc) {
             constexpr int PH = decltype(PHc)::value;
             constexpr bool FAST = decltype(FASTc)::value;
             constexpr int K0 = PH, K1 = (PH + 1) % 3, K2 = (PH + 2) % 3;   // old, center, new
@@ -427,12 +449,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
                     if (s == 1) {
-                        ld_vec<Real>(A1 + OFF_I + own + r * W, acc[r]);
-                        if constexpr (C::KAHAN) ld_vec<Real>(A1 + OFF_CI + own + r * W, cacc[r]);
+                        ld_vec<Real>(I1 + own + r * W, acc[r]);
+                        if constexpr (C::KAHAN) ld_vec<Real>(I1 + OFF_C + own + r * W, cacc[r]);
                     } else if (s == 2) {
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) acc[r][v] = zmR[r][v];
-                        if constexpr (C::KAHAN) ld_vec<Real>(A2 + OFF_CR + own + r * W, cacc[r]);
+                        if constexpr (C::KAHAN) ld_vec<Real>(A2 + OFF_C + own + r * W, cacc[r]);
                     } else {
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
@@ -456,6 +478,50 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 for (int r = 0; r < RPT; ++r) {
                     const Real xl = __shfl_up_sync(kFull, c[r][VEC - 1], 1);
                     const Real xr = __shfl_down_sync(kFull, c[r][0], 1);
+                    if constexpr (PAIRED) {
+                        // lanes (v, v+1) in one instruction; only the x-neighbour sum,
+                        // whose operands are shifted by one lane, stays scalar
+#pragma unroll
+                        for (int v = 0; v < VEC; v += 2) {
+                            auto pr = [](const Real *a, int i) { return make_float2(a[i], a[i + 1]); };
+                            const float2 sx = make_float2(
+                                (v == 0 ? xl : c[r][v - 1]) + c[r][v + 1],
+                                c[r][v] + (v + 2 == VEC ? xr : c[r][v + 2]));
+                            const float2 sy = add2(r == 0 ? pr(ym, v) : pr(c[r - 1], v),
+                                                   r == RPT - 1 ? pr(yp, v) : pr(c[r + 1], v));
+                            const float2 sz = add2(pr(zm[r], v), pr(zp[r], v));
+                            float2 delta = mul2(pr(dd[r], v), pr(c[r], v));
+                            delta = fma2(cz2, sz, delta);
+                            delta = fma2(cy2, sy, delta);
+                            delta = fma2(cx2, sx, delta);
+                            const float2 a = pr(acc[r], v);
+                            float2 o, co = make_float2(0.f, 0.f);
+                            if constexpr (C::KAHAN) {
+                                // odd: y = delta - c, t = a + y, c' = (t - a) - y;
+                                // even (increment -delta): with y' = delta + c = -y exactly,
+                                // t = a - y', c' = (t - a) + y'
+                                const float2 ca = pr(cacc[r], v);
+                                if (odd) {
+                                    const float2 y = sub2(delta, ca);
+                                    o = add2(a, y);
+                                    co = sub2(sub2(o, a), y);
+                                } else {
+                                    const float2 y = add2(delta, ca);
+                                    o = sub2(a, y);
+                                    co = add2(sub2(o, a), y);
+                                }
+                            } else {
+                                o = odd ? add2(a, delta) : sub2(a, delta);
+                            }
+                            out[r][v] = o.x;
+                            out[r][v + 1] = o.y;
+                            if constexpr (C::KAHAN) {
+                                cout[r][v] = co.x;
+                                cout[r][v + 1] = co.y;
+                            }
+                        }
+                        continue;
+                    }
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
                         const Real sx = (v == 0 ? xl : c[r][v - 1]) + (v == VEC - 1 ? xr : c[r][v + 1]);
@@ -599,19 +665,21 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 }
                 issued = it + PF + 1;
             }
-            // ring slots of planes p, p-1, p-2
+            // R slots of planes p, p-1, p-2 and the I slot of plane p-1
             const Real *A0 = ringA + headA * SLOT;
-            const Real *A1 = ringA + (headA >= 1 ? headA - 1 : headA - 1 + NA) * SLOT;
-            const Real *A2 = ringA + (headA >= 2 ? headA - 2 : headA - 2 + NA) * SLOT;
+            const Real *A1 = ringA + (headA >= 1 ? headA - 1 : headA - 1 + NR) * SLOT;
+            const Real *A2 = ringA + (headA >= 2 ? headA - 2 : headA - 2 + NR) * SLOT;
+            const Real *I1 = ringI + (headI >= 1 ? headI - 1 : headI - 1 + NI) * SLOT;
             const Real *sb_prev = sbuf + ((it - 1) & 1) * PLANE;   // + 2 (f) PLANE for F_{f+1}
             Real *sb_cur = sbuf + (it & 1) * PLANE;
             const bool fast = !tile_walls && it >= 2 * H && p >= fast_lo && p < fast_hi &&
                               !(flux_owner && p >= kd + 2 && p <= kd + H);
             if (fast)
-                stages(it, p, A0, A1, A2, sb_prev, sb_cur, PHc, std::true_type{});
+                stages(it, p, A0, A1, A2, I1, sb_prev, sb_cur, PHc, std::true_type{});
             else
-                stages(it, p, A0, A1, A2, sb_prev, sb_cur, PHc, std::false_type{});
-            headA = headA + 1 == NA ? 0 : headA + 1;
+                stages(it, p, A0, A1, A2, I1, sb_prev, sb_cur, PHc, std::false_type{});
+            headA = headA + 1 == NR ? 0 : headA + 1;
+            headI = headI + 1 == NI ? 0 : headI + 1;
             headD = headD + 1 == ND ? 0 : headD + 1;
             headB = headB + 1 == NB ? 0 : headB + 1;
             if (headB == 0) phase ^= 1u;
@@ -686,16 +754,16 @@ const Variant kVariants[] = {
     TDSE_VARIANT(1, 1, "f32_t1_w64_r24x2_pf2_b2", float, 2, 16, 24, 2, false, 2, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w64_r48x2_pf2", float, 2, 16, 48, 2, false, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w128_r24x2_pf2", float, 2, 32, 24, 2, false, 2),
-    TDSE_VARIANT(1, 1, "f32_t1_w64_r64x4_pf1", float, 2, 16, 64, 4, false, 1),
     TDSE_VARIANT(1, 2, "f32_t2_w64_r32x2_pf2", float, 4, 16, 32, 2, false, 2),
+    TDSE_VARIANT(1, 2, "f32_t2_w64_r32x2_pf3", float, 4, 16, 32, 2, false, 3),
     TDSE_VARIANT(1, 2, "f32_t2_w64_r32x1_pf2", float, 4, 16, 32, 1, false, 2),
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x2_pf2", float, 2, 16, 32, 2, true, 2),
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x1_pf2", float, 2, 16, 32, 1, true, 2),
-    TDSE_VARIANT(2, 2, "k32_t2_w64_r28x2_pf1", float, 4, 16, 28, 2, true, 1),
+    TDSE_VARIANT(2, 2, "k32_t2_w64_r32x2_pf1", float, 4, 16, 32, 2, true, 1),
+    TDSE_VARIANT(2, 2, "k32_t2_w64_r28x2_pf2", float, 4, 16, 28, 2, true, 2),
     TDSE_VARIANT(2, 2, "k32_t2_w64_r24x1_pf2", float, 4, 16, 24, 1, true, 2),
     TDSE_VARIANT(0, 1, "f64_t1_w64_r16x2_pf1_b2", double, 2, 32, 16, 2, false, 1, 2),
     TDSE_VARIANT(0, 1, "f64_t1_w64_r16x1_pf2", double, 2, 32, 16, 1, false, 2),
-    TDSE_VARIANT(0, 1, "f64_t1_w64_r32x4_pf1", double, 2, 32, 32, 4, false, 1),
 };
 
 const Variant *find_variant(int precision, int tsteps, int variant)

@@ -7,7 +7,7 @@ Tolerances (written here, used by every case):
                    |Q_gpu - Q_oracle| / Q_oracle <= 1e-5;
   fused vs unfused and batched vs solo: bitwise equal (same arithmetic, same order).
 Small grids span several tiles with ragged tails in x, y and z (default tiles are
-56 x 20 in FP32 T=1, 56 x 28 in FP32 T=2, 56 x 24 in Kahan T=2, 60 x 12 in FP64;
+56 x 20 in FP32 T=1, 56 x 24 in FP32 and Kahan T=2, 60 x 12 in FP64;
 z-chunks are chosen per launch).
 """
 import math
