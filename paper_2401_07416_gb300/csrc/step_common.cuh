@@ -1,0 +1,236 @@
+// Device helpers shared by the fused-step kernels: mbarrier and TMA wrappers,
+// vector shared/global access, correctly rounded and paired FP32 arithmetic,
+// the compile-time kernel shape and the per-item scalars.
+#pragma once
+
+#include "tdse_internal.cuh"
+
+namespace tdse {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per barrier wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait: false if the phase did not complete within kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <typename Real>
+struct VecOf;
+template <>
+struct VecOf<float> {
+    typedef float4 type;
+    static constexpr int N = 4;
+};
+template <>
+struct VecOf<double> {
+    typedef double2 type;
+    static constexpr int N = 2;
+};
+
+template <typename Real>
+__device__ __forceinline__ void ld_vec(const Real *p, Real (&v)[VecOf<Real>::N]);
+template <>
+__device__ __forceinline__ void ld_vec<float>(const float *p, float (&v)[4])
+{
+    float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void ld_vec<double>(const double *p, double (&v)[2])
+{
+    double2 t = *reinterpret_cast<const double2 *>(p);
+    v[0] = t.x; v[1] = t.y;
+}
+template <typename Real>
+__device__ __forceinline__ void st_vec(Real *p, const Real (&v)[VecOf<Real>::N]);
+template <>
+__device__ __forceinline__ void st_vec<float>(float *p, const float (&v)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st_vec<double>(double *p, const double (&v)[2])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+
+// Rounded product that the compiler may not fuse into a following add: the
+// absorbing factor must round identically whether its product is stored
+// (one step per launch) or consumed in registers (several steps per launch).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// Paired FP32 arithmetic (one instruction for two lanes, each lane rounded to
+// nearest exactly as the scalar operation).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// Compile-time shape of one fused-step kernel.
+//   H     half-step stages per launch (2T)
+//   TPX   threads across a region row (VEC cells each)
+//   ROWS  region rows; each thread owns RPT consecutive rows
+//   PF    planes loaded ahead of use
+template <typename Real_, int H_, int TPX_, int ROWS_, int RPT_, bool KAHAN_, int PF_, int MINB_ = 1>
+struct Cfg {
+    typedef Real_ Real;
+    static constexpr int H = H_, TPX = TPX_, ROWS = ROWS_, RPT = RPT_, PF = PF_;
+    static constexpr int MINB = MINB_;                  // CTAs resident per SM
+    static constexpr bool KAHAN = KAHAN_;
+    static constexpr int VEC = VecOf<Real>::N;
+    static constexpr int W = VEC * TPX;                 // region width (elements)
+    static constexpr int AX = 16 / static_cast<int>(sizeof(Real));
+    static constexpr int HX = (H + AX - 1) / AX * AX;   // x halo, TMA-aligned
+    static constexpr int TX = W - 2 * HX;
+    static constexpr int TY = ROWS - 2 * H;
+    static constexpr int NT = TPX * ROWS / RPT;
+    static constexpr int RW = 32 / TPX * RPT;           // rows per warp
+    static constexpr int PLANE = W * ROWS;
+    static constexpr int PLANE_BYTES = PLANE * static_cast<int>(sizeof(Real));
+    static constexpr int NFC = KAHAN ? 2 : 1;           // a field (and its compensation) per slot
+    static constexpr int NR = PF + 3;                   // R ring: read up to two planes back
+    static constexpr int NI = PF + 2;                   // I ring: read one plane back
+    static constexpr int ND = PF + H + 1;               // d is read H planes back
+    static constexpr int NB = PF + 1;
+    static constexpr int NSB = 2 * (H - 1);             // stage planes, double-buffered
+    static constexpr int NPLANES = (NR + NI) * NFC + ND + NSB;
+    static constexpr size_t SMEM = static_cast<size_t>(NPLANES) * PLANE_BYTES + 8 * NB + 128;
+    static constexpr uint32_t TX_BYTES = PLANE_BYTES * (2 * NFC + 1);
+    static_assert(TPX <= 32 && 32 % TPX == 0, "a region row must sit inside one warp");
+    static_assert(ROWS % RPT == 0, "rows per thread must divide the region");
+    static_assert(TX > 0 && TY > 0, "halo larger than region");
+    static_assert(W <= 256 && ROWS <= 256, "TMA box dimension limit");
+    static_assert(H % 2 == 0, "whole time steps only");
+    static_assert(SMEM <= 232448, "more than 227 KB of shared memory per CTA");
+    static_assert(MINB * (SMEM + 1024) <= 233472, "CTAs per SM exceed the shared memory");
+};
+
+// One row of an FP32 stage update in paired instructions: the increment
+// delta = A f = cx (f[x-1] + f[x+1]) + cy (f[y-1] + f[y+1]) + cz (f[z-1] + f[z+1]) + d f
+// at the row's VEC cells, then out = acc + delta (odd stage, Eq. 9) or
+// out = acc - delta (even stage, Eq. 8).  With KAHAN the accumulation carries the
+// compensation term: odd: y = delta - c, t = acc + y, c' = (t - acc) - y;
+// even (increment -delta): with y' = delta + c = -y exactly, t = acc - y',
+// c' = (t - acc) + y'.  Only the x-neighbour sum, whose operands are shifted by
+// one lane, is scalar.  xl / xr are the row's outer x neighbours, ylo / yhi the
+// rows below / above.
+template <bool KAHAN, int VEC>
+__device__ __forceinline__ void update_row_f32(bool odd, const float (&c)[VEC], float xl, float xr,
+                                               const float (&ylo)[VEC], const float (&yhi)[VEC],
+                                               const float (&zm)[VEC], const float (&zp)[VEC],
+                                               const float (&dd)[VEC], const float (&acc)[VEC],
+                                               const float (&cacc)[VEC], float2 cx2, float2 cy2,
+                                               float2 cz2, float (&out)[VEC], float (&cout)[VEC])
+{
+    auto pr = [](const float *a, int i) { return make_float2(a[i], a[i + 1]); };
+#pragma unroll
+    for (int v = 0; v < VEC; v += 2) {
+        const float2 sx = make_float2((v == 0 ? xl : c[v - 1]) + c[v + 1],
+                                      c[v] + (v + 2 == VEC ? xr : c[v + 2]));
+        const float2 sy = add2(pr(ylo, v), pr(yhi, v));
+        const float2 sz = add2(pr(zm, v), pr(zp, v));
+        float2 delta = mul2(pr(dd, v), pr(c, v));
+        delta = fma2(cz2, sz, delta);
+        delta = fma2(cy2, sy, delta);
+        delta = fma2(cx2, sx, delta);
+        const float2 a = pr(acc, v);
+        float2 o;
+        if constexpr (KAHAN) {
+            const float2 ca = pr(cacc, v);
+            float2 co;
+            if (odd) {
+                const float2 y = sub2(delta, ca);
+                o = add2(a, y);
+                co = sub2(sub2(o, a), y);
+            } else {
+                const float2 y = add2(delta, ca);
+                o = sub2(a, y);
+                co = add2(sub2(o, a), y);
+            }
+            cout[v] = co.x;
+            cout[v + 1] = co.y;
+        } else {
+            o = odd ? add2(a, delta) : sub2(a, delta);
+        }
+        out[v] = o.x;
+        out[v + 1] = o.y;
+    }
+}
+
+// Per-item scalars staged in shared memory by thread 0.
+struct ItemScalars {
+    void *outR, *outI, *outCR, *outCI, *mask;
+    double *flux, *jlast;
+    long long plane, pitch;
+    double cx, cy, cz, cj, dt;
+    int m, tile_x, tile_y, kz0, kz1, nx, ny, nz, G;
+    int per_x, per_y, per_z, det_k, mask_lo, mask_hi;
+};
+
+}  // namespace
+}  // namespace tdse

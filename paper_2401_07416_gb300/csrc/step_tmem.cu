@@ -1,0 +1,607 @@
+// Fused leapfrog step with the stage windows in tensor memory (arXiv 2401.07416,
+// Sec. 2.1, Eqs. 8-9), FP32 and FP32 + Kahan.
+//
+// Same schedule and arithmetic as fused_step_kernel: a CTA marches an xy tile
+// along z and runs the 2T half-step stages of T fused time steps as a pipeline,
+// stage s on plane p - s while plane p arrives by TMA.  The difference is where
+// the three-plane windows (old q-1, center q, new q+1) of the intermediate
+// fields F_1 .. F_{2T-1}, and of their Kahan compensation terms, are kept: in
+// tensor memory (TMEM: 128 lanes x 512 columns of 32 bits per SM, beside the
+// register file) instead of registers.  A window value is only ever read back
+// by the thread that wrote it, which is TMEM's access pattern: warp w reaches
+// lanes 32 (w mod 4) .. 32 (w mod 4) + 31, and warps sharing a lane quadrant use
+// disjoint column ranges.  Registers then hold only one stage's temporaries, so
+// a CTA runs one tile row per thread with twice the warps of the register-window
+// kernel.  The phase of each window (which of its three slots is old, center,
+// new) is a runtime column offset, so the z-march needs no unrolling.
+//
+// The newest plane of a window (the stage output just computed) is used by the
+// next stage straight from registers; old and center planes come from TMEM
+// (tcgen05.ld, then tcgen05.wait::ld).  Stores of new planes (tcgen05.st) are
+// waited for once per iteration, before any load that could read them.
+#include <type_traits>
+
+#include "step_common.cuh"
+
+namespace tdse {
+namespace {
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before_sync()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_after_sync()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Four consecutive columns of this thread's lane.
+__device__ __forceinline__ void tmem_st4(uint32_t addr, const float (&v)[4])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+                 "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t addr, float (&v)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"(addr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Values loaded by tcgen05.ld may only be read after tcgen05.wait::ld; passing
+// them through an empty volatile asm after the wait orders every later use.
+__device__ __forceinline__ void after_wait(float (&v)[4])
+{
+    asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]));
+}
+
+// TMEM footprint of a configuration.
+template <class C>
+struct TmemShape {
+    static constexpr int NW = C::NT / 32;                    // warps
+    static constexpr int NF = C::H - 1;                      // windowed fields F_1 .. F_{H-1}
+    static constexpr int NCMP = C::KAHAN ? 2 : 1;            // value (and compensation)
+    static constexpr int SLOT = C::RPT * C::VEC;             // columns of one window plane
+    static constexpr int THREAD_COLS = NF * 3 * NCMP * SLOT; // one thread's windows
+    static constexpr int QUAD_COLS = ((NW + 3) / 4) * THREAD_COLS;   // warps w, w+4, ... share a quadrant
+    static constexpr uint32_t NCOLS = QUAD_COLS <= 32 ? 32 : QUAD_COLS <= 64 ? 64
+                                    : QUAD_COLS <= 128 ? 128 : QUAD_COLS <= 256 ? 256 : 512;
+    static_assert(QUAD_COLS <= 512, "windows exceed tensor memory");
+    // CTAs that shared memory and the thread limit let share an SM must fit in TMEM
+    // together (an allocation that cannot be met would wait for another CTA to exit)
+    static constexpr int MAX_RESIDENT_SMEM = 233472 / static_cast<int>(C::SMEM + 1024);
+    static constexpr int MAX_RESIDENT_THREADS = 2048 / C::NT;
+    static constexpr int MAX_RESIDENT = MAX_RESIDENT_SMEM < MAX_RESIDENT_THREADS ? MAX_RESIDENT_SMEM
+                                                                                 : MAX_RESIDENT_THREADS;
+    static_assert(MAX_RESIDENT * NCOLS <= 512, "co-resident CTAs exceed tensor memory");
+    static_assert(sizeof(typename C::Real) == 4, "TMEM windows are for FP32 fields");
+    static_assert(C::H >= 2, "at least one full step per launch");
+};
+
+template <class C>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    fused_step_tmem_kernel(const MemberDev *__restrict__ members, const WorkDev *__restrict__ work,
+                           int *counter, int *status, int in_buf)
+{
+    typedef float Real;
+    typedef TmemShape<C> TS;
+    constexpr int H = C::H, VEC = C::VEC, W = C::W, ROWS = C::ROWS, PLANE = C::PLANE;
+    constexpr int RPT = C::RPT, NB = C::NB, PF = C::PF, NR = C::NR, NI = C::NI, ND = C::ND;
+    constexpr int SLOT = C::NFC * PLANE;    // one ring slot: a field (and its compensation)
+    constexpr int OFF_C = PLANE;            // compensation term within a slot
+
+    extern __shared__ unsigned char smem_raw[];
+    Real *ringA = reinterpret_cast<Real *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    Real *ringI = ringA + NR * SLOT;
+    Real *ringD = ringI + NI * SLOT;
+    Real *sbuf = ringD + ND * PLANE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sbuf + C::NSB * PLANE);
+    __shared__ int s_item;
+    __shared__ int s_abort;
+    __shared__ uint32_t s_tmem;
+    __shared__ ItemScalars S;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int qx = tid % C::TPX;
+    const int r0 = (tid / C::TPX) * RPT;                 // first region row of this thread
+    const int warp_row0 = warp * C::RW;
+    const int own = r0 * W + qx * VEC;                   // row r of this thread: own + r * W
+    const int off_ym = (r0 > 0 ? r0 - 1 : r0) * W + qx * VEC;
+    const int off_yp = (r0 + RPT < ROWS ? r0 + RPT : r0 + RPT - 1) * W + qx * VEC;
+
+    if (warp == 0) tmem_alloc(&s_tmem, TS::NCOLS);
+    if (tid == 0) {
+        for (int b = 0; b < NB; ++b) mbar_init(&bars[b], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    // this thread's lane and column range: lane quadrant warp % 4, column group warp / 4
+    const uint32_t tbase = s_tmem + ((static_cast<uint32_t>(warp & 3) * 32u) << 16) +
+                           static_cast<uint32_t>(warp >> 2) * TS::THREAD_COLS;
+    // column of window plane k (0..2) of field f (F_{f+1}), value (0) or compensation (1)
+    auto tcol = [&](int f, int k, int cmp) {
+        return tbase + static_cast<uint32_t>(((f * 3 + k) * TS::NCMP + cmp) * TS::SLOT);
+    };
+
+    long long gbase = 0;   // loads issued by this CTA before the current item
+
+    for (;;) {
+        if (tid == 0) {
+            const int it_ = atomicAdd(counter, 1);
+            s_item = it_;
+            if (it_ < work->total) {
+                int mm = 0;
+                while (it_ >= work->item_begin[mm + 1]) ++mm;
+                const MemberDev &Mm = members[mm];
+                const int local = it_ - work->item_begin[mm];
+                const int ntx = work->tiles_x[mm], nty = work->tiles_y[mm];
+                S.m = mm;
+                S.tile_x = local % ntx;
+                S.tile_y = (local / ntx) % nty;
+                S.kz0 = (local / (ntx * nty)) * work->chunk[mm];
+                S.kz1 = min(S.kz0 + work->chunk[mm], Mm.nz);
+                S.nx = Mm.nx; S.ny = Mm.ny; S.nz = Mm.nz; S.G = Mm.G;
+                S.per_x = Mm.per_x; S.per_y = Mm.per_y; S.per_z = Mm.per_z;
+                S.det_k = Mm.det_k; S.mask_lo = Mm.mask_lo; S.mask_hi = Mm.mask_hi;
+                S.pitch = Mm.pitch; S.plane = Mm.plane;
+                S.cx = Mm.cx; S.cy = Mm.cy; S.cz = Mm.cz; S.cj = Mm.cj; S.dt = Mm.dt;
+                S.mask = Mm.mask; S.flux = Mm.flux; S.jlast = Mm.jlast;
+                S.outR = Mm.R[1 - in_buf]; S.outI = Mm.I[1 - in_buf];
+                S.outCR = Mm.cR[1 - in_buf]; S.outCI = Mm.cI[1 - in_buf];
+            }
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= work->total) break;
+        const MemberDev &M = members[S.m];   // tensor maps only (thread 0)
+        const int tile_x = S.tile_x, tile_y = S.tile_y, kz0 = S.kz0, kz1 = S.kz1;
+        const int L0 = kz0 - H;
+        const int nit = (kz1 - kz0) + 2 * H;
+        const int G = S.G, nx = S.nx, ny = S.ny, nz = S.nz;
+        const int bx = G + tile_x * C::TX - C::HX;
+        const int by = G + tile_y * C::TY - H;
+        const int xs = tile_x * C::TX - C::HX + qx * VEC;
+        const int ys0 = tile_y * C::TY - H + r0;
+        const bool zper = S.per_z != 0;
+        const int mlo = S.mask_lo, mhi = nz - S.mask_hi;
+        const float cxs = static_cast<float>(S.cx), cys = static_cast<float>(S.cy),
+                    czs = static_cast<float>(S.cz);
+        const float2 cx2 = make_float2(cxs, cxs), cy2 = make_float2(cys, cys),
+                     cz2 = make_float2(czs, czs);
+        const Real *maskz = reinterpret_cast<const Real *>(S.mask);
+        const int kd = S.det_k;
+        const bool flux_owner = kd >= kz0 && kd < kz1;
+
+        auto inside = [&](int r, int v) {
+            return (S.per_x || (xs + v >= 0 && xs + v < nx)) && (S.per_y || (ys0 + r >= 0 && ys0 + r < ny));
+        };
+        bool walls = false;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) walls |= !inside(r, v);
+        const bool col_in = qx * VEC >= C::HX && qx * VEC < C::HX + C::TX && xs < nx;
+        bool store_row[RPT];
+        bool any_store = false;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            store_row[r] = col_in && r0 + r >= H && r0 + r < H + C::TY && ys0 + r < ny;
+            any_store |= store_row[r];
+        }
+        const long long pitch = S.pitch;
+        const bool seam = (S.per_x && (xs < G || xs >= nx - G)) ||
+                          (S.per_y && (ys0 < G || ys0 + RPT - 1 >= ny - G));
+        Real *outR = reinterpret_cast<Real *>(S.outR);
+        Real *outI = reinterpret_cast<Real *>(S.outI);
+        Real *outCR = reinterpret_cast<Real *>(S.outCR);
+        Real *outCI = reinterpret_cast<Real *>(S.outCI);
+        const long long out0 = static_cast<long long>(ys0 + G) * pitch + (xs + G);
+
+        // Windows start at zero (planes before the first computed one), as in the
+        // register-window kernel.
+        {
+            float zero[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int f = 0; f < TS::NF; ++f)
+                for (int k = 0; k < 3; ++k)
+                    for (int cmp = 0; cmp < TS::NCMP; ++cmp)
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) tmem_st4(tcol(f, k, cmp) + r * VEC, zero);
+            tmem_wait_st();
+        }
+
+        const bool tile_walls = __syncthreads_or(walls) != 0;
+        const int fast_lo = mlo + H;
+        const int fast_hi = zper ? mhi + 1 : min(mhi + 1, nz);
+
+        int headA = 0, headI = 0, headD = 0;
+        int headB = static_cast<int>(gbase % NB);
+        uint32_t phase = static_cast<uint32_t>((gbase / NB) & 1);
+
+        auto issue = [&](int l, int ahead) {
+            const int L = L0 + l;
+            const int zc = zper ? ((L % nz) + nz) % nz : L;
+            int b = headB + ahead; if (b >= NB) b -= NB;
+            int a = headA + ahead; if (a >= NR) a -= NR;
+            int i = headI + ahead; if (i >= NI) i -= NI;
+            int d = headD + ahead; if (d >= ND) d -= ND;
+            uint64_t *bar = &bars[b];
+            Real *slotR = ringA + a * SLOT;
+            Real *slotI = ringI + i * SLOT;
+            mbar_arrive_expect_tx(bar, C::TX_BYTES);
+            tma_load_3d(slotR, &M.tm_R[in_buf], bx, by, zc, bar);
+            tma_load_3d(slotI, &M.tm_I[in_buf], bx, by, zc, bar);
+            if constexpr (C::KAHAN) {
+                tma_load_3d(slotR + OFF_C, &M.tm_cR[in_buf], bx, by, zc, bar);
+                tma_load_3d(slotI + OFF_C, &M.tm_cI[in_buf], bx, by, zc, bar);
+            }
+            tma_load_3d(ringD + d * PLANE, &M.tm_d, bx, by, zc, bar);
+        };
+
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int l = 0; l < PF && l < nit; ++l) issue(l, l);
+        }
+        int issued = min(PF, nit);
+        int waited = 0;
+
+        auto stages = [&](const int it, const int p, const int K0, const int K1, const int K2,
+                          const Real *A0, const Real *A1, const Real *A2, const Real *I1,
+                          const Real *sb_prev, Real *sb_cur, auto FASTc) {
+            constexpr bool FAST = decltype(FASTc)::value;
+            const bool p_out = !FAST && !zper && (p < 0 || p >= nz);
+            Real zmR[RPT][VEC];    // R at plane p-2: stage 1's z- neighbour, stage 2's accumulator
+            Real prev[RPT][VEC];   // the previous stage's output: this stage's z+ neighbour
+#pragma unroll
+            for (int s = 1; s <= H; ++s) {
+                if (!FAST && it < 2 * s) continue;                            // pipeline filling
+                if (warp_row0 + C::RW <= s || warp_row0 >= ROWS - s) continue;  // rows outside the cone
+                const int q = p - s;
+                const bool odd = (s & 1) != 0;
+                bool q_out = false, absorb = false;
+                Real mq = 1.f;
+                if constexpr (!FAST) {
+                    q_out = !zper && (q < 0 || q >= nz);
+                    int qm = q;
+                    if (zper) {
+                        qm = q % nz;
+                        if (qm < 0) qm += nz;
+                    }
+                    absorb = !q_out && (qm < mlo || qm >= mhi);
+                    if (absorb) mq = maskz[qm];
+                }
+                int dslot = headD - s;
+                if (dslot < 0) dslot += ND;
+                const Real *Dp = ringD + dslot * PLANE;
+
+                Real zm[RPT][VEC], c[RPT][VEC], zp[RPT][VEC], ym[VEC], yp[VEC], dd[RPT][VEC];
+                Real acc[RPT][VEC], cacc[RPT][VEC];
+                if (s == 1) {
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        ld_vec<Real>(A2 + own + r * W, zmR[r]);
+                        ld_vec<Real>(A1 + own + r * W, c[r]);
+                        ld_vec<Real>(A0 + own + r * W, zp[r]);
+                        ld_vec<Real>(I1 + own + r * W, acc[r]);
+                        if constexpr (C::KAHAN) ld_vec<Real>(I1 + OFF_C + own + r * W, cacc[r]);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            zm[r][v] = zmR[r][v];
+                            if (p_out) zp[r][v] = 0.f;
+                        }
+                    }
+                    ld_vec<Real>(A1 + off_ym, ym);
+                    ld_vec<Real>(A1 + off_yp, yp);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        tmem_ld4(tcol(s - 2, K0, 0) + r * VEC, zm[r]);
+                        tmem_ld4(tcol(s - 2, K1, 0) + r * VEC, c[r]);
+                        if (s >= 3) {
+                            tmem_ld4(tcol(s - 3, K0, 0) + r * VEC, acc[r]);
+                            if constexpr (C::KAHAN) tmem_ld4(tcol(s - 3, K0, 1) + r * VEC, cacc[r]);
+                        }
+                    }
+                    const Real *Sp = sb_prev + (s - 2) * 2 * PLANE;
+                    ld_vec<Real>(Sp + off_ym, ym);
+                    ld_vec<Real>(Sp + off_yp, yp);
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) zp[r][v] = prev[r][v];
+                        if (s == 2) {
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) acc[r][v] = zmR[r][v];
+                            if constexpr (C::KAHAN) ld_vec<Real>(A2 + OFF_C + own + r * W, cacc[r]);
+                        }
+                    }
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        after_wait(zm[r]);
+                        after_wait(c[r]);
+                        if (s >= 3) {
+                            after_wait(acc[r]);
+                            if constexpr (C::KAHAN) after_wait(cacc[r]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) ld_vec<Real>(Dp + own + r * W, dd[r]);
+
+                if (s >= 3 && odd && absorb) {   // I of the previous step carries its absorbing factor
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            acc[r][v] = mul_rn(acc[r][v], mq);
+                            if constexpr (C::KAHAN) cacc[r][v] = mul_rn(cacc[r][v], mq);
+                        }
+                }
+
+                Real out[RPT][VEC], cout[RPT][VEC];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const Real xl = __shfl_up_sync(kFull, c[r][VEC - 1], 1);
+                    const Real xr = __shfl_down_sync(kFull, c[r][0], 1);
+                    update_row_f32<C::KAHAN, VEC>(odd, c[r], xl, xr, r == 0 ? ym : c[r - 1],
+                                                  r == RPT - 1 ? yp : c[r + 1], zm[r], zp[r], dd[r],
+                                                  acc[r], cacc[r], cx2, cy2, cz2, out[r], cout[r]);
+                }
+                if (!odd && absorb) {   // Eq. 8 step complete: absorbing factor on R
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            out[r][v] = mul_rn(out[r][v], mq);
+                            if constexpr (C::KAHAN) cout[r][v] = mul_rn(cout[r][v], mq);
+                        }
+                }
+                if constexpr (!FAST) {
+                    if (walls || q_out) {
+                        const Real zq = q_out ? 0.f : 1.f;
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) {
+                                const Real keep = inside(r, v) ? 1.f : 0.f;
+                                out[r][v] *= keep * zq;
+                                if constexpr (C::KAHAN) cout[r][v] *= keep * zq;
+                            }
+                    }
+
+                    // detector flux of step (s+1)/2: R^n at planes kd, kd+1 and the new I
+                    if (odd && s < H && flux_owner && q == kd + 1) {
+                        Real ilo[RPT][VEC];   // I at plane kd: the previous output of stage s
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) tmem_ld4(tcol(s - 1, K1, 0) + r * VEC, ilo[r]);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) after_wait(ilo[r]);
+                        if (any_store) {
+#pragma unroll
+                            for (int r = 0; r < RPT; ++r) {
+                                if (!store_row[r]) continue;
+                                const int pix = (ys0 + r) * nx + xs;
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) {
+                                    const double j = S.cj * (static_cast<double>(zm[r][v]) * out[r][v] -
+                                                             static_cast<double>(c[r][v]) * ilo[r][v]);
+                                    S.flux[pix + v] += j * S.dt;
+                                    if (s == H - 1) S.jlast[pix + v] = j;
+                                }
+                            }
+                        }
+                    }
+                }
+
+                if (s < H) {
+                    Real *So = sb_cur + (s - 1) * 2 * PLANE;
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        tmem_st4(tcol(s - 1, K2, 0) + r * VEC, out[r]);
+                        if constexpr (C::KAHAN) tmem_st4(tcol(s - 1, K2, 1) + r * VEC, cout[r]);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) prev[r][v] = out[r][v];
+                        if (r == 0 || r == RPT - 1) st_vec<Real>(So + own + r * W, out[r]);
+                    }
+                } else {
+                    // I of the last step: the center of F_{H-1}'s window
+                    Real vi[RPT][VEC];
+                    Real vci[C::KAHAN ? RPT : 1][VEC];
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        tmem_ld4(tcol(H - 2, K1, 0) + r * VEC, vi[r]);
+                        if constexpr (C::KAHAN) tmem_ld4(tcol(H - 2, K1, 1) + r * VEC, vci[r]);
+                    }
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        after_wait(vi[r]);
+                        if constexpr (C::KAHAN) after_wait(vci[r]);
+                    }
+                    if (any_store && (FAST || (q >= kz0 && q < kz1))) {
+                        const long long zoff = static_cast<long long>(q) * S.plane;
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) {
+                            if (!store_row[r]) continue;
+                            if (absorb) {
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) {
+                                    vi[r][v] = mul_rn(vi[r][v], mq);
+                                    if constexpr (C::KAHAN) vci[r][v] = mul_rn(vci[r][v], mq);
+                                }
+                            }
+                            const long long o = zoff + out0 + r * pitch;
+                            st_vec<Real>(outR + o, out[r]);
+                            st_vec<Real>(outI + o, vi[r]);
+                            if constexpr (C::KAHAN) {
+                                st_vec<Real>(outCR + o, cout[r]);
+                                st_vec<Real>(outCI + o, vci[r]);
+                            }
+                            if (seam) {   // ghost copies of periodic axes (both sides if n < 2G)
+                                const int y = ys0 + r;
+                                int dxs[3] = {0, 0, 0}, dys[3] = {0, 0, 0};
+                                int ndx = 1, ndy = 1;
+                                if (S.per_x) {
+                                    if (xs < G) dxs[ndx++] = nx;
+                                    if (xs >= nx - G) dxs[ndx++] = -nx;
+                                }
+                                if (S.per_y) {
+                                    if (y < G) dys[ndy++] = ny;
+                                    if (y >= ny - G) dys[ndy++] = -ny;
+                                }
+                                for (int a = 0; a < ndy; ++a)
+                                    for (int b = 0; b < ndx; ++b) {
+                                        if (a == 0 && b == 0) continue;
+                                        const long long og = o + dys[a] * pitch + dxs[b];
+                                        st_vec<Real>(outR + og, out[r]);
+                                        st_vec<Real>(outI + og, vi[r]);
+                                        if constexpr (C::KAHAN) {
+                                            st_vec<Real>(outCR + og, cout[r]);
+                                            st_vec<Real>(outCI + og, vci[r]);
+                                        }
+                                    }
+                            }
+                        }
+                    }
+                }
+            }
+        };
+
+        int ph = 0;   // it % 3: window slot of the old plane
+        for (int it = 0; it < nit; ++it) {
+            const int p = L0 + it;
+            if (tid == 0) {
+                if (mbar_wait_bounded(&bars[headB], phase)) {
+                    waited = it + 1;
+                } else {
+                    atomicOr(status, 1);
+                    s_abort = 1;
+                }
+            }
+            __syncthreads();   // plane p has landed; the previous iteration's reads are done
+            if (s_abort) break;
+            if (it + PF < nit) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(it + PF, PF);
+                }
+                issued = it + PF + 1;
+            }
+            tmem_wait_st();   // the previous iteration's window planes are in TMEM
+            const Real *A0 = ringA + headA * SLOT;
+            const Real *A1 = ringA + (headA >= 1 ? headA - 1 : headA - 1 + NR) * SLOT;
+            const Real *A2 = ringA + (headA >= 2 ? headA - 2 : headA - 2 + NR) * SLOT;
+            const Real *I1 = ringI + (headI >= 1 ? headI - 1 : headI - 1 + NI) * SLOT;
+            const Real *sb_prev = sbuf + ((it - 1) & 1) * PLANE;
+            Real *sb_cur = sbuf + (it & 1) * PLANE;
+            const int K0 = ph, K1 = ph == 2 ? 0 : ph + 1, K2 = ph == 0 ? 2 : ph - 1;
+            const bool fast = !tile_walls && it >= 2 * H && p >= fast_lo && p < fast_hi &&
+                              !(flux_owner && p >= kd + 2 && p <= kd + H);
+            if (fast)
+                stages(it, p, K0, K1, K2, A0, A1, A2, I1, sb_prev, sb_cur, std::true_type{});
+            else
+                stages(it, p, K0, K1, K2, A0, A1, A2, I1, sb_prev, sb_cur, std::false_type{});
+            headA = headA + 1 == NR ? 0 : headA + 1;
+            headI = headI + 1 == NI ? 0 : headI + 1;
+            headD = headD + 1 == ND ? 0 : headD + 1;
+            headB = headB + 1 == NB ? 0 : headB + 1;
+            if (headB == 0) phase ^= 1u;
+            ph = ph == 2 ? 0 : ph + 1;
+        }
+
+        if (s_abort) {
+            // wait (bounded) for the loads still in flight, then leave (freeing TMEM below)
+            if (tid == 0) {
+                for (int l = waited; l < issued; ++l) {
+                    const long long g = gbase + l;
+                    mbar_wait_bounded(&bars[g % NB], static_cast<uint32_t>((g / NB) & 1));
+                }
+            }
+            __syncthreads();
+            break;
+        }
+        gbase += nit;
+        tmem_wait_st();
+        __syncthreads();
+    }
+
+    tmem_wait_st();
+    tmem_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(s_tmem, TS::NCOLS);
+}
+
+template <class C>
+cudaError_t launch_tmem_cfg(const StepLaunch &L)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(fused_step_tmem_kernel<C>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(C::SMEM));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    fused_step_tmem_kernel<C><<<L.grid, C::NT, C::SMEM, L.stream>>>(L.members, L.work, L.counter,
+                                                                    L.status, L.in_buf);
+    return cudaGetLastError();
+}
+
+template <class C>
+void fill_tmem_config(StepConfig *cfg)
+{
+    cfg->tile_x = C::TX;
+    cfg->tile_y = C::TY;
+    cfg->box_x = C::W;
+    cfg->box_y = C::ROWS;
+    cfg->threads = C::NT;
+    cfg->smem = C::SMEM;
+    cfg->ctas_per_sm = C::MINB;
+}
+
+}  // namespace
+
+#define TDSE_TMEM_VARIANT(FN, ...)                                                      \
+    cudaError_t launch_##FN(const StepLaunch &L) { return launch_tmem_cfg<Cfg<__VA_ARGS__>>(L); } \
+    void fill_##FN(StepConfig *cfg) { fill_tmem_config<Cfg<__VA_ARGS__>>(cfg); }
+
+// Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched>
+TDSE_TMEM_VARIANT(tmem_k32_t2_r32x1_pf1, float, 4, 16, 32, 1, true, 1)
+TDSE_TMEM_VARIANT(tmem_k32_t2_r28x1_pf2, float, 4, 16, 28, 1, true, 2)
+TDSE_TMEM_VARIANT(tmem_k32_t2_r32x2_pf1, float, 4, 16, 32, 2, true, 1)
+TDSE_TMEM_VARIANT(tmem_f32_t2_r32x1_pf2, float, 4, 16, 32, 1, false, 2)
+TDSE_TMEM_VARIANT(tmem_f32_t2_r32x2_pf2, float, 4, 16, 32, 2, false, 2)
+
+}  // namespace tdse

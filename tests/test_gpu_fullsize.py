@@ -70,8 +70,8 @@ def test_graphs_and_autotuned_variants_bitwise_equal_direct_launches(T):
         got = run(T, wl, T.FP32_KAHAN, 50, **kw)
         for a, b in zip(got[:3], ref[:3]):
             assert np.array_equal(a, b)
-    # every variant of every depth, set explicitly
-    for prec in (T.FP32, T.FP64):
+    # every variant of every depth, set explicitly (register- and TMEM-window kernels)
+    for prec in (T.FP32, T.FP32_KAHAN, T.FP64):
         base = None
         for tb in (1, 2):
             if prec == T.FP64 and tb == 2:

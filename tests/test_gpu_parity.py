@@ -227,3 +227,26 @@ def test_unstable_run_reports_status(T):
         s.step(200)
     s.close()
     assert e.value.status == T.EUNSTABLE
+
+
+@pytest.mark.parametrize("precision", ["FP32", "FP32_KAHAN"])
+@pytest.mark.parametrize("name", ["walls", "mixed", "short"])
+def test_every_two_step_variant_bitwise_equal(T, name, precision):
+    """Register-window and tensor-memory-window kernels, every tile shape: the same
+    arithmetic in the same order, so states and flux maps agree bit for bit."""
+    g, V, p = case(name, seed=5)
+    prec = getattr(T, precision)
+    ref = None
+    for v in range(T.tdse_variant_count(prec, 2)):
+        s = make_sim(g, prec, 2)
+        T.tdse_set_variant(s.ctx, 2, v)
+        s.set_potential(0, V)
+        s.set_packet(0, p)
+        s.step(14)
+        got = (*s.state(0), s.flux_map(0))
+        s.close()
+        if ref is None:
+            ref = got
+            continue
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), (name, precision, v)
