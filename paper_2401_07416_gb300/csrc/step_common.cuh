@@ -136,7 +136,10 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 //   TPX   threads across a region row (VEC cells each)
 //   ROWS  region rows; each thread owns RPT consecutive rows
 //   PF    planes loaded ahead of use
-template <typename Real_, int H_, int TPX_, int ROWS_, int RPT_, bool KAHAN_, int PF_, int MINB_ = 1>
+//   DSTASH  d is copied out of shared memory as each plane lands (tensor-memory
+//           kernel), so its ring only covers the planes in flight
+template <typename Real_, int H_, int TPX_, int ROWS_, int RPT_, bool KAHAN_, int PF_, int MINB_ = 1,
+          bool DSTASH_ = false>
 struct Cfg {
     typedef Real_ Real;
     static constexpr int H = H_, TPX = TPX_, ROWS = ROWS_, RPT = RPT_, PF = PF_;
@@ -155,7 +158,8 @@ struct Cfg {
     static constexpr int NFC = KAHAN ? 2 : 1;           // a field (and its compensation) per slot
     static constexpr int NR = PF + 3;                   // R ring: read up to two planes back
     static constexpr int NI = PF + 2;                   // I ring: read one plane back
-    static constexpr int ND = PF + H + 1;               // d is read H planes back
+    static constexpr bool DSTASH = DSTASH_;
+    static constexpr int ND = DSTASH ? PF + 1 : PF + H + 1;   // d is read H planes back
     static constexpr int NB = PF + 1;
     static constexpr int NSB = 2 * (H - 1);             // stage planes, double-buffered
     static constexpr int NPLANES = (NR + NI) * NFC + ND + NSB;

@@ -31,11 +31,12 @@ namespace tdse {
 #define TDSE_TMEM_DECL(FN)                        \
     cudaError_t launch_##FN(const StepLaunch &L); \
     void fill_##FN(StepConfig *cfg);
-TDSE_TMEM_DECL(tmem_k32_t2_r32x1_pf1)
+TDSE_TMEM_DECL(tmem_k32_t2_r32x1_pf2)
 TDSE_TMEM_DECL(tmem_k32_t2_r28x1_pf2)
-TDSE_TMEM_DECL(tmem_k32_t2_r32x2_pf1)
-TDSE_TMEM_DECL(tmem_f32_t2_r32x1_pf2)
 TDSE_TMEM_DECL(tmem_f32_t2_r32x2_pf2)
+TDSE_TMEM_DECL(tmem_f32_t2_r32x1_pf3)
+TDSE_TMEM_DECL(tmem_f32_t2_r32x1_pf4)
+TDSE_TMEM_DECL(tmem_k32_t2_r28x1_pf3)
 #undef TDSE_TMEM_DECL
 
 namespace {
@@ -548,27 +549,25 @@ struct Variant {
 #define TDSE_VARIANT(P, T, NAME, ...)                                                      \
     Variant{P, T, NAME, &fill_config<Cfg<__VA_ARGS__>>, &launch_cfg<Cfg<__VA_ARGS__>>}
 
-// Kernel variants per (precision, fused steps).
-// Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched, CTAs per SM>
+// Kernel variants per (precision, fused steps): register-window kernels
+// (TDSE_VARIANT: Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan,
+// planes prefetched, CTAs per SM>) and tensor-memory-window kernels (step_tmem.cu).
 // Measured on GB300 (512x512x1024 slab): the first entry of each (precision, steps)
 // group is the fastest and the default; the others remain for the autotuner.
 const Variant kVariants[] = {
     TDSE_VARIANT(1, 1, "f32_t1_w64_r24x2_pf2_b2", float, 2, 16, 24, 2, false, 2, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w64_r48x2_pf2", float, 2, 16, 48, 2, false, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w128_r24x2_pf2", float, 2, 32, 24, 2, false, 2),
-    TDSE_VARIANT(1, 2, "f32_t2_w64_r32x2_pf2", float, 4, 16, 32, 2, false, 2),
-    TDSE_VARIANT(1, 2, "f32_t2_w64_r32x2_pf3", float, 4, 16, 32, 2, false, 3),
-    TDSE_VARIANT(1, 2, "f32_t2_w64_r32x1_pf2", float, 4, 16, 32, 1, false, 2),
-    Variant{1, 2, "f32_t2_tmem_r32x1_pf2", &fill_tmem_f32_t2_r32x1_pf2, &launch_tmem_f32_t2_r32x1_pf2},
+    Variant{1, 2, "f32_t2_tmem_r32x1_pf4", &fill_tmem_f32_t2_r32x1_pf4, &launch_tmem_f32_t2_r32x1_pf4},
+    Variant{1, 2, "f32_t2_tmem_r32x1_pf3", &fill_tmem_f32_t2_r32x1_pf3, &launch_tmem_f32_t2_r32x1_pf3},
     Variant{1, 2, "f32_t2_tmem_r32x2_pf2", &fill_tmem_f32_t2_r32x2_pf2, &launch_tmem_f32_t2_r32x2_pf2},
+    TDSE_VARIANT(1, 2, "f32_t2_w64_r32x2_pf2", float, 4, 16, 32, 2, false, 2),
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x2_pf2", float, 2, 16, 32, 2, true, 2),
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x1_pf2", float, 2, 16, 32, 1, true, 2),
     Variant{2, 2, "k32_t2_tmem_r28x1_pf2", &fill_tmem_k32_t2_r28x1_pf2, &launch_tmem_k32_t2_r28x1_pf2},
+    Variant{2, 2, "k32_t2_tmem_r32x1_pf2", &fill_tmem_k32_t2_r32x1_pf2, &launch_tmem_k32_t2_r32x1_pf2},
+    Variant{2, 2, "k32_t2_tmem_r28x1_pf3", &fill_tmem_k32_t2_r28x1_pf3, &launch_tmem_k32_t2_r28x1_pf3},
     TDSE_VARIANT(2, 2, "k32_t2_w64_r32x2_pf1", float, 4, 16, 32, 2, true, 1),
-    TDSE_VARIANT(2, 2, "k32_t2_w64_r28x2_pf2", float, 4, 16, 28, 2, true, 2),
-    TDSE_VARIANT(2, 2, "k32_t2_w64_r24x1_pf2", float, 4, 16, 24, 1, true, 2),
-    Variant{2, 2, "k32_t2_tmem_r32x1_pf1", &fill_tmem_k32_t2_r32x1_pf1, &launch_tmem_k32_t2_r32x1_pf1},
-    Variant{2, 2, "k32_t2_tmem_r32x2_pf1", &fill_tmem_k32_t2_r32x2_pf1, &launch_tmem_k32_t2_r32x2_pf1},
     TDSE_VARIANT(0, 1, "f64_t1_w64_r16x2_pf1_b2", double, 2, 32, 16, 2, false, 1, 2),
     TDSE_VARIANT(0, 1, "f64_t1_w64_r16x1_pf2", double, 2, 32, 16, 1, false, 2),
 };

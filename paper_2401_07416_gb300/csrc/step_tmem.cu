@@ -88,7 +88,9 @@ struct TmemShape {
     static constexpr int NF = C::H - 1;                      // windowed fields F_1 .. F_{H-1}
     static constexpr int NCMP = C::KAHAN ? 2 : 1;            // value (and compensation)
     static constexpr int SLOT = C::RPT * C::VEC;             // columns of one window plane
-    static constexpr int THREAD_COLS = NF * 3 * NCMP * SLOT; // one thread's windows
+    static constexpr int NDT = C::H + 2;                     // d planes kept (p .. p-H, one spare)
+    static constexpr int WIN_COLS = NF * 3 * NCMP * SLOT;    // one thread's windows
+    static constexpr int THREAD_COLS = WIN_COLS + NDT * SLOT;
     static constexpr int QUAD_COLS = ((NW + 3) / 4) * THREAD_COLS;   // warps w, w+4, ... share a quadrant
     static constexpr uint32_t NCOLS = QUAD_COLS <= 32 ? 32 : QUAD_COLS <= 64 ? 64
                                     : QUAD_COLS <= 128 ? 128 : QUAD_COLS <= 256 ? 256 : 512;
@@ -102,6 +104,7 @@ struct TmemShape {
     static_assert(MAX_RESIDENT * NCOLS <= 512, "co-resident CTAs exceed tensor memory");
     static_assert(sizeof(typename C::Real) == 4, "TMEM windows are for FP32 fields");
     static_assert(C::H >= 2, "at least one full step per launch");
+    static_assert(C::DSTASH, "the tensor-memory kernel keeps d in TMEM");
 };
 
 template <class C>
@@ -153,6 +156,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     auto tcol = [&](int f, int k, int cmp) {
         return tbase + static_cast<uint32_t>(((f * 3 + k) * TS::NCMP + cmp) * TS::SLOT);
     };
+    // column of the d plane kept in slot j (0 .. NDT-1)
+    auto dcol = [&](int j) { return tbase + static_cast<uint32_t>(TS::WIN_COLS + j * TS::SLOT); };
 
     long long gbase = 0;   // loads issued by this CTA before the current item
 
@@ -276,8 +281,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         int waited = 0;
 
         auto stages = [&](const int it, const int p, const int K0, const int K1, const int K2,
-                          const Real *A0, const Real *A1, const Real *A2, const Real *I1,
-                          const Real *sb_prev, Real *sb_cur, auto FASTc) {
+                          const int dj, const Real *A0, const Real *A1, const Real *A2,
+                          const Real *I1, const Real *sb_prev, Real *sb_cur, auto FASTc) {
             constexpr bool FAST = decltype(FASTc)::value;
             const bool p_out = !FAST && !zper && (p < 0 || p >= nz);
             Real zmR[RPT][VEC];    // R at plane p-2: stage 1's z- neighbour, stage 2's accumulator
@@ -300,12 +305,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     absorb = !q_out && (qm < mlo || qm >= mhi);
                     if (absorb) mq = maskz[qm];
                 }
-                int dslot = headD - s;
-                if (dslot < 0) dslot += ND;
-                const Real *Dp = ringD + dslot * PLANE;
+                int dk = dj - s;   // TMEM slot of d at plane q
+                if (dk < 0) dk += TS::NDT;
 
                 Real zm[RPT][VEC], c[RPT][VEC], zp[RPT][VEC], ym[VEC], yp[VEC], dd[RPT][VEC];
                 Real acc[RPT][VEC], cacc[RPT][VEC];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) tmem_ld4(dcol(dk) + r * VEC, dd[r]);
                 if (s == 1) {
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
@@ -322,6 +328,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     }
                     ld_vec<Real>(A1 + off_ym, ym);
                     ld_vec<Real>(A1 + off_yp, yp);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) after_wait(dd[r]);
                 } else {
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
@@ -348,6 +357,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     tmem_wait_ld();
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
+                        after_wait(dd[r]);
                         after_wait(zm[r]);
                         after_wait(c[r]);
                         if (s >= 3) {
@@ -356,9 +366,6 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                         }
                     }
                 }
-#pragma unroll
-                for (int r = 0; r < RPT; ++r) ld_vec<Real>(Dp + own + r * W, dd[r]);
-
                 if (s >= 3 && odd && absorb) {   // I of the previous step carries its absorbing factor
 #pragma unroll
                     for (int r = 0; r < RPT; ++r)
@@ -500,6 +507,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         };
 
         int ph = 0;   // it % 3: window slot of the old plane
+        int dj = 0;   // it % NDT: TMEM slot of d at plane p
         for (int it = 0; it < nit; ++it) {
             const int p = L0 + it;
             if (tid == 0) {
@@ -520,6 +528,16 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 issued = it + PF + 1;
             }
             tmem_wait_st();   // the previous iteration's window planes are in TMEM
+            {
+                // d at plane p moves to TMEM slot dj; its shared-memory slot is free
+                // again once every thread has copied it (next iteration's barrier)
+                Real dp[RPT][VEC];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    ld_vec<Real>(ringD + headD * PLANE + own + r * W, dp[r]);
+                    tmem_st4(dcol(dj) + r * VEC, dp[r]);
+                }
+            }
             const Real *A0 = ringA + headA * SLOT;
             const Real *A1 = ringA + (headA >= 1 ? headA - 1 : headA - 1 + NR) * SLOT;
             const Real *A2 = ringA + (headA >= 2 ? headA - 2 : headA - 2 + NR) * SLOT;
@@ -530,15 +548,16 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             const bool fast = !tile_walls && it >= 2 * H && p >= fast_lo && p < fast_hi &&
                               !(flux_owner && p >= kd + 2 && p <= kd + H);
             if (fast)
-                stages(it, p, K0, K1, K2, A0, A1, A2, I1, sb_prev, sb_cur, std::true_type{});
+                stages(it, p, K0, K1, K2, dj, A0, A1, A2, I1, sb_prev, sb_cur, std::true_type{});
             else
-                stages(it, p, K0, K1, K2, A0, A1, A2, I1, sb_prev, sb_cur, std::false_type{});
+                stages(it, p, K0, K1, K2, dj, A0, A1, A2, I1, sb_prev, sb_cur, std::false_type{});
             headA = headA + 1 == NR ? 0 : headA + 1;
             headI = headI + 1 == NI ? 0 : headI + 1;
             headD = headD + 1 == ND ? 0 : headD + 1;
             headB = headB + 1 == NB ? 0 : headB + 1;
             if (headB == 0) phase ^= 1u;
             ph = ph == 2 ? 0 : ph + 1;
+            dj = dj + 1 == TS::NDT ? 0 : dj + 1;
         }
 
         if (s_abort) {
@@ -597,11 +616,13 @@ void fill_tmem_config(StepConfig *cfg)
     cudaError_t launch_##FN(const StepLaunch &L) { return launch_tmem_cfg<Cfg<__VA_ARGS__>>(L); } \
     void fill_##FN(StepConfig *cfg) { fill_tmem_config<Cfg<__VA_ARGS__>>(cfg); }
 
-// Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched>
-TDSE_TMEM_VARIANT(tmem_k32_t2_r32x1_pf1, float, 4, 16, 32, 1, true, 1)
-TDSE_TMEM_VARIANT(tmem_k32_t2_r28x1_pf2, float, 4, 16, 28, 1, true, 2)
-TDSE_TMEM_VARIANT(tmem_k32_t2_r32x2_pf1, float, 4, 16, 32, 2, true, 1)
-TDSE_TMEM_VARIANT(tmem_f32_t2_r32x1_pf2, float, 4, 16, 32, 1, false, 2)
-TDSE_TMEM_VARIANT(tmem_f32_t2_r32x2_pf2, float, 4, 16, 32, 2, false, 2)
+// Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched, CTAs per SM,
+//     d kept in TMEM>
+TDSE_TMEM_VARIANT(tmem_k32_t2_r32x1_pf2, float, 4, 16, 32, 1, true, 2, 1, true)
+TDSE_TMEM_VARIANT(tmem_k32_t2_r28x1_pf2, float, 4, 16, 28, 1, true, 2, 1, true)
+TDSE_TMEM_VARIANT(tmem_f32_t2_r32x2_pf2, float, 4, 16, 32, 2, false, 2, 1, true)
+TDSE_TMEM_VARIANT(tmem_f32_t2_r32x1_pf3, float, 4, 16, 32, 1, false, 3, 1, true)
+TDSE_TMEM_VARIANT(tmem_f32_t2_r32x1_pf4, float, 4, 16, 32, 1, false, 4, 1, true)
+TDSE_TMEM_VARIANT(tmem_k32_t2_r28x1_pf3, float, 4, 16, 28, 1, true, 3, 1, true)
 
 }  // namespace tdse
