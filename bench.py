@@ -56,7 +56,9 @@ def parse():
     ap.add_argument("--precision", default="kahan", choices=["kahan", "fp32", "fp64"])
     ap.add_argument("--tblock", type=int, default=0, help="steps fused per launch (0: autotuned)")
     ap.add_argument("--ncu-case", action="store_true", help="mid-size run of the fused kernel for ncu")
-    ap.add_argument("--variant", type=int, default=0, help="kernel variant for --ncu-case")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="kernel variant (with --tblock) instead of the autotuner's pick; "
+                         "--ncu-case default 0")
     ap.add_argument("--no-extras", action="store_true", help="skip variants, e2e and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -130,10 +132,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+KERNEL_SOURCES = ("step_common.cuh", "step_kernels.cu", "step_tmem.cu")
+
+
 def kernel_source_hash() -> str:
-    """Hash of the fused-step kernel source the traffic figures were taken on."""
-    with open(os.path.join(ROOT, "paper_2401_07416_gb300", "csrc", "step_kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the fused-step kernel sources the traffic figures were taken on."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2401_07416_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(variant: str, cells: int):
@@ -289,7 +297,7 @@ def ncu_case(args):
                mask_hi=20, det_k=180, obs_every=10 ** 6)
     atoms = W.square_slab(8, 4, 1.6, 0.4 * 25.6, 12.8, 12.8, W.rng_for(5), 0.05)
     with Sim(g, precision=prec, tblock=tb) as s:
-        T.tdse_set_variant(s.ctx, tb, args.variant)
+        T.tdse_set_variant(s.ctx, tb, args.variant or 0)
         s.set_atoms(0, atoms)
         s.set_packet(0, W.Packet((6.4, 6.4, 12.74), (0.0, 0.0, 2.0), (0.0, 0.0, -1.9)))
         s.step(2 * tb)
@@ -377,8 +385,14 @@ def main():
     cells = g.cells
     hbm_peak, peak_kind = measured_peaks()
 
-    # headline: the fused step on the full grid, autotuned on it
-    s = make_ctx(T, wl, prec, tblock)
+    # headline: the fused step on the full grid, autotuned on it (or a fixed variant,
+    # e.g. to profile exactly the kernel a plain run picks)
+    fixed = args.variant is not None
+    if fixed and tblock == 0:
+        tblock = 2
+    s = make_ctx(T, wl, prec, tblock, autotune=not fixed)
+    if fixed:
+        T.tdse_set_variant(s.ctx, tblock, args.variant)
     tuning = s.tuning()
     V_dev = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
     T.tdse_get_potential(s.ctx, 0, V_dev)
@@ -405,7 +419,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS hbm_gbs)",
-                "kernel": f"fused_step_kernel {variant} ({tb} steps per launch)",
+                "kernel": f"{'fused_step_tmem_kernel' if 'tmem' in variant else 'fused_step_kernel'} "
+                          f"{variant} ({tb} steps per launch)",
                 "algorithmic_bytes_per_launch": bytes_launch,
                 "bytes_per_node_per_launch": BYTES_PER_NODE[prec],
                 "avg_launch_ms": launch_ms, "launches": prof["step_launches"],
