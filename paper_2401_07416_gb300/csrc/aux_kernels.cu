@@ -423,62 +423,144 @@ struct ColumnSum<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
-template <typename Real>
-__global__ void observables_kernel(MemberDev m, int buf, double *__restrict__ partials)
+// Sums of the detector flux map (last step and time-integrated) over this
+// block's share of the pixels.
+__device__ __forceinline__ void flux_partials(const MemberDev &m, double &fl, double &fi)
+{
+    if (m.det_k < 0) return;
+    const long long npix = static_cast<long long>(m.nx) * m.ny;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < npix;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        fl += m.jlast[i];
+        fi += m.flux[i];
+    }
+}
+
+__device__ __forceinline__ void write_partials(double *partials, double *sh, double q, double pn,
+                                               double e, double fl, double fi)
+{
+    const double v[5] = {q, pn, e, fl, fi};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double t = block_sum(v[k], sh);
+        if (threadIdx.x == 0) partials[kObsPartialsPerBlock * blockIdx.x + k] = t;
+    }
+}
+
+// Q, paper norm and energy numerator over (column group, z-chunk) items: each
+// thread marches a chunk of kObsZ planes of V adjacent (x, y) columns (one 16-byte
+// vector per field and plane) with a three-plane window and accumulates the chunk
+// in ColumnSum.  Items go to threads in a fixed order and the block count is fixed
+// by the grid shape, so the sums are reproducible.  V = 1 is the scalar form for
+// rows whose length is not a multiple of the vector width.
+template <typename Real, int V>
+__global__ void __launch_bounds__(kObsThreads)
+    observables_kernel(MemberDev m, int buf, double *__restrict__ partials)
 {
     __shared__ double sh[32];
     const Real *__restrict__ R = reinterpret_cast<const Real *>(m.R[buf]);
     const Real *__restrict__ I = reinterpret_cast<const Real *>(m.I[buf]);
     const Real *__restrict__ D = reinterpret_cast<const Real *>(m.d);
-    const long long ncol = static_cast<long long>(m.nx) * m.ny;
+    const int ngx = m.nx / V;
+    const long long ngrp = static_cast<long long>(ngx) * m.ny;
+    const int nch = (m.nz + kObsZ - 1) / kObsZ;
+    const long long nitems = ngrp * nch;
     const Real cx = static_cast<Real>(m.cx), cy = static_cast<Real>(m.cy),
                cz = static_cast<Real>(m.cz);
     const long long plane = m.plane, pitch = m.pitch;
-    double q = 0.0, pn = 0.0, e = 0.0;
-    for (long long col = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; col < ncol;
-         col += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(col % m.nx), y = static_cast<int>(col / m.nx);
-        const long long base = static_cast<long long>(y + m.G) * pitch + (x + m.G);
-        const long long last = base + static_cast<long long>(m.nz - 1) * plane;
-        Real rm = m.per_z ? R[last] : Real(0), im = m.per_z ? I[last] : Real(0);
-        Real rc = R[base], ic = I[base];
-        ColumnSum<Real> sq, sp, se;
-        for (int z = 0; z < m.nz; ++z) {
-            const long long o = base + static_cast<long long>(z) * plane;
-            Real rp, ip;
-            if (z + 1 < m.nz) {
-                rp = R[o + plane];
-                ip = I[o + plane];
+    auto ld = [](const Real *p, Real (&v)[V]) {
+        if constexpr (V * sizeof(Real) == 16) {
+            if constexpr (sizeof(Real) == 4) {
+                const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+                v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
             } else {
-                rp = m.per_z ? R[base] : Real(0);
-                ip = m.per_z ? I[base] : Real(0);
+                const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+                v[0] = t.x; v[1] = t.y;
             }
-            const Real d = D[o];
-            const Real ar = fma(cx, R[o + 1] + R[o - 1],
-                                fma(cy, R[o + pitch] + R[o - pitch], fma(cz, rm + rp, d * rc)));
-            const Real ai = fma(cx, I[o + 1] + I[o - 1],
-                                fma(cy, I[o + pitch] + I[o - pitch], fma(cz, im + ip, d * ic)));
-            const Real ipl = ic + ar;
-            sq.add(rc * rc + ipl * ic);
-            sp.add(rc * rc + ic * ic);
-            se.add(rc * ar + ipl * ai);
-            rm = rc;
-            rc = rp;
-            im = ic;
-            ic = ip;
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[k] = __ldg(p + k);
+        }
+    };
+    double q = 0.0, pn = 0.0, e = 0.0;
+    for (long long item = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+         item < nitems; item += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long grp = item % ngrp;
+        const int z0 = static_cast<int>(item / ngrp) * kObsZ;
+        const int z1 = min(z0 + kObsZ, m.nz);
+        const int x0 = static_cast<int>(grp % ngx) * V, y = static_cast<int>(grp / ngx);
+        const long long base = static_cast<long long>(y + m.G) * pitch + (x0 + m.G);
+        const long long last = base + static_cast<long long>(m.nz - 1) * plane;
+        Real rm[V], rc[V], im[V], ic[V];
+        if (z0 > 0) {
+            ld(R + base + static_cast<long long>(z0 - 1) * plane, rm);
+            ld(I + base + static_cast<long long>(z0 - 1) * plane, im);
+        } else if (m.per_z) {
+            ld(R + last, rm);
+            ld(I + last, im);
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) rm[k] = im[k] = Real(0);
+        }
+        ld(R + base + static_cast<long long>(z0) * plane, rc);
+        ld(I + base + static_cast<long long>(z0) * plane, ic);
+        ColumnSum<Real> sq, sp, se;
+        // one plane at offset o, its z+1 neighbours given
+        auto plane_terms = [&](long long o, const Real (&rp)[V], const Real (&ip)[V]) {
+            Real d[V], ryp[V], rym[V], iyp[V], iym[V];
+            ld(D + o, d);
+            ld(R + o + pitch, ryp);
+            ld(R + o - pitch, rym);
+            ld(I + o + pitch, iyp);
+            ld(I + o - pitch, iym);
+            const Real rxl = __ldg(R + o - 1), rxr = __ldg(R + o + V);
+            const Real ixl = __ldg(I + o - 1), ixr = __ldg(I + o + V);
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const Real rsx = (k == 0 ? rxl : rc[k - 1]) + (k == V - 1 ? rxr : rc[k + 1]);
+                const Real isx = (k == 0 ? ixl : ic[k - 1]) + (k == V - 1 ? ixr : ic[k + 1]);
+                const Real ar = fma(cx, rsx, fma(cy, ryp[k] + rym[k], fma(cz, rm[k] + rp[k], d[k] * rc[k])));
+                const Real ai = fma(cx, isx, fma(cy, iyp[k] + iym[k], fma(cz, im[k] + ip[k], d[k] * ic[k])));
+                const Real ipl = ic[k] + ar;
+                sq.add(rc[k] * rc[k] + ipl * ic[k]);
+                sp.add(rc[k] * rc[k] + ic[k] * ic[k]);
+                se.add(rc[k] * ar + ipl * ai);
+            }
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                rm[k] = rc[k];
+                rc[k] = rp[k];
+                im[k] = ic[k];
+                ic[k] = ip[k];
+            }
+        };
+        const int zin = min(z1, m.nz - 1);   // planes whose z+1 neighbour lies in the grid
+#pragma unroll 2
+        for (int z = z0; z < zin; ++z) {
+            const long long o = base + static_cast<long long>(z) * plane;
+            Real rp[V], ip[V];
+            ld(R + o + plane, rp);
+            ld(I + o + plane, ip);
+            plane_terms(o, rp, ip);
+        }
+        if (z1 == m.nz) {   // top plane: periodic wrap or wall
+            Real rp[V], ip[V];
+            if (m.per_z) {
+                ld(R + base, rp);
+                ld(I + base, ip);
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) rp[k] = ip[k] = Real(0);
+            }
+            plane_terms(last, rp, ip);
         }
         q += sq.value();
         pn += sp.value();
         e += se.value();
     }
-    const double sq = block_sum(q, sh);
-    const double sp = block_sum(pn, sh);
-    const double se = block_sum(e, sh);
-    if (threadIdx.x == 0) {
-        partials[3 * blockIdx.x + 0] = sq;
-        partials[3 * blockIdx.x + 1] = sp;
-        partials[3 * blockIdx.x + 2] = se;
-    }
+    double fl = 0.0, fi = 0.0;
+    flux_partials(m, fl, fi);
+    write_partials(partials, sh, q, pn, e, fl, fi);
 }
 
 // record = {step, Q, norm_paper, energy, flux_last, flux_integrated}; sets
@@ -488,24 +570,14 @@ __global__ void observables_finalize_kernel(MemberDev m, const double *__restric
                                             int *status, double q_ref, long long step)
 {
     __shared__ double sh[32];
-    double q = 0.0, pn = 0.0, e = 0.0, fl = 0.0, fi = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        q += partials[3 * i + 0];
-        pn += partials[3 * i + 1];
-        e += partials[3 * i + 2];
-    }
-    const long long npix = static_cast<long long>(m.nx) * m.ny;
-    if (m.det_k >= 0)
-        for (long long i = threadIdx.x; i < npix; i += blockDim.x) {
-            fl += m.jlast[i];
-            fi += m.flux[i];
-        }
-    q = block_sum(q, sh);
-    pn = block_sum(pn, sh);
-    e = block_sum(e, sh);
-    fl = block_sum(fl, sh);
-    fi = block_sum(fi, sh);
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[k] += partials[kObsPartialsPerBlock * i + k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = block_sum(v[k], sh);
     if (threadIdx.x == 0) {
+        const double q = v[0], pn = v[1], e = v[2], fl = v[3], fi = v[4];
         const double h3 = m.hx * m.hy * m.hz;
         const double hxy = m.hx * m.hy;
         record[0] = static_cast<double>(step);
@@ -632,13 +704,19 @@ cudaError_t launch_observables(const MemberDev &m, int precision, int buf, doubl
                                double *record, int *status, double q_ref, long long step,
                                cudaStream_t s)
 {
-    const long long ncol = static_cast<long long>(m.nx) * m.ny;
-    const int threads = 128;
-    const int nparts = static_cast<int>(std::min<long long>((ncol + threads - 1) / threads, kObsParts));
-    if (precision == 0)
-        observables_kernel<double><<<nparts, threads, 0, s>>>(m, buf, partials);
-    else
-        observables_kernel<float><<<nparts, threads, 0, s>>>(m, buf, partials);
+    const int vec = precision == 0 ? 2 : 4;          // one 16-byte vector per field and plane
+    const bool vector = m.nx % vec == 0;
+    const long long groups = static_cast<long long>(vector ? m.nx / vec : m.nx) * m.ny;
+    const long long nitems = groups * ((m.nz + kObsZ - 1) / kObsZ);
+    const int nparts = static_cast<int>(
+        std::max<long long>(1, std::min<long long>((nitems + kObsThreads - 1) / kObsThreads, kObsParts)));
+    if (precision == 0) {
+        if (vector) observables_kernel<double, 2><<<nparts, kObsThreads, 0, s>>>(m, buf, partials);
+        else observables_kernel<double, 1><<<nparts, kObsThreads, 0, s>>>(m, buf, partials);
+    } else {
+        if (vector) observables_kernel<float, 4><<<nparts, kObsThreads, 0, s>>>(m, buf, partials);
+        else observables_kernel<float, 1><<<nparts, kObsThreads, 0, s>>>(m, buf, partials);
+    }
     observables_finalize_kernel<<<1, kThreads, 0, s>>>(m, partials, nparts, record, status, q_ref,
                                                        step);
     return cudaGetLastError();

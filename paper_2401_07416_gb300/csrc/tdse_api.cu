@@ -360,7 +360,8 @@ tdse_status ensure_device(tdse_ctx *c)
     void *p;
     TRY(dalloc(c, sizeof(int), &p)); c->d_counter = static_cast<int *>(p);
     TRY(dalloc(c, sizeof(int), &p)); c->d_status = static_cast<int *>(p);
-    TRY(dalloc(c, kObsParts * 3 * sizeof(double), &p)); c->d_partials = static_cast<double *>(p);
+    TRY(dalloc(c, kObsParts * kObsPartialsPerBlock * sizeof(double), &p));
+    c->d_partials = static_cast<double *>(p);
     TRY(dalloc(c, sizeof(double), &p)); c->d_scale = static_cast<double *>(p);
     TRY(dalloc(c, c->m.size() * kRecCap * kRecLen * sizeof(double), &p));
     c->d_records = static_cast<double *>(p);
