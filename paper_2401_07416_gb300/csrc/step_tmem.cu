@@ -88,8 +88,9 @@ struct TmemShape {
     static constexpr int NF = C::H - 1;                      // windowed fields F_1 .. F_{H-1}
     static constexpr int NCMP = C::KAHAN ? 2 : 1;            // value (and compensation)
     static constexpr int SLOT = C::RPT * C::VEC;             // columns of one window plane
-    static constexpr int NDT = C::H + 2;                     // d planes kept (p .. p-H, one spare)
-    static constexpr int WIN_COLS = NF * 3 * NCMP * SLOT;    // one thread's windows
+    static constexpr int NDT = C::H + 2 <= 8 ? 8 : 16;      // d planes kept (p .. p-H), a power of two
+    static constexpr int PHASE_COLS = NF * NCMP * SLOT;      // one window plane of every field
+    static constexpr int WIN_COLS = 3 * PHASE_COLS;          // one thread's windows
     static constexpr int THREAD_COLS = WIN_COLS + NDT * SLOT;
     static constexpr int QUAD_COLS = ((NW + 3) / 4) * THREAD_COLS;   // warps w, w+4, ... share a quadrant
     static constexpr uint32_t NCOLS = QUAD_COLS <= 32 ? 32 : QUAD_COLS <= 64 ? 64
@@ -152,12 +153,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     // this thread's lane and column range: lane quadrant warp % 4, column group warp / 4
     const uint32_t tbase = s_tmem + ((static_cast<uint32_t>(warp & 3) * 32u) << 16) +
                            static_cast<uint32_t>(warp >> 2) * TS::THREAD_COLS;
-    // column of window plane k (0..2) of field f (F_{f+1}), value (0) or compensation (1)
-    auto tcol = [&](int f, int k, int cmp) {
-        return tbase + static_cast<uint32_t>(((f * 3 + k) * TS::NCMP + cmp) * TS::SLOT);
-    };
-    // column of the d plane kept in slot j (0 .. NDT-1)
-    auto dcol = [&](int j) { return tbase + static_cast<uint32_t>(TS::WIN_COLS + j * TS::SLOT); };
+    // Column layout of a thread: window plane k (0..2) of every field first (k
+    // outermost, so one base address per phase serves all fields), then the d ring.
+    // Within a phase: field f (F_{f+1}), value (0) or compensation (1).
+    auto fcol = [](int f, int cmp) { return static_cast<uint32_t>((f * TS::NCMP + cmp) * TS::SLOT); };
+    auto pbase = [&](int k) { return tbase + static_cast<uint32_t>(k * TS::PHASE_COLS); };
+    const uint32_t dbase = tbase + TS::WIN_COLS;
+    auto dcol = [&](int j) { return dbase + static_cast<uint32_t>((j & (TS::NDT - 1)) * TS::SLOT); };
 
     long long gbase = 0;   // loads issued by this CTA before the current item
 
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 for (int k = 0; k < 3; ++k)
                     for (int cmp = 0; cmp < TS::NCMP; ++cmp)
 #pragma unroll
-                        for (int r = 0; r < RPT; ++r) tmem_st4(tcol(f, k, cmp) + r * VEC, zero);
+                        for (int r = 0; r < RPT; ++r) tmem_st4(pbase(k) + fcol(f, cmp) + r * VEC, zero);
             tmem_wait_st();
         }
 
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         int issued = min(PF, nit);
         int waited = 0;
 
-        auto stages = [&](const int it, const int p, const int K0, const int K1, const int K2,
+        auto stages = [&](const int it, const int p, const uint32_t K0, const uint32_t K1, const uint32_t K2,
                           const int dj, const Real *A0, const Real *A1, const Real *A2,
                           const Real *I1, const Real *sb_prev, Real *sb_cur, auto FASTc) {
             constexpr bool FAST = decltype(FASTc)::value;
@@ -305,13 +307,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     absorb = !q_out && (qm < mlo || qm >= mhi);
                     if (absorb) mq = maskz[qm];
                 }
-                int dk = dj - s;   // TMEM slot of d at plane q
-                if (dk < 0) dk += TS::NDT;
 
                 Real zm[RPT][VEC], c[RPT][VEC], zp[RPT][VEC], ym[VEC], yp[VEC], dd[RPT][VEC];
                 Real acc[RPT][VEC], cacc[RPT][VEC];
 #pragma unroll
-                for (int r = 0; r < RPT; ++r) tmem_ld4(dcol(dk) + r * VEC, dd[r]);
+                for (int r = 0; r < RPT; ++r) tmem_ld4(dcol(dj - s) + r * VEC, dd[r]);   // d at plane q
                 if (s == 1) {
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
@@ -334,11 +334,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 } else {
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
-                        tmem_ld4(tcol(s - 2, K0, 0) + r * VEC, zm[r]);
-                        tmem_ld4(tcol(s - 2, K1, 0) + r * VEC, c[r]);
+                        tmem_ld4(K0 + fcol(s - 2, 0) + r * VEC, zm[r]);
+                        tmem_ld4(K1 + fcol(s - 2, 0) + r * VEC, c[r]);
                         if (s >= 3) {
-                            tmem_ld4(tcol(s - 3, K0, 0) + r * VEC, acc[r]);
-                            if constexpr (C::KAHAN) tmem_ld4(tcol(s - 3, K0, 1) + r * VEC, cacc[r]);
+                            tmem_ld4(K0 + fcol(s - 3, 0) + r * VEC, acc[r]);
+                            if constexpr (C::KAHAN) tmem_ld4(K0 + fcol(s - 3, 1) + r * VEC, cacc[r]);
                         }
                     }
                     const Real *Sp = sb_prev + (s - 2) * 2 * PLANE;
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     if (odd && s < H && flux_owner && q == kd + 1) {
                         Real ilo[RPT][VEC];   // I at plane kd: the previous output of stage s
 #pragma unroll
-                        for (int r = 0; r < RPT; ++r) tmem_ld4(tcol(s - 1, K1, 0) + r * VEC, ilo[r]);
+                        for (int r = 0; r < RPT; ++r) tmem_ld4(K1 + fcol(s - 1, 0) + r * VEC, ilo[r]);
                         tmem_wait_ld();
 #pragma unroll
                         for (int r = 0; r < RPT; ++r) after_wait(ilo[r]);
@@ -436,8 +436,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     Real *So = sb_cur + (s - 1) * 2 * PLANE;
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
-                        tmem_st4(tcol(s - 1, K2, 0) + r * VEC, out[r]);
-                        if constexpr (C::KAHAN) tmem_st4(tcol(s - 1, K2, 1) + r * VEC, cout[r]);
+                        tmem_st4(K2 + fcol(s - 1, 0) + r * VEC, out[r]);
+                        if constexpr (C::KAHAN) tmem_st4(K2 + fcol(s - 1, 1) + r * VEC, cout[r]);
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) prev[r][v] = out[r][v];
                         if (r == 0 || r == RPT - 1) st_vec<Real>(So + own + r * W, out[r]);
@@ -448,8 +448,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     Real vci[C::KAHAN ? RPT : 1][VEC];
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
-                        tmem_ld4(tcol(H - 2, K1, 0) + r * VEC, vi[r]);
-                        if constexpr (C::KAHAN) tmem_ld4(tcol(H - 2, K1, 1) + r * VEC, vci[r]);
+                        tmem_ld4(K1 + fcol(H - 2, 0) + r * VEC, vi[r]);
+                        if constexpr (C::KAHAN) tmem_ld4(K1 + fcol(H - 2, 1) + r * VEC, vci[r]);
                     }
                     tmem_wait_ld();
 #pragma unroll
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         };
 
         int ph = 0;   // it % 3: window slot of the old plane
-        int dj = 0;   // it % NDT: TMEM slot of d at plane p
+        int dj = 0;   // TMEM slot of d at plane p (modulo NDT)
         for (int it = 0; it < nit; ++it) {
             const int p = L0 + it;
             if (tid == 0) {
@@ -544,7 +544,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             const Real *I1 = ringI + (headI >= 1 ? headI - 1 : headI - 1 + NI) * SLOT;
             const Real *sb_prev = sbuf + ((it - 1) & 1) * PLANE;
             Real *sb_cur = sbuf + (it & 1) * PLANE;
-            const int K0 = ph, K1 = ph == 2 ? 0 : ph + 1, K2 = ph == 0 ? 2 : ph - 1;
+            // TMEM bases of the old, center and new window planes at this phase
+            const uint32_t K0 = pbase(ph), K1 = pbase(ph == 2 ? 0 : ph + 1), K2 = pbase(ph == 0 ? 2 : ph - 1);
             const bool fast = !tile_walls && it >= 2 * H && p >= fast_lo && p < fast_hi &&
                               !(flux_owner && p >= kd + 2 && p <= kd + H);
             if (fast)
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             headB = headB + 1 == NB ? 0 : headB + 1;
             if (headB == 0) phase ^= 1u;
             ph = ph == 2 ? 0 : ph + 1;
-            dj = dj + 1 == TS::NDT ? 0 : dj + 1;
+            ++dj;   // slots are taken modulo NDT
         }
 
         if (s_abort) {
