@@ -12,6 +12,7 @@
 //   e. I = It - A R,  Q = Qt                                  (undo Eq. 9)
 // after which (R, I) = (R^n, I^{n-1/2}) and (P, Q) their adjoints.  Arrays are
 // unpadded [nz][ny][nx]; neighbours wrap on periodic axes and read zero on walls.
+#include <algorithm>
 #include <cmath>
 
 #include "tdse_internal.cuh"
@@ -25,6 +26,8 @@ struct Geo {
     int nx, ny, nz;
     int per[3];
     double cx, cy, cz, cv, c0;   // c0 = -2 (cx + cy + cz)
+    long long pitch, pplane;     // strides of the forward's padded arrays (d)
+    int G;                       // their ghost width
 };
 
 __device__ __forceinline__ long long cell(const Geo &g, int x, int y, int z)
@@ -50,32 +53,52 @@ __device__ __forceinline__ Real nb(const Real *f, const Geo &g, int x, int y, in
     return f[cell(g, x, y, z)];
 }
 
-// (A f)(x, y, z) with d = -2 (cx + cy + cz) - cv V rounded to Real like the forward step.
+// d = -2 (cx + cy + cz) - cv V at a cell, read from the forward step's own array so
+// that the reconstruction undoes exactly the forward's arithmetic.
 template <typename Real>
-__device__ __forceinline__ Real apply_A(const Real *f, const double *V, const Geo &g, int x, int y,
-                                        int z, long long o)
+__device__ __forceinline__ Real dval(const Real *__restrict__ D, const Geo &g, int x, int y, int z)
 {
-    const Real d = static_cast<Real>(g.c0 - g.cv * V[o]);
-    const Real sx = nb(f, g, x + 1, y, z) + nb(f, g, x - 1, y, z);
-    const Real sy = nb(f, g, x, y + 1, z) + nb(f, g, x, y - 1, z);
-    const Real sz = nb(f, g, x, y, z + 1) + nb(f, g, x, y, z - 1);
-    return fma(static_cast<Real>(g.cx), sx,
-               fma(static_cast<Real>(g.cy), sy, fma(static_cast<Real>(g.cz), sz, d * f[o])));
+    return D[static_cast<long long>(z) * g.pplane + static_cast<long long>(y + g.G) * g.pitch + (x + g.G)];
 }
+
+// (A f)(x, y, z), cell offset o: interior neighbours by offset, boundary ones through nb().
+template <typename Real>
+__device__ __forceinline__ Real apply_A(const Real *f, Real d, const Geo &g, int x, int y, int z,
+                                        long long o)
+{
+    const long long plane = static_cast<long long>(g.nx) * g.ny;
+    const Real xm = x > 0 ? f[o - 1] : nb(f, g, x - 1, y, z);
+    const Real xp = x + 1 < g.nx ? f[o + 1] : nb(f, g, x + 1, y, z);
+    const Real ym = y > 0 ? f[o - g.nx] : nb(f, g, x, y - 1, z);
+    const Real yp = y + 1 < g.ny ? f[o + g.nx] : nb(f, g, x, y + 1, z);
+    const Real zm = z > 0 ? f[o - plane] : nb(f, g, x, y, z - 1);
+    const Real zp = z + 1 < g.nz ? f[o + plane] : nb(f, g, x, y, z + 1);
+    return fma(static_cast<Real>(g.cx), xp + xm,
+               fma(static_cast<Real>(g.cy), yp + ym, fma(static_cast<Real>(g.cz), zp + zm, d * f[o])));
+}
+
+// The step kernels below run a 2-D grid: blockIdx.x * blockDim.x + threadIdx.x
+// is the cell (x, y) of a plane (32-bit index arithmetic), the planes are
+// blockIdx.y, blockIdx.y + gridDim.y, ...
 
 #define GRID_STRIDE(t, n)                                                                     \
     for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < (n); \
          t += static_cast<long long>(gridDim.x) * blockDim.x)
 
+// a. It = I'/M, Rt = R'/M, Pt = M P on the absorbing planes (M = 1 elsewhere):
+// blockIdx.y enumerates the mask_lo bottom and the mask_hi top planes.
 template <typename Real>
-__global__ void adj_unmask_kernel(Geo g, const double *__restrict__ M, Real *R, Real *I, Real *P)
+__global__ void adj_unmask_kernel(Geo g, int mask_lo, int mask_hi, const double *__restrict__ M,
+                                  Real *R, Real *I, Real *P)
 {
-    const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+    const int xy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (xy >= g.nx * g.ny) return;
     const long long plane = static_cast<long long>(g.nx) * g.ny;
-    GRID_STRIDE(t, n)
-    {
-        const double m = M[t / plane];
+    for (int j = blockIdx.y; j < mask_lo + mask_hi; j += gridDim.y) {
+        const int z = j < mask_lo ? j : g.nz - mask_hi + (j - mask_lo);
+        const double m = M[z];
         if (m != 1.0) {
+            const long long t = z * plane + xy;
             R[t] = static_cast<Real>(R[t] / m);
             I[t] = static_cast<Real>(I[t] / m);
             P[t] = static_cast<Real>(P[t] * m);
@@ -83,21 +106,23 @@ __global__ void adj_unmask_kernel(Geo g, const double *__restrict__ M, Real *R, 
     }
 }
 
+// b. R = Rt + A It (undo Eq. 8), Qt = M Q - A Pt (adjoint of Eq. 8)
 template <typename Real>
-__global__ void adj_b_kernel(Geo g, const double *__restrict__ M, const double *__restrict__ V,
+__global__ void adj_b_kernel(Geo g, const double *__restrict__ M, const Real *__restrict__ D,
                              Real *R, const Real *__restrict__ I, const Real *__restrict__ P, Real *Q)
 {
-    const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
-    GRID_STRIDE(t, n)
-    {
-        const int x = static_cast<int>(t % g.nx);
-        const int y = static_cast<int>((t / g.nx) % g.ny);
-        const int z = static_cast<int>(t / (static_cast<long long>(g.nx) * g.ny));
-        R[t] = R[t] + apply_A(I, V, g, x, y, z, t);
-        Q[t] = static_cast<Real>(M[z] * Q[t]) - apply_A(P, V, g, x, y, z, t);
+    const int xy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (xy >= g.nx * g.ny) return;
+    const int x = xy % g.nx, y = xy / g.nx;
+    for (int z = blockIdx.y; z < g.nz; z += gridDim.y) {
+        const long long o = cell(g, x, y, z);
+        const Real d = dval(D, g, x, y, z);
+        R[o] = R[o] + apply_A(I, d, g, x, y, z, o);
+        Q[o] = static_cast<Real>(M[z] * Q[o]) - apply_A(P, d, g, x, y, z, o);
     }
 }
 
+// c. the detector flux w.r.t. It
 template <typename Real>
 __global__ void adj_flux_q_kernel(Geo g, int kd, const double *__restrict__ w, const Real *R, Real *Q)
 {
@@ -110,41 +135,39 @@ __global__ void adj_flux_q_kernel(Geo g, int kd, const double *__restrict__ w, c
     }
 }
 
+// d. gV -= cv (Qt R - Pt It), P = Pt + A Qt + dj/dR (adjoint of Eq. 9)
 template <typename Real>
-__global__ void adj_d_kernel(Geo g, const double *__restrict__ V, int kd,
-                             const double *__restrict__ w, const Real *__restrict__ R,
-                             const Real *__restrict__ I, Real *P, const Real *__restrict__ Q,
-                             double *gV)
+__global__ void adj_d_kernel(Geo g, const Real *__restrict__ D, int kd, const double *__restrict__ w,
+                             const Real *__restrict__ R, const Real *__restrict__ I, Real *P,
+                             const Real *__restrict__ Q, double *gV)
 {
-    const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
     const long long plane = static_cast<long long>(g.nx) * g.ny;
-    GRID_STRIDE(t, n)
-    {
-        const int x = static_cast<int>(t % g.nx);
-        const int y = static_cast<int>((t / g.nx) % g.ny);
-        const int z = static_cast<int>(t / plane);
-        const Real pt = P[t];
-        gV[t] -= g.cv * (static_cast<double>(Q[t]) * R[t] - static_cast<double>(pt) * I[t]);
-        Real pn = pt + apply_A(Q, V, g, x, y, z, t);
+    const int xy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (xy >= g.nx * g.ny) return;
+    const int x = xy % g.nx, y = xy / g.nx;
+    for (int z = blockIdx.y; z < g.nz; z += gridDim.y) {
+        const long long o = cell(g, x, y, z);
+        const Real pt = P[o];
+        gV[o] -= g.cv * (static_cast<double>(Q[o]) * R[o] - static_cast<double>(pt) * I[o]);
+        Real pn = pt + apply_A(Q, dval(D, g, x, y, z), g, x, y, z, o);
         if (kd >= 0) {
-            const long long p = t % plane;
-            if (z == kd) pn += static_cast<Real>(w[p]) * I[t + plane];
-            else if (z == kd + 1) pn -= static_cast<Real>(w[p]) * I[t - plane];
+            if (z == kd) pn += static_cast<Real>(w[xy]) * I[o + plane];
+            else if (z == kd + 1) pn -= static_cast<Real>(w[xy]) * I[o - plane];
         }
-        P[t] = pn;
+        P[o] = pn;
     }
 }
 
+// e. I = It - A R (undo Eq. 9)
 template <typename Real>
-__global__ void adj_e_kernel(Geo g, const double *__restrict__ V, const Real *__restrict__ R, Real *I)
+__global__ void adj_e_kernel(Geo g, const Real *__restrict__ D, const Real *__restrict__ R, Real *I)
 {
-    const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
-    GRID_STRIDE(t, n)
-    {
-        const int x = static_cast<int>(t % g.nx);
-        const int y = static_cast<int>((t / g.nx) % g.ny);
-        const int z = static_cast<int>(t / (static_cast<long long>(g.nx) * g.ny));
-        I[t] = I[t] - apply_A(R, V, g, x, y, z, t);
+    const int xy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (xy >= g.nx * g.ny) return;
+    const int x = xy % g.nx, y = xy / g.nx;
+    for (int z = blockIdx.y; z < g.nz; z += gridDim.y) {
+        const long long o = cell(g, x, y, z);
+        I[o] = I[o] - apply_A(R, dval(D, g, x, y, z), g, x, y, z, o);
     }
 }
 
@@ -278,6 +301,9 @@ Geo make_geo(const MemberDev &m)
     g.cz = m.cz;
     g.cv = m.cv;
     g.c0 = -2.0 * (m.cx + m.cy + m.cz);
+    g.pitch = m.pitch;
+    g.pplane = m.plane;
+    g.G = m.G;
     return g;
 }
 
@@ -285,17 +311,25 @@ template <typename Real>
 cudaError_t backward_step_t(const MemberDev &m, const AdjointBuffers &b, cudaStream_t s)
 {
     const Geo g = make_geo(m);
-    const long long n = static_cast<long long>(m.nx) * m.ny * m.nz;
     const long long plane = static_cast<long long>(m.nx) * m.ny;
-    const int grid = grid_for(n);
+    // planes: one block row per plane up to 65535, then a plane-stride loop
+    const dim3 grid(static_cast<unsigned>((plane + kThreads - 1) / kThreads),
+                    static_cast<unsigned>(std::min(m.nz, 65535)));
     Real *R = static_cast<Real *>(b.R), *I = static_cast<Real *>(b.I);
     Real *P = static_cast<Real *>(b.P), *Q = static_cast<Real *>(b.Q);
-    adj_unmask_kernel<Real><<<grid, kThreads, 0, s>>>(g, b.M, R, I, P);
-    adj_b_kernel<Real><<<grid, kThreads, 0, s>>>(g, b.M, b.V, R, I, P, Q);
+    const Real *D = static_cast<const Real *>(m.d);
+    // absorbing planes only (all planes, each once, if the layers overlap)
+    int lo = m.mask_lo, hi = m.mask_hi;
+    if (lo + hi > m.nz) lo = m.nz, hi = 0;
+    if (lo + hi > 0) {
+        const dim3 ug(grid.x, static_cast<unsigned>(std::min(lo + hi, 65535)));
+        adj_unmask_kernel<Real><<<ug, kThreads, 0, s>>>(g, lo, hi, b.M, R, I, P);
+    }
+    adj_b_kernel<Real><<<grid, kThreads, 0, s>>>(g, b.M, D, R, I, P, Q);
     const int kd = m.det_k;
     if (kd >= 0) adj_flux_q_kernel<Real><<<grid_for(plane), kThreads, 0, s>>>(g, kd, b.w, R, Q);
-    adj_d_kernel<Real><<<grid, kThreads, 0, s>>>(g, b.V, kd, b.w, R, I, P, Q, b.gV);
-    adj_e_kernel<Real><<<grid, kThreads, 0, s>>>(g, b.V, R, I);
+    adj_d_kernel<Real><<<grid, kThreads, 0, s>>>(g, D, kd, b.w, R, I, P, Q, b.gV);
+    adj_e_kernel<Real><<<grid, kThreads, 0, s>>>(g, D, R, I);
     return cudaGetLastError();
 }
 

@@ -514,14 +514,32 @@ tdse_status issue_segment(tdse_ctx *c, long long nsteps)
 // Same launches, replayed from a captured CUDA graph keyed by (steps, ping-pong
 // parity, fused depth).  Captured on a private stream that is ordered after and
 // before the context's stream with events.
-tdse_status run_segment(tdse_ctx *c, long long nsteps)
+tdse_status ensure_gstream(tdse_ctx *c)
 {
-    if (!c->graphs || c->profiling || nsteps <= 0) return issue_segment(c, nsteps);
     if (!c->gstream) {
         CUDA_TRY(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming));
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming));
     }
+    return TDSE_OK;
+}
+
+// Launch an instantiated graph on the private stream, ordered after and before
+// the context's stream.
+tdse_status replay_graph(tdse_ctx *c, cudaGraphExec_t exec)
+{
+    CUDA_TRY(c, cudaEventRecord(c->gev[0], c->stream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+    CUDA_TRY(c, cudaGraphLaunch(exec, c->gstream));
+    CUDA_TRY(c, cudaEventRecord(c->gev[1], c->gstream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->gev[1], 0));
+    return TDSE_OK;
+}
+
+tdse_status run_segment(tdse_ctx *c, long long nsteps)
+{
+    if (!c->graphs || c->profiling || nsteps <= 0) return issue_segment(c, nsteps);
+    TRY(ensure_gstream(c));
     cudaGraphExec_t exec = nullptr;
     for (auto &g : c->graph_cache)
         if (g.nsteps == nsteps && g.parity == c->cur && g.tblock == c->tblock) exec = g.exec;
@@ -544,11 +562,7 @@ tdse_status run_segment(tdse_ctx *c, long long nsteps)
         if (e != cudaSuccess) return fail(c, TDSE_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
         c->graph_cache.push_back({static_cast<int>(nsteps), cur0, c->tblock, exec});
     }
-    CUDA_TRY(c, cudaEventRecord(c->gev[0], c->stream));
-    CUDA_TRY(c, cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
-    CUDA_TRY(c, cudaGraphLaunch(exec, c->gstream));
-    CUDA_TRY(c, cudaEventRecord(c->gev[1], c->gstream));
-    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->gev[1], 0));
+    TRY(replay_graph(c, exec));
     // the replay advanced the state exactly like issue_segment would have
     long long left = nsteps;
     while (left > 0) {
@@ -1005,6 +1019,40 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
     }
     AdjointBuffers b{R, I, P, Q, static_cast<double *>(gV), static_cast<double *>(w), mb.mask64,
                      mb.V64};
+    // backward steps of one checkpoint segment, replayed from a CUDA graph per
+    // segment length (the buffers are this call's, so the graphs are too)
+    std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
+    auto back_steps = [&](long long nsteps) -> tdse_status {
+        if (nsteps <= 0) return TDSE_OK;
+        if (!c->graphs) {
+            for (long long k = 0; k < nsteps; ++k)
+                CUDA_TRY(c, adjoint_backward_step(d, elem, b, c->stream));
+            return TDSE_OK;
+        }
+        TRY(ensure_gstream(c));
+        cudaGraphExec_t exec = nullptr;
+        for (auto &g : graphs)
+            if (g.first == nsteps) exec = g.second;
+        if (!exec) {
+            cudaGraph_t graph = nullptr;
+            CUDA_TRY(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (long long k = 0; k < nsteps && e == cudaSuccess; ++k)
+                e = adjoint_backward_step(d, elem, b, c->gstream);
+            const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &graph);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess)
+                return fail(c, TDSE_ECUDA, "adjoint graph capture failed: %s", cudaGetErrorString(e));
+            graphs.push_back({nsteps, exec});
+        }
+        return replay_graph(c, exec);
+    };
+    auto drop_graphs = [&]() {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        graphs.clear();
+    };
     auto run = [&]() -> tdse_status {
         CUDA_TRY(c, cudaMemcpyAsync(gF, dL_dF, npix * 8,
                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -1017,7 +1065,8 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
         long long n = c->step;
         for (int k = static_cast<int>(mb.ckpts.size()) - 1; k >= 0; --k) {
             const long long n0 = mb.ckpts[k].first;
-            for (; n > n0; --n) CUDA_TRY(c, adjoint_backward_step(d, elem, b, c->stream));
+            TRY(back_steps(n - n0));
+            n = n0;
             // re-anchor the reconstructed forward state on the FP64 checkpoint
             const double *ck = mb.ckpts[k].second;
             CUDA_TRY(c, adjoint_load_state(d, elem, b, ck, ck + cells, c->stream));
@@ -1048,6 +1097,7 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
     };
     st = run();
     cleanup();
+    drop_graphs();
     return st;
 }
 
