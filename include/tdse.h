@@ -168,6 +168,40 @@ TDSE_API tdse_status tdse_get_state(tdse_ctx *ctx, int member, double *R, double
 /* Time-integrated detector flux F[ny][nx] = sum_n j^n dt (FP64). */
 TDSE_API tdse_status tdse_get_flux_map(tdse_ctx *ctx, int member, double *F, int on_device);
 
+/* Detector-plane density frames (Sec. 2.3, Eq. 15): rho[y][x] = R^n^2 + I^{n-1/2}^2
+ * on plane det_k (the paper's density of Sec. 2.1 restricted to the detector
+ * plane D), FP64, recorded into a device buffer of `capacity` frames per member
+ * at the start of a run (tdse_set_wavepacket / tdse_set_state) and at every
+ * observation point (every obs_every steps).  Recording stops when the buffer is
+ * full.  Setting a capacity (0 frees the buffer) discards recorded frames.
+ * EINVAL: member has no detector plane (det_k < 0) or capacity < 0. */
+TDSE_API tdse_status tdse_set_frame_capacity(tdse_ctx *ctx, int member, int capacity);
+
+/* Copy up to `cap` recorded frames of member m into frames[cap][ny][nx] and their
+ * step numbers into steps[cap] (either may be NULL); *count receives the number
+ * recorded. */
+TDSE_API tdse_status tdse_get_frames(tdse_ctx *ctx, int member, double *frames, long long *steps,
+                                     int cap, int *count, int on_device);
+
+/* Eq. 16 dissimilarity of K detector-density trajectories:
+ *   d_kj = 1/(t1 - t0) * integral_{t0}^{t1} ( integral_D (rho_k - rho_j)^2 dA )^{1/2} dt,
+ * discretised over the frames whose time lies in [t0, t1]: the inner integral is
+ * dA * sum over the P pixels, the outer one the trapezoidal rule on those frame
+ * times (a single frame in the window counts for the whole window).
+ *   frames  [K][M][P] FP64, trajectory k's M frames of P pixels (same times t[M],
+ *           increasing, for every trajectory)
+ *   d       [K][K] FP64 output; symmetric, zero diagonal
+ * Both arrays are on the device if on_device != 0, else on the host.  The work
+ * (K (K+1)/2 pairs x frames x pixels in FP64, then the time sums) runs on
+ * `stream` (a cudaStream_t; NULL: legacy default stream), which is synchronised
+ * before returning; scratch memory comes from cudaMallocAsync on that stream.
+ * EINVAL: NULL pointer, K < 1, M < 1, P < 1, dA <= 0, t1 <= t0 or no frame time
+ * in [t0, t1]; ENOMEM / ECUDA: a CUDA allocation or call failed.  Stateless: no
+ * context is involved. */
+TDSE_API tdse_status tdse_dissimilarity(const double *frames, int K, int M, long long P,
+                                        const double *t, double t0, double t1, double dA,
+                                        double *d, int on_device, void *stream);
+
 /* Reverse-mode gradient of a loss L(F) of the time-integrated flux of member m,
  * over all steps since tdse_set_wavepacket (requires ckpt_every > 0).
  * dL_dF[ny][nx] is dL/dF; outputs (each may be NULL): dL_dV[nz][ny][nx] and,

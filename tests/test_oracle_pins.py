@@ -445,3 +445,73 @@ def test_adjoint_chain_rule_to_atoms_matches_finite_differences():
             lp, _ = _loss(g, oracle.potential_atoms(g, ap), R0, I0, nsteps, target)
             lm, _ = _loss(g, oracle.potential_atoms(g, am), R0, I0, nsteps, target)
             assert gatoms[a, p] == pytest.approx((lp - lm) / (2 * eps), rel=1e-6)
+
+
+# ---------------------------------------------------------------- Eqs. 15-16
+
+def test_detector_frame_is_the_density_on_the_plane():
+    """Eq. 15: the frame is R^2 + I^2 of the detector plane, nothing else."""
+    from oracle import detector as D
+    rng = np.random.default_rng(11)
+    R = rng.normal(size=(6, 5, 4))
+    I = rng.normal(size=(6, 5, 4))
+    f = D.detector_frame(R, I, 3)
+    assert f.shape == (5, 4)
+    for y in range(5):
+        for x in range(4):
+            assert f[y, x] == R[3, y, x] ** 2 + I[3, y, x] ** 2
+
+
+def test_dissimilarity_closed_forms():
+    """Eq. 16 on inputs with a known answer.  (i) Trajectories that differ by a
+    constant c on every pixel and frame: d = |c| sqrt(P dA).  (ii) A difference
+    growing linearly in time, c t: the trapezoidal rule is exact for a linear
+    integrand, so d = |c| sqrt(P dA) (t0 + t1) / 2 on [t0, t1] covered by frames."""
+    from oracle import detector as D
+    P, M, dA = 30, 7, 0.04
+    t = np.linspace(0.0, 1.2, M)
+    base = np.random.default_rng(3).uniform(0.0, 1.0, size=(M, P))
+    c = 0.37
+    frames = np.stack([base, base + c])
+    d = D.dissimilarity(frames, t, 0.0, 1.2, dA)
+    assert d[0, 1] == pytest.approx(c * np.sqrt(P * dA), rel=1e-13)
+    lin = np.stack([base, base + c * t[:, None]])
+    d = D.dissimilarity(lin, t, 0.0, 1.2, dA)
+    assert d[0, 1] == pytest.approx(c * np.sqrt(P * dA) * 0.6, rel=1e-13)
+    # window of frames 2..5: t0 = t[2], t1 = t[5]
+    d = D.dissimilarity(lin, t, t[2], t[5], dA)
+    assert d[0, 1] == pytest.approx(c * np.sqrt(P * dA) * 0.5 * (t[2] + t[5]), rel=1e-13)
+
+
+def test_dissimilarity_is_a_metric():
+    """Each frame's term is an L2 distance and the time sum has non-negative
+    weights, so d is symmetric, zero on the diagonal, and obeys the triangle
+    inequality."""
+    from oracle import detector as D
+    rng = np.random.default_rng(5)
+    frames = rng.uniform(0.0, 1.0, size=(6, 5, 40))
+    t = np.array([0.0, 0.1, 0.25, 0.3, 0.5])
+    d = D.dissimilarity(frames, t, 0.05, 0.5, 0.01)
+    assert np.all(np.diag(d) == 0.0)
+    assert np.allclose(d, d.T, rtol=0, atol=0)
+    for a in range(6):
+        for b in range(6):
+            for c in range(6):
+                assert d[a, c] <= d[a, b] + d[b, c] + 1e-15
+    # frame 0 lies outside the window: changing it changes nothing
+    g = frames.copy()
+    g[:, 0] += 5.0
+    assert np.array_equal(D.dissimilarity(g, t, 0.05, 0.5, 0.01), d)
+
+
+def test_dissimilarity_single_frame_window():
+    """One frame inside [t0, t1] stands for the whole window: d = its L2 distance."""
+    from oracle import detector as D
+    rng = np.random.default_rng(8)
+    frames = rng.uniform(size=(2, 3, 10))
+    t = np.array([0.0, 1.0, 2.0])
+    d = D.dissimilarity(frames, t, 0.5, 1.5, 0.3)
+    expect = np.sqrt(0.3 * np.sum((frames[0, 1] - frames[1, 1]) ** 2))
+    assert d[0, 1] == pytest.approx(expect, rel=1e-14)
+    with pytest.raises(ValueError):
+        D.dissimilarity(frames, t, 2.5, 3.0, 0.3)
