@@ -34,6 +34,9 @@ struct Member {
     double *mask64 = nullptr;       // absorbing factor per plane, FP64 (adjoint)
     bool from_packet = false;       // the run started with tdse_set_wavepacket
     std::vector<std::pair<long long, double *>> ckpts;   // (step, FP64 R then I)
+    double *frames = nullptr;       // detector density frames [frame_cap][ny][nx] (Eq. 15)
+    int frame_cap = 0;
+    std::vector<long long> frame_steps;   // step of each recorded frame
 };
 
 struct StepPlan {
@@ -611,6 +614,19 @@ tdse_status current_obs(tdse_ctx *c, int i, double *rec)
     return TDSE_OK;
 }
 
+// Record the detector density frame of member i at the current step, if the
+// member has a frame buffer with room left.
+tdse_status capture_frame(tdse_ctx *c, int i)
+{
+    Member &mb = c->m[i];
+    if (!mb.frames || static_cast<int>(mb.frame_steps.size()) >= mb.frame_cap) return TDSE_OK;
+    const size_t npix = static_cast<size_t>(mb.dev.nx) * mb.dev.ny;
+    CUDA_TRY(c, launch_frame(mb.dev, c->precision, c->cur, mb.frames + mb.frame_steps.size() * npix,
+                             c->stream));
+    mb.frame_steps.push_back(c->step);
+    return TDSE_OK;
+}
+
 tdse_status reset_run(tdse_ctx *c, int i)
 {
     Member &mb = c->m[i];
@@ -625,6 +641,8 @@ tdse_status reset_run(tdse_ctx *c, int i)
     TRY(current_obs(c, i, rec));
     mb.q0 = rec[1];
     mb.hist.insert(mb.hist.end(), {static_cast<double>(c->step), rec[1], rec[2], rec[3]});
+    mb.frame_steps.clear();
+    TRY(capture_frame(c, i));
     return TDSE_OK;
 }
 
@@ -892,6 +910,7 @@ tdse_status tdse_step(tdse_ctx *c, long long nsteps)
         left -= seg;
         if (c->step % c->obs_every == 0) {
             TRY(observe_all(c, nrec));
+            for (size_t i = 0; i < c->m.size(); ++i) TRY(capture_frame(c, static_cast<int>(i)));
             if (++nrec == kRecCap) {
                 TRY(drain_records(c, nrec));
                 nrec = 0;
@@ -920,6 +939,45 @@ tdse_status tdse_observables(tdse_ctx *c, int member, tdse_obs *out)
     out->flux_integrated = rec[5];
     out->step = c->step;
     out->t = c->step * mb.p.dt;
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_frame_capacity(tdse_ctx *c, int member, int capacity)
+{
+    TRY(check_member(c, member));
+    Member &mb = c->m[member];
+    if (mb.p.det_k < 0) return fail(c, TDSE_EINVAL, "member %d has no detector plane", member);
+    if (capacity < 0) return fail(c, TDSE_EINVAL, "negative frame capacity");
+    TRY(ensure_device(c));
+    dfree(c, mb.frames);
+    mb.frames = nullptr;
+    mb.frame_cap = 0;
+    mb.frame_steps.clear();
+    if (capacity > 0) {
+        void *p = nullptr;
+        TRY(dalloc(c, static_cast<size_t>(capacity) * mb.dev.nx * mb.dev.ny * sizeof(double), &p));
+        mb.frames = static_cast<double *>(p);
+        mb.frame_cap = capacity;
+    }
+    return TDSE_OK;
+}
+
+tdse_status tdse_get_frames(tdse_ctx *c, int member, double *frames, long long *steps, int cap,
+                            int *count, int on_device)
+{
+    TRY(check_member(c, member));
+    const Member &mb = c->m[member];
+    const int n = static_cast<int>(mb.frame_steps.size());
+    if (count) *count = n;
+    const int k = std::min(std::max(cap, 0), n);
+    if (steps && k > 0) memcpy(steps, mb.frame_steps.data(), k * sizeof(long long));
+    if (frames && k > 0) {
+        const size_t bytes = static_cast<size_t>(k) * mb.dev.nx * mb.dev.ny * sizeof(double);
+        CUDA_TRY(c, cudaMemcpyAsync(frames, mb.frames, bytes,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
     return TDSE_OK;
 }
 

@@ -101,6 +101,8 @@ cudaError_t launch_scale_half(const MemberDev &m, const double *V64, const doubl
                               cudaStream_t s);
 cudaError_t launch_set_state(const MemberDev &m, const double *R64, const double *I64,
                              int precision, int buf, cudaStream_t s);
+// Eq. 15 density of plane det_k at the current time level into out[ny][nx] (FP64).
+cudaError_t launch_frame(const MemberDev &m, int precision, int buf, double *out, cudaStream_t s);
 cudaError_t launch_get_state(const MemberDev &m, double *R64, double *I64, int precision,
                              int buf, cudaStream_t s);
 // copy the interior of one padded field out to (to_field = 0) or in from an

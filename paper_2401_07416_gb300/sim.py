@@ -86,6 +86,15 @@ class Sim:
         T.tdse_get_state(self.ctx, member, R, I)
         return R, I
 
+    def set_frames(self, capacity: int, member: int = 0):
+        """Record up to `capacity` detector density frames (Eq. 15) of member m."""
+        T.tdse_set_frame_capacity(self.ctx, member, capacity)
+
+    def frames(self, member: int = 0):
+        """(frames [count][ny][nx], steps [count]) recorded so far."""
+        g = self.grids[member]
+        return T.tdse_get_frames(self.ctx, member, g.ny, g.nx)
+
     def flux_map(self, member: int = 0) -> np.ndarray:
         g = self.grids[member]
         F = np.zeros((g.ny, g.nx))

@@ -84,6 +84,10 @@ SIGNATURES = {
     "tdse_get_obs_history": (_I, [_VP, _I, _VP, _I, ctypes.POINTER(_I)]),
     "tdse_get_state": (_I, [_VP, _I, _VP, _VP, _I]),
     "tdse_get_flux_map": (_I, [_VP, _I, _VP, _I]),
+    "tdse_set_frame_capacity": (_I, [_VP, _I, _I]),
+    "tdse_get_frames": (_I, [_VP, _I, _VP, _VP, _I, ctypes.POINTER(_I), _I]),
+    "tdse_dissimilarity": (_I, [_VP, _I, _I, ctypes.c_longlong, _VP, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, _VP, _I, _VP]),
     "tdse_adjoint": (_I, [_VP, _I, _VP, _VP, _VP, _I]),
     "tdse_save_state": (_I, [_VP, ctypes.c_char_p]),
     "tdse_load_state": (_I, [_VP, ctypes.c_char_p]),
@@ -248,6 +252,46 @@ def tdse_get_flux_map(ctx, member: int, F):
     p, dev, _ = _arg(F, writable=True)
     _check(ctx, lib().tdse_get_flux_map(ctx, member, p, dev))
     return F
+
+
+def tdse_set_frame_capacity(ctx, member: int, capacity: int):
+    _check(ctx, lib().tdse_set_frame_capacity(ctx, member, capacity))
+
+
+def tdse_get_frames(ctx, member: int, ny: int, nx: int):
+    """(frames [count][ny][nx], steps [count]) recorded for member m (Eq. 15)."""
+    n = ctypes.c_int()
+    _check(ctx, lib().tdse_get_frames(ctx, member, None, None, 0, ctypes.byref(n), 0))
+    frames = np.zeros((n.value, ny, nx))
+    steps = np.zeros(n.value, dtype=np.int64)
+    _check(ctx, lib().tdse_get_frames(ctx, member, frames.ctypes.data_as(ctypes.c_void_p),
+                                      steps.ctypes.data_as(ctypes.c_void_p), n.value,
+                                      ctypes.byref(n), 0))
+    return frames, steps
+
+
+def tdse_dissimilarity(frames, t, t0: float, t1: float, dA: float, d=None, stream_ptr: int = 0):
+    """Eq. 16 for frames [K][M][P...] (numpy, or torch CUDA float64); returns d [K][K]
+    (numpy for numpy input, else the given or a new torch tensor)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    shape = tuple(frames.shape)
+    K, M = shape[0], shape[1]
+    P = int(np.prod(shape[2:])) if len(shape) > 2 else 1
+    pf, dev, keep = _arg(frames)
+    if d is None:
+        if dev:
+            import torch
+            d = torch.empty((K, K), dtype=torch.float64, device=frames.device)
+        else:
+            d = np.zeros((K, K))
+    pd, ddev, _ = _arg(d, writable=True)
+    if ddev != dev:
+        raise TypeError("frames and d must both be on the device or both on the host")
+    st = lib().tdse_dissimilarity(pf, K, M, P, t.ctypes.data_as(ctypes.c_void_p), t0, t1, dA,
+                                  pd, dev, ctypes.c_void_p(stream_ptr))
+    if st != OK:
+        raise TdseError(st, "tdse_dissimilarity failed")
+    return d
 
 
 def tdse_adjoint(ctx, member: int, dL_dF, dL_dV=None, dL_datoms=None):
