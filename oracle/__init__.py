@@ -34,7 +34,8 @@ class OrcGrid(ctypes.Structure):
                 ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
                 ("dt", ctypes.c_double), ("hbar", ctypes.c_double), ("mass", ctypes.c_double),
                 ("bc", ctypes.c_int * 3), ("mask_lo", ctypes.c_int), ("mask_hi", ctypes.c_int),
-                ("mask_eta", ctypes.c_double), ("det_k", ctypes.c_int)]
+                ("mask_eta", ctypes.c_double), ("det_k", ctypes.c_int),
+                ("mask_kind", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -81,7 +82,8 @@ def lib():
 
 def _grid(g) -> OrcGrid:
     return OrcGrid(g.nx, g.ny, g.nz, g.hx, g.hy, g.hz, g.dt, g.hbar, g.mass,
-                   (ctypes.c_int * 3)(*g.bc), g.mask_lo, g.mask_hi, g.mask_eta, g.det_k)
+                   (ctypes.c_int * 3)(*g.bc), g.mask_lo, g.mask_hi, g.mask_eta, g.det_k,
+                   getattr(g, "mask_kind", 0))
 
 
 def _ptr(a: Optional[np.ndarray]):

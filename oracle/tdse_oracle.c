@@ -40,6 +40,7 @@ typedef struct {
     int mask_lo, mask_hi;
     double mask_eta;
     int det_k;          /* detector face kd (between planes kd and kd+1), -1 off */
+    int mask_kind;      /* 0: cos^2 layers; 1: Eq. 10 quadratic absorbing potential, split */
 } orc_grid;
 
 static size_t ncells(const orc_grid *g) { return (size_t)g->nx * g->ny * g->nz; }
@@ -139,20 +140,31 @@ void orc_apply_A(const orc_grid *g, const double *V, const double *f, double *ou
 }
 
 /* Absorbing layer factor per z plane (reading: cos^2 profile, see header). */
+/* Absorbing factor of one layer plane at depth d = 1..W from the layer's inner
+ * edge (d = W is the outermost plane).
+ * kind 0: M = cos^2(eta (pi/2) d / W).
+ * kind 1: Eq. 10's absorbing potential -i W(d) with the quadratic profile
+ *   W(d) = eta (d / W)^2 (eta: the strength at the outermost plane, in energy
+ *   units; Eq. 10 grows as the square of the distance into the layer), applied by
+ *   operator splitting: the term alone, d psi / dt = -W psi / hbar, advances psi by
+ *   exactly exp(-W dt / hbar) over one step. */
+static double layer_factor(const orc_grid *g, int d, int W)
+{
+    if (g->mask_kind == 1) {
+        double u = (double)d / W;
+        return exp(-g->mask_eta * u * u * g->dt / g->hbar);
+    }
+    double s = cos(g->mask_eta * 0.5 * M_PI * (double)d / W);
+    return s * s;
+}
+
 void orc_mask(const orc_grid *g, double *M)
 {
     for (int k = 0; k < g->nz; ++k) {
         double m = 1.0;
-        if (g->mask_lo > 0 && k < g->mask_lo) {
-            double d = (double)(g->mask_lo - k);
-            double s = cos(g->mask_eta * 0.5 * M_PI * d / g->mask_lo);
-            m = s * s;
-        }
-        if (g->mask_hi > 0 && k >= g->nz - g->mask_hi) {
-            double d = (double)(k - (g->nz - g->mask_hi) + 1);
-            double s = cos(g->mask_eta * 0.5 * M_PI * d / g->mask_hi);
-            m = s * s;
-        }
+        if (g->mask_lo > 0 && k < g->mask_lo) m = layer_factor(g, g->mask_lo - k, g->mask_lo);
+        if (g->mask_hi > 0 && k >= g->nz - g->mask_hi)
+            m = layer_factor(g, k - (g->nz - g->mask_hi) + 1, g->mask_hi);
         M[k] = m;
     }
 }

@@ -35,6 +35,8 @@ import numpy as np
 PERIODIC = 0
 DIRICHLET = 1
 
+MASK_COS2 = 0
+MASK_CAP = 1
 FP64 = 0
 FP32 = 1
 FP32_KAHAN = 2
@@ -56,9 +58,10 @@ class Grid:
     bc: Tuple[int, int, int] = (PERIODIC, PERIODIC, DIRICHLET)
     mask_lo: int = 0          # absorbing cells at the z = 0 end
     mask_hi: int = 0          # absorbing cells at the z = nz-1 end
-    mask_eta: float = 0.1     # absorbing-layer strength
+    mask_eta: float = 0.1     # absorbing-layer strength (cos^2: eta; CAP: W at the outer plane)
     det_k: int = -1           # detector face between planes det_k and det_k+1 (-1: off)
     obs_every: int = 20       # period of the norm/energy reductions (Sec. 2.3: h = 20)
+    mask_kind: int = 0        # MASK_COS2, or MASK_CAP: Eq. 10's quadratic potential, split
 
     @property
     def cells(self) -> int:

@@ -515,3 +515,48 @@ def test_dissimilarity_single_frame_window():
     assert d[0, 1] == pytest.approx(expect, rel=1e-14)
     with pytest.raises(ValueError):
         D.dissimilarity(frames, t, 2.5, 3.0, 0.3)
+
+
+# ---------------------------------------------------------------- Eq. 10 absorbing potential
+
+def test_cap_mask_is_the_split_step_of_eq10():
+    """MASK_CAP: each layer plane's factor is what the absorbing term alone,
+    d psi/dt = -W psi / hbar, does over one step (checked by an ODE solve, not the
+    closed form), with Eq. 10's W growing as the square of the depth into the layer
+    and equal to mask_eta at the outermost plane."""
+    import dataclasses
+    from scipy.integrate import solve_ivp
+    g = W.small_grid(4, 4, 40, dt=0.01, bc=(0, 0, 0))
+    g = dataclasses.replace(g, mask_lo=12, mask_hi=0, mask_eta=30.0, mask_kind=W.MASK_CAP,
+                            hbar=1.0)
+    M = oracle.mask(g)
+    assert np.all(M[12:] == 1.0)
+    for k in range(12):
+        depth = 12 - k                                  # 12 at the outermost plane k = 0
+        Wk = 30.0 * (depth / 12.0) ** 2                 # Eq. 10: quadratic in the depth
+        sol = solve_ivp(lambda t, y: -Wk * y, (0.0, g.dt), [1.0], rtol=1e-12, atol=1e-14)
+        assert M[k] == pytest.approx(sol.y[0, -1], rel=1e-9)
+    # quadratic profile: ln M is proportional to depth^2
+    ratios = np.log(M[:12]) / np.log(M[0])
+    assert np.allclose(ratios, ((12 - np.arange(12)) / 12.0) ** 2, rtol=1e-12)
+
+
+def test_cap_absorbs_and_vanishes_at_zero_strength():
+    """With the CAP the invariant Q never grows; with zero strength the layer is
+    transparent (Q conserved as without any mask)."""
+    import dataclasses
+    g = W.small_grid(8, 8, 60, h=(0.3, 0.3, 0.2), dt=0.004, bc=(0, 0, 0))
+    p = W.Packet((1.2, 1.2, 4.0), (0.0, 0.0, 1.0), (0.0, 0.0, -3.0))
+    cap = dataclasses.replace(g, mask_lo=15, mask_kind=W.MASK_CAP, mask_eta=20.0)
+    R, I = oracle.initial_state(cap, p, None)
+    q = [oracle.observables(cap, None, R, I)["Q"]]
+    for _ in range(30):
+        R, I, _, _ = oracle.run(cap, None, R, I, 20, flux=False)
+        q.append(oracle.observables(cap, None, R, I)["Q"])
+    assert all(b <= a * (1 + 1e-13) for a, b in zip(q, q[1:]))
+    assert q[-1] < 0.5 * q[0]                      # the packet ran into the layer
+    off = dataclasses.replace(cap, mask_eta=0.0)
+    R, I = oracle.initial_state(off, p, None)
+    q0 = oracle.observables(off, None, R, I)["Q"]
+    R, I, _, _ = oracle.run(off, None, R, I, 600, flux=False)
+    assert oracle.observables(off, None, R, I)["Q"] == pytest.approx(q0, rel=1e-12)
