@@ -325,6 +325,59 @@ def batch_throughput(torch, T, steps, warmup):
             "graphs": "profiling pass (direct launches)"}
 
 
+def absorber_reflection(torch, T):
+    """Reflection coefficients of the absorbing layers.  A packet that is a plane wave
+    in x, y (sigma_z = 2 bohr, k = 1.9 bohr^-1, kinetic energy 1.8 Ha, as in the
+    diffraction runs) starts 12 bohr above a layer at the bottom of a 32 x 32 x
+    (W + 300) grid (h = 0.1, walls in z, V = 0) and runs 28000 steps (14 a.u.).  The
+    time-integrated flux through the face 2 bohr above the layer is the net downward
+    transfer Phi, so the absorbed fraction is -Phi / Q0 and the reflection
+    R = 1 + Phi / Q0 (FP64)."""
+    from paper_2401_07416_gb300.sim import Sim
+    out = {}
+    cases = [("cos2_W20_eta0.1", W.MASK_COS2, 20, 0.1), ("cos2_W20_eta0.3", W.MASK_COS2, 20, 0.3),
+             ("cos2_W100_eta0.1", W.MASK_COS2, 100, 0.1), ("cap_W100_0.5Ha", W.MASK_CAP, 100, 0.5),
+             ("cap_W100_2Ha", W.MASK_CAP, 100, 2.0), ("cap_W100_8Ha", W.MASK_CAP, 100, 8.0)]
+    for name, kind, width, eta in cases:
+        g = W.Grid(nx=32, ny=32, nz=width + 300, hx=0.1, hy=0.1, hz=0.1, dt=5e-4,
+                   bc=(W.PERIODIC, W.PERIODIC, W.DIRICHLET), mask_lo=width, mask_hi=0,
+                   mask_eta=eta, mask_kind=kind, det_k=width + 20, obs_every=10 ** 6)
+        p = W.Packet((1.6, 1.6, width * g.hz + 12.0), (0.0, 0.0, 2.0), (0.0, 0.0, -1.9))
+        with Sim(g, precision=W.FP64, tblock=1) as s:
+            s.set_packet(0, p)
+            q0 = s.observables(0)["Q"]
+            s.step(28000)
+            q1 = s.observables(0)["Q"]
+            phi = float(s.flux_map(0).sum()) * g.hx * g.hy
+        out[name] = {"reflection": 1.0 + phi / q0, "norm_left": q1 / q0}
+    return out
+
+
+def dissimilarity_cost(torch, T, K=48, M=100, ny=128, nx=128):
+    """Eq. 16 over a batch of K synthetic detector-density trajectories (M frames of
+    ny x nx pixels, seeded, on the device), the whole window: FP64 pairwise kernel."""
+    rng = np.random.default_rng(16)
+    frames = torch.from_numpy(rng.uniform(0.0, 1e-3, size=(K, M, ny * nx))).cuda()
+    t = np.arange(M) * 20 * 5e-4
+    stream = torch.cuda.current_stream()
+    T.tdse_dissimilarity(frames, t, t[0], t[-1], 0.01, stream_ptr=stream.cuda_stream)   # warm-up
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    T.tdse_dissimilarity(frames, t, t[0], t[-1], 0.01, stream_ptr=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    terms = K * (K + 1) // 2 * M * ny * nx
+    del frames
+    return {"trajectories": K, "frames": M, "pixels": ny * nx, "ms": ms,
+            "pair_frame_pixels_per_s": terms / (ms * 1e-3),
+            "fp64_gflops": 3 * terms / (ms * 1e-3) / 1e9,
+            "includes": "pairwise FP64 sums of squared differences and the time sums "
+                        "(allocation of the scratch on the stream included)"}
+
+
 def adjoint_cost(torch, T):
     """96x96x192, 3000 steps: forward with FP64 checkpoints every 100 steps, then the
     adjoint of the detector-flux loss (dL/dV and the 32 atoms)."""
@@ -448,6 +501,8 @@ def main():
         extras["batched_48_films"] = batch_throughput(torch, T, max(20, args.steps // 2),
                                                       min(args.warmup, 6))
         extras["adjoint_96x96x192_3000"] = adjoint_cost(torch, T)
+        extras["dissimilarity_48x100x128x128"] = dissimilarity_cost(torch, T)
+        extras["absorbing_layer_reflection"] = absorber_reflection(torch, T)
 
         # end to end through the C ABI from pinned host buffers: potential in,
         # packet set-up, the steps, flux map and observables out

@@ -77,14 +77,27 @@ typedef struct tdse_params {
     double hbar, mass;       /* <= 0 selects 1 (atomic units) */
     int bc[3];               /* TDSE_BC_* per axis x, y, z */
     int mask_lo, mask_hi;    /* absorbing cells at the z = 0 and z = nz-1 ends (0: none) */
-    double mask_eta;         /* absorbing strength eta (M at the outermost cell = cos^2(eta pi/2)) */
+    double mask_eta;         /* absorbing strength: TDSE_MASK_COS2: eta (M at the outermost cell =
+                                cos^2(eta pi/2)); TDSE_MASK_CAP: W at the outermost cell (energy) */
     int det_k;               /* detector face between planes det_k, det_k+1; -1: no detector */
     int obs_every;           /* norm/energy reduction every obs_every steps (<= 0: 20, Sec. 2.3) */
     int ckpt_every;          /* > 0: keep FP64 checkpoints every ckpt_every steps for tdse_adjoint */
     int precision;           /* TDSE_FP64 / TDSE_FP32 / TDSE_FP32_KAHAN (same for all members) */
     int tblock;              /* steps fused per kernel launch (temporal blocking); 0: automatic */
-    int reserved[6];         /* must be zero */
+    int mask_kind;           /* TDSE_MASK_COS2 (0) or TDSE_MASK_CAP (1), see below */
+    int reserved[5];         /* must be zero */
 } tdse_params;
+
+/* Absorbing layers (mask_lo planes at z = 0, mask_hi at z = nz-1; depth d = 1..W
+ * from the layer's inner edge, d = W the outermost plane).  After every step both
+ * parts of psi are multiplied by a per-plane factor M(d):
+ *   TDSE_MASK_COS2  M = cos^2(eta (pi/2) d / W)
+ *   TDSE_MASK_CAP   M = exp(-W(d) dt / hbar), W(d) = mask_eta (d / W)^2: Eq. 10's
+ *                   absorbing potential -i W (quadratic in the depth into the layer),
+ *                   applied by operator splitting (exp(-W dt/hbar) is the exact
+ *                   action of that term alone over one step).  The paper's set-up is
+ *                   one layer (mask_lo only) on an appended bottom region. */
+enum { TDSE_MASK_COS2 = 0, TDSE_MASK_CAP = 1 };
 
 typedef struct tdse_obs {
     double Q;                /* h^3 sum (R^n R^n + I^{n+1/2} I^{n-1/2}), exactly conserved by the

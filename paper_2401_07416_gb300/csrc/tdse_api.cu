@@ -183,6 +183,10 @@ tdse_status validate(tdse_ctx *c, const tdse_params &q, int idx)
     if (!(q.dt > 0) || q.dt * emax >= 2.0)
         return fail(c, TDSE_EINVAL, "member %d: dt=%g violates dt*max|E|/hbar < 2 (max %g)", idx,
                     q.dt, 2.0 / emax);
+    if (q.mask_kind != TDSE_MASK_COS2 && q.mask_kind != TDSE_MASK_CAP)
+        return fail(c, TDSE_EINVAL, "member %d: unknown mask_kind %d", idx, q.mask_kind);
+    if (q.mask_kind == TDSE_MASK_CAP && !(q.mask_eta >= 0.0))
+        return fail(c, TDSE_EINVAL, "member %d: negative absorbing strength", idx);
     for (int r : q.reserved)
         if (r != 0) return fail(c, TDSE_EINVAL, "member %d: reserved fields must be zero", idx);
     return TDSE_OK;
@@ -338,18 +342,23 @@ tdse_status ensure_device(tdse_ctx *c)
         TRY(dalloc(c, cells * sizeof(double), &p)); mb.V64 = static_cast<double *>(p);
         TRY(dalloc(c, static_cast<size_t>(d.nx) * d.ny * sizeof(double), &p)); d.flux = static_cast<double *>(p);
         TRY(dalloc(c, static_cast<size_t>(d.nx) * d.ny * sizeof(double), &p)); d.jlast = static_cast<double *>(p);
-        // absorbing factor per plane: M = cos^2(eta (pi/2) depth / W) inside the layers
+        // absorbing factor per plane at depth dep = 1..W into a layer of W planes:
+        // cos^2(eta (pi/2) dep / W), or exp(-W(dep) dt / hbar) with the quadratic
+        // W(dep) = eta (dep / W)^2 of Eq. 10 (operator split)
         std::vector<double> M(d.nz, 1.0);
         const tdse_params &q = mb.p;
+        auto factor = [&](int dep, int W) {
+            if (q.mask_kind == TDSE_MASK_CAP) {
+                const double u = static_cast<double>(dep) / W;
+                return std::exp(-q.mask_eta * u * u * q.dt / q.hbar);
+            }
+            const double s = std::cos(q.mask_eta * 0.5 * M_PI * dep / W);
+            return s * s;
+        };
         for (int k = 0; k < d.nz; ++k) {
-            if (q.mask_lo > 0 && k < q.mask_lo) {
-                const double s = std::cos(q.mask_eta * 0.5 * M_PI * (q.mask_lo - k) / q.mask_lo);
-                M[k] = s * s;
-            }
-            if (q.mask_hi > 0 && k >= d.nz - q.mask_hi) {
-                const double s = std::cos(q.mask_eta * 0.5 * M_PI * (k - (d.nz - q.mask_hi) + 1) / q.mask_hi);
-                M[k] = s * s;
-            }
+            if (q.mask_lo > 0 && k < q.mask_lo) M[k] = factor(q.mask_lo - k, q.mask_lo);
+            if (q.mask_hi > 0 && k >= d.nz - q.mask_hi)
+                M[k] = factor(k - (d.nz - q.mask_hi) + 1, q.mask_hi);
         }
         TRY(dalloc(c, d.nz * sizeof(double), &p)); mb.mask64 = static_cast<double *>(p);
         CUDA_TRY(c, cudaMemcpyAsync(mb.mask64, M.data(), d.nz * sizeof(double),
@@ -667,7 +676,7 @@ bool same_grid(const tdse_params &a, const tdse_params &b)
            a.hz == b.hz && a.dt == b.dt && a.hbar == b.hbar && a.mass == b.mass &&
            a.bc[0] == b.bc[0] && a.bc[1] == b.bc[1] && a.bc[2] == b.bc[2] &&
            a.mask_lo == b.mask_lo && a.mask_hi == b.mask_hi && a.mask_eta == b.mask_eta &&
-           a.det_k == b.det_k && a.precision == b.precision;
+           a.mask_kind == b.mask_kind && a.det_k == b.det_k && a.precision == b.precision;
 }
 
 template <typename T>

@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
                 ("mask_eta", ctypes.c_double), ("det_k", ctypes.c_int),
                 ("obs_every", ctypes.c_int), ("ckpt_every", ctypes.c_int),
                 ("precision", ctypes.c_int), ("tblock", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("mask_kind", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class Obs(ctypes.Structure):
@@ -162,6 +162,7 @@ def params_from_grid(g: W.Grid, precision: int = FP64, tblock: int = 0,
     p.ckpt_every = ckpt_every
     p.precision = precision
     p.tblock = tblock
+    p.mask_kind = getattr(g, "mask_kind", 0)
     return p
 
 

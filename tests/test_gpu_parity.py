@@ -250,3 +250,27 @@ def test_every_two_step_variant_bitwise_equal(T, name, precision):
             continue
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), (name, precision, v)
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32_KAHAN"])
+def test_eq10_absorbing_layer_matches_oracle(T, precision):
+    """The paper's set-up of Eq. 10: one quadratic absorbing layer at the bottom of a
+    z-periodic domain (MASK_CAP, operator split), fused kernel vs oracle."""
+    import dataclasses
+    g = W.small_grid(24, 20, 64, h=(0.21, 0.19, 0.23), dt=0.004, bc=(0, 0, 0), det_k=30)
+    g = dataclasses.replace(g, mask_lo=22, mask_hi=0, mask_kind=W.MASK_CAP, mask_eta=15.0)
+    V = W.random_potential(g, 300, 2.0)
+    L = g.lengths
+    p = W.Packet((0.5 * L[0], 0.5 * L[1], 0.40 * L[2]), (1.0, 1.0, 0.9), (0.2, 0.1, -2.5))
+    n = 41
+    _, (Ro, Io, Fo, _), oo = oracle_run(g, V, p, n)
+    _, (Rg, Ig, Fg), og = gpu_run(g, V, p, n, getattr(T, precision))
+    if precision == "FP64":
+        scale = max(np.abs(Ro).max(), np.abs(Io).max())
+        assert max(np.abs(Rg - Ro).max(), np.abs(Ig - Io).max()) / scale < TOL64
+        assert maxrel(Fg, Fo) < TOL64
+        assert og["Q"] == pytest.approx(oo["Q"], rel=TOL64)
+    else:
+        assert l2rel(np.concatenate([Rg, Ig]), np.concatenate([Ro, Io])) < TOL32_L2
+        assert abs(og["Q"] - oo["Q"]) / oo["Q"] < TOL32_Q
+    assert oo["Q"] < 0.999   # the layer absorbed part of the packet
