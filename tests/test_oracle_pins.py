@@ -560,3 +560,66 @@ def test_cap_absorbs_and_vanishes_at_zero_strength():
     q0 = oracle.observables(off, None, R, I)["Q"]
     R, I, _, _ = oracle.run(off, None, R, I, 600, flux=False)
     assert oracle.observables(off, None, R, I)["Q"] == pytest.approx(q0, rel=1e-12)
+
+
+# ---------------------------------------------------------------- potential interpolation
+
+def test_interpolation_reproduces_lattice_values_and_tensor_products():
+    """Trilinear interpolation of the periodic cell: (i) nodes that coincide with
+    lattice points take the lattice value; (ii) a tensor product f(x) g(y) q(z) of
+    periodic piecewise-linear functions with knots on the lattice is reproduced
+    exactly everywhere (trilinear interpolation is exact on that space)."""
+    from oracle import interp as OI
+    cnx, cny, cnz = 6, 5, 7
+    cell = (3.0, 2.5, 3.5)
+    rng = np.random.default_rng(2)
+    Vc = rng.normal(size=(cnz, cny, cnx))
+    # (i) simulation spacing = lattice spacing, origin on the lattice
+    h = (cell[0] / cnx, cell[1] / cny, cell[2] / cnz)
+    V = OI.trilinear_periodic(Vc, cell, (0.0, 0.0, 0.0), (2 * cnz, cny, 3 * cnx), h)
+    for k in range(2 * cnz):
+        for i in range(3 * cnx):
+            assert V[k, 2, i] == pytest.approx(Vc[k % cnz, 2, i % cnx], abs=1e-12)
+    # (ii) tensor products of knot-wise linear periodic functions, off-lattice nodes
+    fx, fy, fz = rng.normal(size=cnx), rng.normal(size=cny), rng.normal(size=cnz)
+    Vt = fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+    origin = (0.31, -0.7, 1.9)
+
+    def pl(vals, L, n, o, pos):                       # periodic piecewise-linear
+        u = (pos - o) / L * n
+        i0 = int(np.floor(u))
+        t = u - i0
+        return vals[i0 % n] * (1 - t) + vals[(i0 + 1) % n] * t
+
+    hh = (0.37, 0.29, 0.41)
+    V = OI.trilinear_periodic(Vt, cell, origin, (9, 8, 11), hh)
+    for k in range(9):
+        for j in range(8):
+            for i in range(11):
+                expect = (pl(fz, cell[2], cnz, origin[2], k * hh[2]) *
+                          pl(fy, cell[1], cny, origin[1], j * hh[1]) *
+                          pl(fx, cell[0], cnx, origin[0], i * hh[0]))
+                assert V[k, j, i] == pytest.approx(expect, rel=1e-12, abs=1e-12)
+
+
+def test_interpolation_matches_scipy_on_a_padded_lattice():
+    """Independent check: scipy's RegularGridInterpolator on the lattice padded by
+    one periodic image gives the same values."""
+    from scipy.interpolate import RegularGridInterpolator
+    from oracle import interp as OI
+    cnx, cny, cnz = 7, 4, 9
+    cell = (2.1, 1.3, 4.4)
+    Vc = np.random.default_rng(9).normal(size=(cnz, cny, cnx))
+    pad = np.pad(Vc, ((0, 1), (0, 1), (0, 1)), mode="wrap")
+    axes = [np.arange(n + 1) * L / n for n, L in ((cnz, cell[2]), (cny, cell[1]), (cnx, cell[0]))]
+    f = RegularGridInterpolator(axes, pad)
+    h, origin = (0.23, 0.17, 0.31), (0.05, 0.4, -1.0)
+    V = OI.trilinear_periodic(Vc, cell, origin, (10, 7, 12), h)
+    pts = []
+    for k in range(10):
+        for j in range(7):
+            for i in range(12):
+                pts.append([((k * h[2] - origin[2]) % cell[2]), ((j * h[1] - origin[1]) % cell[1]),
+                            ((i * h[0] - origin[0]) % cell[0])])
+    ref = f(np.array(pts)).reshape(10, 7, 12)
+    assert np.abs(V - ref).max() < 1e-12
