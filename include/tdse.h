@@ -135,6 +135,18 @@ TDSE_API tdse_status tdse_set_stream(tdse_ctx *ctx, void *cuda_stream);
  * (Sec. 2.3 interpolates a DFT potential; any gridded V is accepted). */
 TDSE_API tdse_status tdse_set_potential(tdse_ctx *ctx, int member, const double *V, int on_device);
 
+/* Potential of member m interpolated from one periodic cell (Sec. 2.3: the
+ * electrostatic potential of a unit cell, expanded and interpolated onto the
+ * mesh, the step the paper found dominant).  Vc[cnz][cny][cnx] holds the cell's
+ * potential at origin + (i Lx/cnx, j Ly/cny, k Lz/cnz), cell = (Lx, Ly, Lz); the
+ * cell repeats in every axis.  V at node (i hx, j hy, k hz) is the trilinear
+ * interpolation of that periodic lattice, computed in FP64 on the GPU, then used
+ * exactly like tdse_set_potential.  EINVAL: NULL pointer, cnx/cny/cnz < 1, a
+ * cell length <= 0, or a non-finite cell length or origin. */
+TDSE_API tdse_status tdse_set_potential_grid(tdse_ctx *ctx, int member, const double *Vc, int cnx,
+                                             int cny, int cnz, const double cell[3],
+                                             const double origin[3], int on_device);
+
 /* Build V on the GPU from n atoms, xyzZ[n][4] = (x, y, z, Z):
  * V(r) = -sum_a Z_a phi(|r - r_a|), phi = 1/sqrt(r^2 + a^2) minus its second-order
  * Taylor polynomial in r^2 about r_cut for r < r_cut, 0 beyond; minimum-image

@@ -700,6 +700,56 @@ cudaError_t launch_field_io(const MemberDev &m, void *field, int elem, double *a
     return cudaGetLastError();
 }
 
+// Trilinear interpolation of a periodic cell lattice Vc[cnz][cny][cnx] (cell lengths L,
+// lattice origin o) at every grid node (i hx, j hy, k hz) into V[nz][ny][nx] (FP64).
+__global__ void interp_kernel(int nx, int ny, int nz, double hx, double hy, double hz,
+                              const double *__restrict__ Vc, int cnx, int cny, int cnz, double Lx,
+                              double Ly, double Lz, double ox, double oy, double oz,
+                              double *__restrict__ V)
+{
+    const long long cells = static_cast<long long>(nx) * ny * nz;
+    auto locate = [](double pos, double o, double L, int n, int &i0, int &i1, double &f) {
+        const double u = (pos - o) / L * n;
+        const double fl = floor(u);
+        f = u - fl;
+        long long k = static_cast<long long>(fl) % n;
+        if (k < 0) k += n;
+        i0 = static_cast<int>(k);
+        i1 = i0 + 1 == n ? 0 : i0 + 1;
+    };
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % nx);
+        const int y = static_cast<int>((t / nx) % ny);
+        const int z = static_cast<int>(t / (static_cast<long long>(nx) * ny));
+        int x0, x1, y0, y1, z0, z1;
+        double fx, fy, fz;
+        locate(x * hx, ox, Lx, cnx, x0, x1, fx);
+        locate(y * hy, oy, Ly, cny, y0, y1, fy);
+        locate(z * hz, oz, Lz, cnz, z0, z1, fz);
+        auto at = [&](int k, int j, int i) {
+            return Vc[(static_cast<long long>(k) * cny + j) * cnx + i];
+        };
+        const double c00 = at(z0, y0, x0) * (1 - fx) + at(z0, y0, x1) * fx;
+        const double c01 = at(z0, y1, x0) * (1 - fx) + at(z0, y1, x1) * fx;
+        const double c10 = at(z1, y0, x0) * (1 - fx) + at(z1, y0, x1) * fx;
+        const double c11 = at(z1, y1, x0) * (1 - fx) + at(z1, y1, x1) * fx;
+        const double c0 = c00 * (1 - fy) + c01 * fy;
+        const double c1 = c10 * (1 - fy) + c11 * fy;
+        V[t] = c0 * (1 - fz) + c1 * fz;
+    }
+}
+
+cudaError_t launch_interp(const MemberDev &m, double hx, double hy, double hz, const double *Vc,
+                          int cnx, int cny, int cnz, const double L[3], const double o[3], double *V,
+                          cudaStream_t s)
+{
+    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    interp_kernel<<<grid_for(cells), kThreads, 0, s>>>(m.nx, m.ny, m.nz, hx, hy, hz, Vc, cnx, cny,
+                                                       cnz, L[0], L[1], L[2], o[0], o[1], o[2], V);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_observables(const MemberDev &m, int precision, int buf, double *partials,
                                double *record, int *status, double q_ref, long long step,
                                cudaStream_t s)

@@ -808,6 +808,51 @@ tdse_status tdse_set_potential(tdse_ctx *c, int member, const double *V, int on_
     return st;
 }
 
+tdse_status tdse_set_potential_grid(tdse_ctx *c, int member, const double *Vc, int cnx, int cny,
+                                    int cnz, const double cell[3], const double origin[3],
+                                    int on_device)
+{
+    TRY(check_member(c, member));
+    if (!Vc || !cell || !origin) return fail(c, TDSE_EINVAL, "NULL argument");
+    if (cnx < 1 || cny < 1 || cnz < 1) return fail(c, TDSE_EINVAL, "empty cell lattice");
+    for (int a = 0; a < 3; ++a)
+        if (!(cell[a] > 0 && std::isfinite(cell[a]) && std::isfinite(origin[a])))
+            return fail(c, TDSE_EINVAL, "cell lengths must be positive and finite, origin finite");
+    TRY(ensure_device(c));
+    Member &mb = c->m[member];
+    const size_t cbytes = static_cast<size_t>(cnx) * cny * cnz * sizeof(double);
+    const size_t bytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz * sizeof(double);
+    void *tmpc = nullptr, *tmpv = nullptr;
+    auto release = [&]() {
+        cudaStreamSynchronize(c->stream);
+        dfree(c, tmpc);
+        dfree(c, tmpv);
+    };
+    const double *Vcd = Vc;
+    tdse_status st = TDSE_OK;
+    if (!on_device) {
+        if ((st = dalloc(c, cbytes, &tmpc)) != TDSE_OK) return st;
+        if (cudaMemcpyAsync(tmpc, Vc, cbytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            release();
+            return fail(c, TDSE_ECUDA, "copy of the cell potential failed");
+        }
+        Vcd = static_cast<const double *>(tmpc);
+    }
+    if ((st = dalloc(c, bytes, &tmpv)) != TDSE_OK) {
+        release();
+        return st;
+    }
+    if (launch_interp(mb.dev, mb.p.hx, mb.p.hy, mb.p.hz, Vcd, cnx, cny, cnz, cell, origin,
+                      static_cast<double *>(tmpv), c->stream) != cudaSuccess) {
+        release();
+        return fail(c, TDSE_ECUDA, "interpolation kernel failed");
+    }
+    st = potential_to_d(c, mb, static_cast<const double *>(tmpv));
+    release();
+    mb.atoms.clear();
+    return st;
+}
+
 tdse_status tdse_set_atoms(tdse_ctx *c, int member, int n, const double *xyzZ, double soft_a2,
                            double r_cut)
 {

@@ -101,6 +101,10 @@ cudaError_t launch_scale_half(const MemberDev &m, const double *V64, const doubl
                               cudaStream_t s);
 cudaError_t launch_set_state(const MemberDev &m, const double *R64, const double *I64,
                              int precision, int buf, cudaStream_t s);
+// Trilinear interpolation of a periodic cell potential onto the grid (FP64, unpadded).
+cudaError_t launch_interp(const MemberDev &m, double hx, double hy, double hz, const double *Vc,
+                          int cnx, int cny, int cnz, const double L[3], const double o[3], double *V,
+                          cudaStream_t s);
 // Eq. 15 density of plane det_k at the current time level into out[ny][nx] (FP64).
 cudaError_t launch_frame(const MemberDev &m, int precision, int buf, double *out, cudaStream_t s);
 cudaError_t launch_get_state(const MemberDev &m, double *R64, double *I64, int precision,

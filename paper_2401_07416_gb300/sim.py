@@ -49,6 +49,10 @@ class Sim:
     def set_potential(self, member: int, V):
         T.tdse_set_potential(self.ctx, member, V)
 
+    def set_potential_grid(self, member: int, Vc, cell, origin=(0.0, 0.0, 0.0)):
+        """Potential interpolated from one periodic cell (Sec. 2.3)."""
+        T.tdse_set_potential_grid(self.ctx, member, Vc, cell, origin)
+
     def potential(self, member: int = 0) -> np.ndarray:
         g = self.grids[member]
         V = np.zeros((g.nz, g.ny, g.nx))

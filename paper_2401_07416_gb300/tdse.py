@@ -85,6 +85,7 @@ SIGNATURES = {
     "tdse_get_state": (_I, [_VP, _I, _VP, _VP, _I]),
     "tdse_get_flux_map": (_I, [_VP, _I, _VP, _I]),
     "tdse_set_frame_capacity": (_I, [_VP, _I, _I]),
+    "tdse_set_potential_grid": (_I, [_VP, _I, _VP, _I, _I, _I, _VP, _VP, _I]),
     "tdse_get_frames": (_I, [_VP, _I, _VP, _VP, _I, ctypes.POINTER(_I), _I]),
     "tdse_dissimilarity": (_I, [_VP, _I, _I, ctypes.c_longlong, _VP, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, _VP, _I, _VP]),
@@ -253,6 +254,16 @@ def tdse_get_flux_map(ctx, member: int, F):
     p, dev, _ = _arg(F, writable=True)
     _check(ctx, lib().tdse_get_flux_map(ctx, member, p, dev))
     return F
+
+
+def tdse_set_potential_grid(ctx, member: int, Vc, cell, origin=(0.0, 0.0, 0.0)):
+    """Potential interpolated from one periodic cell Vc[cnz][cny][cnx] of lengths
+    `cell` whose lattice starts at `origin` (numpy or torch CUDA float64)."""
+    pv, dev, keep = _arg(Vc)
+    cnz, cny, cnx = tuple(Vc.shape)
+    c = (ctypes.c_double * 3)(*cell)
+    o = (ctypes.c_double * 3)(*origin)
+    _check(ctx, lib().tdse_set_potential_grid(ctx, member, pv, cnx, cny, cnz, c, o, dev))
 
 
 def tdse_set_frame_capacity(ctx, member: int, capacity: int):

@@ -274,3 +274,30 @@ def test_eq10_absorbing_layer_matches_oracle(T, precision):
         assert l2rel(np.concatenate([Rg, Ig]), np.concatenate([Ro, Io])) < TOL32_L2
         assert abs(og["Q"] - oo["Q"]) / oo["Q"] < TOL32_Q
     assert oo["Q"] < 0.999   # the layer absorbed part of the packet
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_potential_interpolated_from_a_periodic_cell(T, on_device):
+    """Sec. 2.3's expansion + interpolation of a cell potential, on the GPU, against
+    the oracle's trilinear interpolation (FP64, lattice incommensurate with the grid,
+    origin off the grid, ragged sizes)."""
+    import torch
+    from oracle import interp as OI
+    g = W.small_grid(36, 22, 31, h=(0.21, 0.19, 0.23), bc=(0, 0, 1))
+    rng = np.random.default_rng(14)
+    Vc = rng.normal(scale=3.0, size=(29, 11, 13))
+    cell, origin = (2.73, 1.91, 6.05), (0.37, -0.52, 0.8)
+    Vo = OI.trilinear_periodic(Vc, cell, origin, (g.nz, g.ny, g.nx), (g.hx, g.hy, g.hz))
+    s = make_sim(g, T.FP64)
+    src = torch.from_numpy(Vc).cuda() if on_device else Vc
+    s.set_potential_grid(0, src, cell, origin)
+    Vg = s.potential(0)
+    s.close()
+    assert np.abs(Vg - Vo).max() <= 1e-14 * np.abs(Vo).max()
+    with pytest.raises(T.TdseError) as e:
+        s2 = make_sim(g, T.FP64)
+        try:
+            s2.set_potential_grid(0, Vc, (2.73, 0.0, 6.05), origin)
+        finally:
+            s2.close()
+    assert e.value.status == T.EINVAL
