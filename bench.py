@@ -145,17 +145,20 @@ def kernel_source_hash() -> str:
 
 
 def ncu_traffic(variant: str, cells: int):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
-    scaled to `cells` grid nodes; None if absent or taken on another kernel build."""
+    """(DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    scaled to `cells` grid nodes, or None; why it is None)."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
-        e = d[variant]
-        if e.get("source_hash") != kernel_source_hash():
-            return None
-        return e["dram_bytes_per_launch"] * cells / e["cells"]
-    except Exception:
-        return None
+    except OSError as e:
+        return None, f"no traffic file: {e}"
+    if variant not in d:
+        return None, f"no ncu capture of variant {variant}"
+    e = d[variant]
+    h = kernel_source_hash()
+    if e.get("source_hash") != h:
+        return None, f"kernel sources changed since the capture ({e.get('source_hash')} != {h})"
+    return e["dram_bytes_per_launch"] * cells / e["cells"], "ncu capture on the 256x256x512 case, scaled by nodes"
 
 
 # ------------------------------------------------------------------ CPU oracle timing
@@ -353,6 +356,45 @@ def absorber_reflection(torch, T):
     return out
 
 
+def paper_cu111_throughput(torch, T, steps=400, warmup=8):
+    """The paper's benchmark geometry (Sec. 3.1: 240 x 240 x 420 + 100 absorbing
+    planes = 29,952,000 nodes, anisotropic spacing, Eq. 11 time step, Eq. 4 packet)
+    with the synthetic Cu(111)-like slab, FP32 + Kahan, autotuned; cell-updates/s
+    over `steps` steps (context: the paper reports about 6 ns per node and step on
+    its Quadro K620)."""
+    wl = W.cu111(W.FP32_KAHAN)
+    g = wl.grid
+    s = make_ctx(T, wl, W.FP32_KAHAN, 0)
+    ms, prof = timed_steps(torch, T, s, steps, warmup, lambda: None)
+    tun = s.tuning()
+    s.close()
+    return {"nodes": g.cells, "steps": steps, "value": g.cells * steps / (ms * 1e-3),
+            "unit": "cell-updates/s", "ns_per_node_step": ms * 1e6 / (g.cells * steps),
+            "variant": tun["name"][prof["steps_per_launch"]],
+            "steps_per_launch": prof["steps_per_launch"]}
+
+
+def interpolation_cost(torch, T):
+    """Sec. 2.3's expansion + interpolation of a cell potential onto the paper's mesh
+    size (240 x 240 x 520 nodes, FP64 context) from a 96 x 96 x 560 periodic cell
+    lattice on the device: the whole tdse_set_potential_grid call (interpolation,
+    d build, ghost zones), wall clock after a warm-up call."""
+    from paper_2401_07416_gb300.sim import Sim
+    g = W.Grid(nx=240, ny=240, nz=520, hx=0.322, hy=0.322, hz=0.3149, dt=0.0,
+               bc=(W.PERIODIC, W.PERIODIC, W.PERIODIC), obs_every=10 ** 6)
+    Vc = torch.from_numpy(np.random.default_rng(23).normal(size=(560, 96, 96))).cuda()
+    cell = (g.nx * g.hx / 15 * 6, g.ny * g.hy / 15 * 6, g.nz * g.hz)
+    with Sim(g, precision=W.FP64) as s:
+        s.set_potential_grid(0, Vc, cell)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_potential_grid(0, Vc, cell)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+    return {"nodes": g.cells, "cell_lattice": [96, 96, 560], "ms": el * 1e3,
+            "nodes_per_s": g.cells / el}
+
+
 def dissimilarity_cost(torch, T, K=48, M=100, ny=128, nx=128):
     """Eq. 16 over a batch of K synthetic detector-density trajectories (M frames of
     ny x nx pixels, seeded, on the device), the whole window: FP64 pairwise kernel."""
@@ -468,9 +510,9 @@ def main():
     bytes_launch = BYTES_PER_NODE[prec] * cells
     achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
     variant = tuning["name"][tb]
-    traffic = ncu_traffic(variant, cells)
+    traffic, traffic_note = ncu_traffic(variant, cells)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic,
+                "frac": achieved / hbm_peak, "traffic": traffic, "traffic_source": traffic_note,
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS hbm_gbs)",
                 "kernel": f"{'fused_step_tmem_kernel' if 'tmem' in variant else 'fused_step_kernel'} "
                           f"{variant} ({tb} steps per launch)",
@@ -503,6 +545,8 @@ def main():
         extras["adjoint_96x96x192_3000"] = adjoint_cost(torch, T)
         extras["dissimilarity_48x100x128x128"] = dissimilarity_cost(torch, T)
         extras["absorbing_layer_reflection"] = absorber_reflection(torch, T)
+        extras["potential_interp_240x240x520"] = interpolation_cost(torch, T)
+        extras["paper_cu111_240x240x520"] = paper_cu111_throughput(torch, T)
 
         # end to end through the C ABI from pinned host buffers: potential in,
         # packet set-up, the steps, flux map and observables out

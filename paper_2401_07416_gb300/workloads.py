@@ -220,6 +220,59 @@ def config5(precision: int = FP32_KAHAN) -> Workload:
                     steps=1000, precision=precision)
 
 
+# Atomic-unit conversions for the paper's SI / eV / angstrom settings.
+BOHR_PER_ANGSTROM = 1.0 / 0.529177210903
+HARTREE_PER_EV = 1.0 / 27.211386245988
+
+
+def wavevector_from_energy(E: float, hbar: float = 1.0, mass: float = 1.0) -> float:
+    """Eq. 4: lambda = sqrt(2 hbar^2 pi^2 / (m E)), so |k| = 2 pi / lambda = sqrt(2 m E) / hbar."""
+    lam = math.sqrt(2.0 * hbar * hbar * math.pi * math.pi / (mass * E))
+    return 2.0 * math.pi / lam
+
+
+def cu111(precision: int = FP32_KAHAN, nx: int = 240, ny: int = 240, nz: int = 420,
+          cap_planes: int = 100, cap_strength: float = 2.0) -> Workload:
+    """The paper's Cu(111) electron-diffraction geometry (Sec. 2.1 and Sec. 3.1) with a
+    synthetic potential.
+
+    Mesh: 240 x 240 x 420 nodes over 35.4 x 35.4 x 70 angstrom (anisotropic: h_x =
+    h_y = 0.1475 A, h_z = 0.1667 A; the 35.4 A extent is the one that reproduces
+    Eq. 11's 0.38 as), plus `cap_planes` absorbing planes appended at the bottom of
+    a z-periodic domain (Eq. 10's set-up, here as the quadratic split-step layer of
+    strength `cap_strength` Ha).  dt from Eq. 11.  Packet (Eqs. 3-4): sigma = 1.8 A,
+    E = 60 eV, centred in x, y at r_z0 = 42 A above the appended region, moving -z.
+    Slab (synthetic stand-in for the DFT potential): four Cu(111)-like layers of
+    15 x 15 atoms, 2.087 A apart with the top layer at 30 A, each layer's square
+    lattice shifted by a third of a site from the one above (ABC stacking), charge
+    11 (the 3d10 4s1 valence shell) in the softened Coulomb form.  The detector
+    plane sits at 37.6 A (Sec. 2.3).  Smaller nx, ny keep the spacings and the atom
+    density (15 atoms per 240 nodes; a narrow window of the same geometry for tests)."""
+    A = BOHR_PER_ANGSTROM
+    hx = hy = 35.4 / 240 * A
+    hz = 70.0 / 420 * A
+    z0 = cap_planes * hz                       # the physical domain starts above the layer
+    lx, ly = nx * hx, ny * hy
+    g = Grid(nx=nx, ny=ny, nz=nz + cap_planes, hx=hx, hy=hy, hz=hz, dt=0.0,
+             bc=(PERIODIC, PERIODIC, PERIODIC), mask_lo=cap_planes, mask_hi=0,
+             mask_eta=cap_strength, mask_kind=MASK_CAP,
+             det_k=min(nz + cap_planes - 2, int(round(z0 / hz + 37.6 * A / hz))), obs_every=20)
+    n_side = max(1, round(15 * nx / 240))
+    ax, ay = lx / n_side, ly / n_side
+    rows = []
+    for layer in range(4):
+        z = z0 + (30.0 - 2.087 * layer) * A
+        shift = (layer % 3) / 3.0
+        for j in range(n_side):
+            for i in range(n_side):
+                rows.append(((i + 0.5 + shift) * ax % lx, (j + 0.5 + shift) * ay % ly, z, 11.0))
+    atoms = np.array(rows)
+    k = wavevector_from_energy(60.0 * HARTREE_PER_EV)
+    packet = Packet((0.5 * lx, 0.5 * ly, z0 + 42.0 * A), (1.8 * A, 1.8 * A, 1.8 * A), (0.0, 0.0, -k))
+    return Workload("Cu(111) 240x240x420 + 100 CAP planes", g, packet, atoms, steps=8000,
+                    precision=precision)
+
+
 def random_field(shape, seed: int, scale: float = 1.0) -> np.ndarray:
     """Seeded standard-normal test array (FP64)."""
     return np.random.default_rng(seed).normal(0.0, scale, size=shape)

@@ -301,3 +301,34 @@ def test_potential_interpolated_from_a_periodic_cell(T, on_device):
         finally:
             s2.close()
     assert e.value.status == T.EINVAL
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32_KAHAN"])
+def test_paper_cu111_geometry_window(T, precision):
+    """The paper's Cu(111) run set-up (anisotropic 35.4 x 35.4 x 70 A mesh spacing,
+    100 appended Eq. 10 absorbing planes on a z-periodic domain, Eq. 11 time step,
+    Eq. 4 packet at 60 eV) on a 32 x 32 window in x, y, against the oracle."""
+    import dataclasses
+    wl = W.cu111(nx=32, ny=32)
+    g = wl.grid                                   # dt = 0: the library applies Eq. 11
+    go = dataclasses.replace(g, dt=oracle.default_dt(g.hx, g.hy, g.hz))   # the oracle, explicitly
+    V = oracle.potential_atoms(go, wl.atoms)
+    R0, I0 = oracle.initial_state(go, wl.packet, V)
+    n = 30
+    Ro, Io, Fo, _ = oracle.run(go, V, R0, I0, n)
+    oo = oracle.observables(go, V, Ro, Io)
+    from paper_2401_07416_gb300.sim import Sim
+    with Sim(g, precision=getattr(T, precision)) as s:
+        s.set_atoms(0, wl.atoms)
+        s.set_packet(0, wl.packet)
+        s.step(n)
+        Rg, Ig = s.state(0)
+        og = s.observables(0)
+        assert og["t"] == pytest.approx(n * go.dt, rel=1e-15)
+    if precision == "FP64":
+        scale = max(np.abs(Ro).max(), np.abs(Io).max())
+        assert max(np.abs(Rg - Ro).max(), np.abs(Ig - Io).max()) / scale < TOL64
+        assert og["Q"] == pytest.approx(oo["Q"], rel=TOL64)
+    else:
+        assert l2rel(np.concatenate([Rg, Ig]), np.concatenate([Ro, Io])) < TOL32_L2
+        assert abs(og["Q"] - oo["Q"]) / oo["Q"] < TOL32_Q
