@@ -71,6 +71,13 @@ def dist_info():
     return rank, world, local
 
 
+def job_time_and_value(ms_local: float, cells: int, steps: int, world: int, reduce_max):
+    """Max over ranks of the timed region (ms) and the whole-job value: every rank
+    advances its own replica of `cells` nodes for `steps` steps (weak scaling)."""
+    t_max = float(reduce_max(ms_local))
+    return t_max, world * cells * steps / (t_max * 1e-3)
+
+
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -497,13 +504,15 @@ def main():
     obs = s.observables(0)
     s.close()
 
-    t_max = ms
-    if world > 1:
+    def reduce_max(x):
+        if world == 1:
+            return x
         import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * cells * args.steps / (t_max * 1e-3)
+        return t.item()
+
+    t_max, value = job_time_and_value(ms, cells, args.steps, world, reduce_max)
 
     tb = prof["steps_per_launch"]
     launch_ms = prof["step_ms"] / max(1, prof["step_launches"])
