@@ -79,6 +79,7 @@ def _params(**kw):
     ("mask_lo", 30),
     ("precision", 7),
     ("tblock", 5),
+    ("mask_kind", 2),      # neither cos^2 nor the Eq. 10 absorbing potential
 ])
 def test_create_rejects_bad_parameters(lib, field, value):
     with pytest.raises(T.TdseError) as e:
@@ -114,6 +115,32 @@ def test_call_order_and_no_gpu_errors(lib):
             assert e.value.status in (T.ECUDA, T.ENOMEM)
     finally:
         T.tdse_destroy(ctx)
+
+
+def test_new_entry_points_validate_before_device_work(lib):
+    """Argument checks of the frame buffer, the cell-potential interpolation and the
+    Eq. 16 dissimilarity answer EINVAL without touching a GPU."""
+    import numpy as np
+    ctx = T.tdse_create([_params(det_k=-1)])
+    try:
+        with pytest.raises(T.TdseError) as e:
+            T.tdse_set_frame_capacity(ctx, 0, 4)            # no detector plane
+        assert e.value.status == T.EINVAL
+        with pytest.raises(T.TdseError) as e:
+            T.tdse_set_potential_grid(ctx, 0, np.zeros((3, 3, 3)), (1.0, -1.0, 1.0))
+        assert e.value.status == T.EINVAL
+        with pytest.raises(T.TdseError) as e:
+            T.tdse_set_potential_grid(ctx, 0, np.zeros((3, 3, 3)), (1.0, 1.0, 1.0),
+                                      (0.0, float("nan"), 0.0))
+        assert e.value.status == T.EINVAL
+    finally:
+        T.tdse_destroy(ctx)
+    f = np.zeros((2, 3, 4))
+    t = np.array([0.0, 1.0, 2.0])
+    for args in [(f, t, 1.0, 1.0, 0.1), (f, t, 0.0, 1.0, -1.0), (f, t, 5.0, 6.0, 0.1)]:
+        with pytest.raises(T.TdseError) as e:
+            T.tdse_dissimilarity(*args)
+        assert e.value.status == T.EINVAL
 
 
 def test_version_string(lib):
