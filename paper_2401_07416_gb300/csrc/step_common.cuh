@@ -236,5 +236,76 @@ struct ItemScalars {
     int per_x, per_y, per_z, det_k, mask_lo, mask_hi;
 };
 
+// Thread 0 of a fused-step CTA: take the next work item (member, xy tile, z-chunk)
+// from the counter into *item and, if there is one, stage the member's scalars in
+// shared memory (loop invariants then never come back from global memory).
+__device__ __forceinline__ void fetch_item(const MemberDev *__restrict__ members,
+                                           const WorkDev *__restrict__ work, int *counter,
+                                           int in_buf, int *item, ItemScalars &S)
+{
+    const int it_ = atomicAdd(counter, 1);
+    *item = it_;
+    if (it_ >= work->total) return;
+    int mm = 0;
+    while (it_ >= work->item_begin[mm + 1]) ++mm;
+    const MemberDev &Mm = members[mm];
+    const int local = it_ - work->item_begin[mm];
+    const int ntx = work->tiles_x[mm], nty = work->tiles_y[mm];
+    S.m = mm;
+    S.tile_x = local % ntx;
+    S.tile_y = (local / ntx) % nty;
+    S.kz0 = (local / (ntx * nty)) * work->chunk[mm];
+    S.kz1 = min(S.kz0 + work->chunk[mm], Mm.nz);
+    S.nx = Mm.nx; S.ny = Mm.ny; S.nz = Mm.nz; S.G = Mm.G;
+    S.per_x = Mm.per_x; S.per_y = Mm.per_y; S.per_z = Mm.per_z;
+    S.det_k = Mm.det_k; S.mask_lo = Mm.mask_lo; S.mask_hi = Mm.mask_hi;
+    S.pitch = Mm.pitch; S.plane = Mm.plane;
+    S.cx = Mm.cx; S.cy = Mm.cy; S.cz = Mm.cz; S.cj = Mm.cj; S.dt = Mm.dt;
+    S.mask = Mm.mask; S.flux = Mm.flux; S.jlast = Mm.jlast;
+    S.outR = Mm.R[1 - in_buf]; S.outI = Mm.I[1 - in_buf];
+    S.outCR = Mm.cR[1 - in_buf]; S.outCI = Mm.cI[1 - in_buf];
+}
+
+// One output row of the last stage at offset o of the padded arrays: R, I (and the
+// compensation terms), plus the ghost copies of periodic axes when the row touches
+// a seam (both sides when an axis is shorter than twice the ghost width).
+template <typename Real, bool KAHAN, int VEC>
+__device__ __forceinline__ void store_output_row(const ItemScalars &S, Real *outR, Real *outI,
+                                                 Real *outCR, Real *outCI, long long o,
+                                                 long long pitch, bool seam, int xs, int y,
+                                                 const Real (&r)[VEC], const Real (&i)[VEC],
+                                                 const Real (&cr)[VEC], const Real (&ci)[VEC])
+{
+    st_vec<Real>(outR + o, r);
+    st_vec<Real>(outI + o, i);
+    if constexpr (KAHAN) {
+        st_vec<Real>(outCR + o, cr);
+        st_vec<Real>(outCI + o, ci);
+    }
+    if (!seam) return;
+    const int G = S.G, nx = S.nx, ny = S.ny;
+    int dxs[3] = {0, 0, 0}, dys[3] = {0, 0, 0};
+    int ndx = 1, ndy = 1;
+    if (S.per_x) {
+        if (xs < G) dxs[ndx++] = nx;
+        if (xs >= nx - G) dxs[ndx++] = -nx;
+    }
+    if (S.per_y) {
+        if (y < G) dys[ndy++] = ny;
+        if (y >= ny - G) dys[ndy++] = -ny;
+    }
+    for (int a = 0; a < ndy; ++a)
+        for (int b = 0; b < ndx; ++b) {
+            if (a == 0 && b == 0) continue;
+            const long long og = o + dys[a] * pitch + dxs[b];
+            st_vec<Real>(outR + og, r);
+            st_vec<Real>(outI + og, i);
+            if constexpr (KAHAN) {
+                st_vec<Real>(outCR + og, cr);
+                st_vec<Real>(outCI + og, ci);
+            }
+        }
+}
+
 }  // namespace
 }  // namespace tdse

@@ -164,30 +164,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     long long gbase = 0;   // loads issued by this CTA before the current item
 
     for (;;) {
-        if (tid == 0) {
-            const int it_ = atomicAdd(counter, 1);
-            s_item = it_;
-            if (it_ < work->total) {
-                int mm = 0;
-                while (it_ >= work->item_begin[mm + 1]) ++mm;
-                const MemberDev &Mm = members[mm];
-                const int local = it_ - work->item_begin[mm];
-                const int ntx = work->tiles_x[mm], nty = work->tiles_y[mm];
-                S.m = mm;
-                S.tile_x = local % ntx;
-                S.tile_y = (local / ntx) % nty;
-                S.kz0 = (local / (ntx * nty)) * work->chunk[mm];
-                S.kz1 = min(S.kz0 + work->chunk[mm], Mm.nz);
-                S.nx = Mm.nx; S.ny = Mm.ny; S.nz = Mm.nz; S.G = Mm.G;
-                S.per_x = Mm.per_x; S.per_y = Mm.per_y; S.per_z = Mm.per_z;
-                S.det_k = Mm.det_k; S.mask_lo = Mm.mask_lo; S.mask_hi = Mm.mask_hi;
-                S.pitch = Mm.pitch; S.plane = Mm.plane;
-                S.cx = Mm.cx; S.cy = Mm.cy; S.cz = Mm.cz; S.cj = Mm.cj; S.dt = Mm.dt;
-                S.mask = Mm.mask; S.flux = Mm.flux; S.jlast = Mm.jlast;
-                S.outR = Mm.R[1 - in_buf]; S.outI = Mm.I[1 - in_buf];
-                S.outCR = Mm.cR[1 - in_buf]; S.outCI = Mm.cI[1 - in_buf];
-            }
-        }
+        if (tid == 0) fetch_item(members, work, counter, in_buf, &s_item, S);
         __syncthreads();
         const int item = s_item;
         if (item >= work->total) break;
@@ -469,37 +446,10 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                                     if constexpr (C::KAHAN) vci[r][v] = mul_rn(vci[r][v], mq);
                                 }
                             }
-                            const long long o = zoff + out0 + r * pitch;
-                            st_vec<Real>(outR + o, out[r]);
-                            st_vec<Real>(outI + o, vi[r]);
-                            if constexpr (C::KAHAN) {
-                                st_vec<Real>(outCR + o, cout[r]);
-                                st_vec<Real>(outCI + o, vci[r]);
-                            }
-                            if (seam) {   // ghost copies of periodic axes (both sides if n < 2G)
-                                const int y = ys0 + r;
-                                int dxs[3] = {0, 0, 0}, dys[3] = {0, 0, 0};
-                                int ndx = 1, ndy = 1;
-                                if (S.per_x) {
-                                    if (xs < G) dxs[ndx++] = nx;
-                                    if (xs >= nx - G) dxs[ndx++] = -nx;
-                                }
-                                if (S.per_y) {
-                                    if (y < G) dys[ndy++] = ny;
-                                    if (y >= ny - G) dys[ndy++] = -ny;
-                                }
-                                for (int a = 0; a < ndy; ++a)
-                                    for (int b = 0; b < ndx; ++b) {
-                                        if (a == 0 && b == 0) continue;
-                                        const long long og = o + dys[a] * pitch + dxs[b];
-                                        st_vec<Real>(outR + og, out[r]);
-                                        st_vec<Real>(outI + og, vi[r]);
-                                        if constexpr (C::KAHAN) {
-                                            st_vec<Real>(outCR + og, cout[r]);
-                                            st_vec<Real>(outCI + og, vci[r]);
-                                        }
-                                    }
-                            }
+                            store_output_row<Real, C::KAHAN, VEC>(S, outR, outI, outCR, outCI,
+                                                                  zoff + out0 + r * pitch, pitch,
+                                                                  seam, xs, ys0 + r, out[r], vi[r],
+                                                                  cout[r], vci[C::KAHAN ? r : 0]);
                         }
                     }
                 }
