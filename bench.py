@@ -572,19 +572,27 @@ def main():
         barrier()
         t0 = time.perf_counter()
         T.tdse_set_potential(se.ctx, 0, V_host)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         se.set_packet(0, wl.packet)
+        t2 = time.perf_counter()
         se.step(args.steps)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
         T.tdse_get_flux_map(se.ctx, 0, F_host)
         se.observables(0)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        phases_ms = {"set_potential_h2d": (t1 - t0) * 1e3, "set_wavepacket": (t2 - t1) * 1e3,
+                     "steps": (t3 - t2) * 1e3, "flux_and_observables_d2h": (time.perf_counter() - t3) * 1e3}
         barrier()
         se.close()
         e2e = {"value": world * cells * args.steps / el, "unit": "cell-updates/s",
                "h2d_bytes_per_step": V_host.numel() * 8 / args.steps,
                "d2h_bytes_per_step": (F_host.numel() * 8 + 64) / args.steps,
                "includes": "tdse_set_potential (pinned host V, FP64), tdse_set_wavepacket, "
-                           "tdse_step (CUDA-graph replay), tdse_get_flux_map, tdse_observables"}
+                           "tdse_step (CUDA-graph replay), tdse_get_flux_map, tdse_observables",
+               "phases_ms": phases_ms}
         del V_host
         if rank == 0 and world == 1:
             cpu = time_oracle(args.cpu_seconds)

@@ -236,92 +236,89 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return s;   // valid in thread 0
 }
 
-__global__ void packet_kernel(MemberDev m, PacketArgs P, double *__restrict__ R,
-                              double *__restrict__ I, double *__restrict__ partials)
+// Eq. 3 factorises over the axes: psi0(r) = prod_a g_a(r_a) exp(i k_a (r_a - r0_a)) with
+// g_a = exp(-(r_a - r0_a)^2 / (2 sigma_a^2)) (1 on a plane-wave axis, sigma_a <= 0).
+// One block per axis writes that axis' complex factors and the sum of their squared
+// moduli; the product of the three sums times h^3 is the discrete norm of psi0.
+__global__ void packet_axes_kernel(MemberDev m, PacketArgs P, double2 *__restrict__ fac,
+                                   double *__restrict__ sums)
 {
     __shared__ double sh[32];
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const int a = blockIdx.x;
+    const int n = a == 0 ? m.nx : a == 1 ? m.ny : m.nz;
+    const double h = a == 0 ? m.hx : a == 1 ? m.hy : m.hz;
+    double2 *f = fac + (a == 0 ? 0 : a == 1 ? m.nx : m.nx + m.ny);
     double acc = 0.0;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(t % m.nx);
-        const int y = static_cast<int>((t / m.nx) % m.ny);
-        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
-        const double r[3] = {x * m.hx, y * m.hy, z * m.hz};
-        double amp = 1.0, phase = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            const double d = r[a] - P.r0[a];
-            if (P.sigma[a] > 0.0) amp *= exp(-d * d / (2.0 * P.sigma[a] * P.sigma[a]));
-            phase += P.k0[a] * d;
-        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double d = i * h - P.r0[a];
+        const double amp = P.sigma[a] > 0.0 ? exp(-d * d / (2.0 * P.sigma[a] * P.sigma[a])) : 1.0;
         double sn, cs;
-        sincos(phase, &sn, &cs);
-        R[t] = amp * cs;
-        I[t] = amp * sn;
+        sincos(P.k0[a] * d, &sn, &cs);
+        f[i] = make_double2(amp * cs, amp * sn);
         acc += amp * amp;
     }
     const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (threadIdx.x == 0) sums[a] = s;
 }
 
-__global__ void sum_partials_kernel(const double *__restrict__ partials, int n, double scale,
-                                    double *__restrict__ out)
-{
-    __shared__ double sh[32];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) out[0] = 1.0 / sqrt(s * scale);
-}
-
-// R^0 = s Re psi0, I^{-1/2} = s (Im psi0 - A[Re psi0] / 2), stored as Real (+ compensation).
+// R^0 = s Re psi0 and I^{-1/2} = s (Im psi0 - A[Re psi0] / 2), stored as Real (+ the
+// compensation terms), with psi0 at a node and its neighbours formed from the axis
+// factors (x factor times y factor, times z factor) and s = 1 / sqrt(h^3 Sx Sy Sz).
+// Blocks take z planes, threads the cells of a plane.
 template <typename Real>
-__global__ void scale_half_kernel(MemberDev m, const double *__restrict__ V64,
-                                  const double *__restrict__ R, const double *__restrict__ I,
-                                  const double *__restrict__ scale, int kahan, int buf)
+__global__ void packet_start_kernel(MemberDev m, const double *__restrict__ V64,
+                                    const double2 *__restrict__ fac, const double *__restrict__ sums,
+                                    int kahan, int buf)
 {
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
-    const double s = scale[0];
+    const double s = 1.0 / sqrt(m.hx * m.hy * m.hz * sums[0] * sums[1] * sums[2]);
+    const double2 *fx = fac, *fy = fac + m.nx, *fz = fac + m.nx + m.ny;
+    auto psi = [&](int x, int y, int z) {
+        const double2 a = fx[x], b = fy[y], c = fz[z];
+        const double re = a.x * b.x - a.y * b.y, im = a.x * b.y + a.y * b.x;
+        return make_double2(re * c.x - im * c.y, re * c.y + im * c.x);
+    };
+    // Re psi0 one node away: wrap on a periodic axis, zero beyond a wall
+    auto re_nb = [&](int x, int y, int z) -> double {
+        if (x < 0 || x >= m.nx) {
+            if (!m.per_x) return 0.0;
+            x = x < 0 ? x + m.nx : x - m.nx;
+        }
+        if (y < 0 || y >= m.ny) {
+            if (!m.per_y) return 0.0;
+            y = y < 0 ? y + m.ny : y - m.ny;
+        }
+        if (z < 0 || z >= m.nz) {
+            if (!m.per_z) return 0.0;
+            z = z < 0 ? z + m.nz : z - m.nz;
+        }
+        return psi(x, y, z).x;
+    };
     Real *oR = reinterpret_cast<Real *>(m.R[buf]);
     Real *oI = reinterpret_cast<Real *>(m.I[buf]);
     Real *oCR = reinterpret_cast<Real *>(m.cR[buf]);
     Real *oCI = reinterpret_cast<Real *>(m.cI[buf]);
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(t % m.nx);
-        const int y = static_cast<int>((t / m.nx) % m.ny);
-        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
-        auto at = [&](int xx, int yy, int zz) -> double {
-            if (xx < 0 || xx >= m.nx) {
-                if (!m.per_x) return 0.0;
-                xx = (xx % m.nx + m.nx) % m.nx;
+    const int plane = m.nx * m.ny;
+    const double c0 = -2.0 * (m.cx + m.cy + m.cz);
+    for (int z = blockIdx.x; z < m.nz; z += gridDim.x)
+        for (int xy = threadIdx.x; xy < plane; xy += blockDim.x) {
+            const int x = xy % m.nx, y = xy / m.nx;
+            const double2 p0 = psi(x, y, z);
+            const double r0 = p0.x;
+            const double ar = m.cx * (re_nb(x + 1, y, z) + re_nb(x - 1, y, z)) +
+                              m.cy * (re_nb(x, y + 1, z) + re_nb(x, y - 1, z)) +
+                              m.cz * (re_nb(x, y, z + 1) + re_nb(x, y, z - 1)) +
+                              (c0 - m.cv * V64[static_cast<long long>(z) * plane + xy]) * r0;
+            const double rv = s * r0;
+            const double iv = s * (p0.y - 0.5 * ar);
+            const long long o = pidx(m, x, y, z);
+            const Real rs = static_cast<Real>(rv), is = static_cast<Real>(iv);
+            oR[o] = rs;
+            oI[o] = is;
+            if (kahan) {
+                oCR[o] = static_cast<Real>(static_cast<double>(rs) - rv);
+                oCI[o] = static_cast<Real>(static_cast<double>(is) - iv);
             }
-            if (yy < 0 || yy >= m.ny) {
-                if (!m.per_y) return 0.0;
-                yy = (yy % m.ny + m.ny) % m.ny;
-            }
-            if (zz < 0 || zz >= m.nz) {
-                if (!m.per_z) return 0.0;
-                zz = (zz % m.nz + m.nz) % m.nz;
-            }
-            return R[uidx(m, xx, yy, zz)];
-        };
-        const double r0 = R[t];
-        const double ar = m.cx * (at(x + 1, y, z) + at(x - 1, y, z)) +
-                          m.cy * (at(x, y + 1, z) + at(x, y - 1, z)) +
-                          m.cz * (at(x, y, z + 1) + at(x, y, z - 1)) +
-                          (-2.0 * (m.cx + m.cy + m.cz) - m.cv * V64[t]) * r0;
-        const double rv = s * r0;
-        const double iv = s * (I[t] - 0.5 * ar);
-        const long long o = pidx(m, x, y, z);
-        const Real rs = static_cast<Real>(rv), is = static_cast<Real>(iv);
-        oR[o] = rs;
-        oI[o] = is;
-        if (kahan) {
-            oCR[o] = static_cast<Real>(static_cast<double>(rs) - rv);
-            oCI[o] = static_cast<Real>(static_cast<double>(is) - iv);
         }
-    }
 }
 
 // ---------------------------------------------------------------- state copies
@@ -639,9 +636,14 @@ cudaError_t launch_build_d(const MemberDev &m, int elem, const double *V, double
     return cudaGetLastError();
 }
 
-cudaError_t launch_packet(const MemberDev &m, const double *r0, const double *sigma,
-                          const double *k0, double *R64, double *I64, double *partials,
-                          int nparts, double *scale, cudaStream_t s)
+size_t packet_scratch_bytes(const MemberDev &m)
+{
+    return (static_cast<size_t>(m.nx) + m.ny + m.nz) * sizeof(double2) + 4 * sizeof(double);
+}
+
+cudaError_t launch_packet_start(const MemberDev &m, const double *V64, const double *r0,
+                                const double *sigma, const double *k0, void *scratch,
+                                int precision, int buf, cudaStream_t s)
 {
     PacketArgs P;
     for (int a = 0; a < 3; ++a) {
@@ -649,21 +651,14 @@ cudaError_t launch_packet(const MemberDev &m, const double *r0, const double *si
         P.sigma[a] = sigma[a];
         P.k0[a] = k0[a];
     }
-    packet_kernel<<<nparts, kThreads, 0, s>>>(m, P, R64, I64, partials);
-    sum_partials_kernel<<<1, kThreads, 0, s>>>(partials, nparts, m.hx * m.hy * m.hz, scale);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scale_half(const MemberDev &m, const double *V64, const double *R64,
-                              const double *I64, const double *scale, int precision, int buf,
-                              cudaStream_t s)
-{
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    double2 *fac = static_cast<double2 *>(scratch);
+    double *sums = reinterpret_cast<double *>(fac + m.nx + m.ny + m.nz);
+    packet_axes_kernel<<<3, kThreads, 0, s>>>(m, P, fac, sums);
+    const int blocks = std::min(m.nz, 8192);
     if (precision == 0)
-        scale_half_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, V64, R64, I64, scale, 0, buf);
+        packet_start_kernel<double><<<blocks, kThreads, 0, s>>>(m, V64, fac, sums, 0, buf);
     else
-        scale_half_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, V64, R64, I64, scale,
-                                                                     precision == 2, buf);
+        packet_start_kernel<float><<<blocks, kThreads, 0, s>>>(m, V64, fac, sums, precision == 2, buf);
     return cudaGetLastError();
 }
 

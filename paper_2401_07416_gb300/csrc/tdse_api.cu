@@ -64,7 +64,6 @@ struct tdse_ctx {
     int *d_counter = nullptr;
     int *d_status = nullptr;
     double *d_partials = nullptr;
-    double *d_scale = nullptr;
     double *d_records = nullptr;    // [B][kRecCap][kRecLen]
     int cur = 0;                    // ping-pong buffer holding the state
     long long step = 0;
@@ -374,7 +373,6 @@ tdse_status ensure_device(tdse_ctx *c)
     TRY(dalloc(c, sizeof(int), &p)); c->d_status = static_cast<int *>(p);
     TRY(dalloc(c, kObsParts * kObsPartialsPerBlock * sizeof(double), &p));
     c->d_partials = static_cast<double *>(p);
-    TRY(dalloc(c, sizeof(double), &p)); c->d_scale = static_cast<double *>(p);
     TRY(dalloc(c, c->m.size() * kRecCap * kRecLen * sizeof(double), &p));
     c->d_records = static_cast<double *>(p);
     TRY(build_plans(c));
@@ -903,20 +901,13 @@ tdse_status tdse_set_wavepacket(tdse_ctx *c, int member, const double r0[3], con
     TRY(ensure_device(c));
     Member &mb = c->m[member];
     if (!mb.have_potential) TRY(potential_to_d(c, mb, nullptr));   // V = 0
-    const size_t cells = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz;
-    void *R = nullptr, *I = nullptr;
-    TRY(dalloc(c, cells * sizeof(double), &R));
-    TRY(dalloc(c, cells * sizeof(double), &I));
-    CUDA_TRY(c, launch_packet(mb.dev, r0, sigma, k0, static_cast<double *>(R),
-                              static_cast<double *>(I), c->d_partials, kObsParts, c->d_scale,
-                              c->stream));
-    CUDA_TRY(c, launch_scale_half(mb.dev, mb.V64, static_cast<double *>(R),
-                                  static_cast<double *>(I), c->d_scale, c->precision, c->cur,
-                                  c->stream));
+    void *scratch = nullptr;
+    TRY(dalloc(c, packet_scratch_bytes(mb.dev), &scratch));
+    CUDA_TRY(c, launch_packet_start(mb.dev, mb.V64, r0, sigma, k0, scratch, c->precision, c->cur,
+                                    c->stream));
     TRY(fill_all_ghosts(c, mb, c->cur));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    dfree(c, R);
-    dfree(c, I);
+    dfree(c, scratch);
     mb.from_packet = true;
     return reset_run(c, member);
 }

@@ -93,12 +93,12 @@ size_t atom_cell_bytes(int n);
 cudaError_t launch_build_d(const MemberDev &m, int elem, const double *V, double *V64,
                            cudaStream_t s);
 // psi0 of Eq. 3 into R64/I64 (unpadded FP64) and the normalisation factor into *scale
-cudaError_t launch_packet(const MemberDev &m, const double *r0, const double *sigma,
-                          const double *k0, double *R64, double *I64, double *partials,
-                          int nparts, double *scale, cudaStream_t s);
-cudaError_t launch_scale_half(const MemberDev &m, const double *V64, const double *R64,
-                              const double *I64, const double *scale, int precision, int buf,
-                              cudaStream_t s);
+// Eq. 3 packet and the half-step start I^{-1/2} = Im psi0 - A[Re psi0]/2 written straight
+// into the state (scratch: packet_scratch_bytes, device memory).
+size_t packet_scratch_bytes(const MemberDev &m);
+cudaError_t launch_packet_start(const MemberDev &m, const double *V64, const double *r0,
+                                const double *sigma, const double *k0, void *scratch,
+                                int precision, int buf, cudaStream_t s);
 cudaError_t launch_set_state(const MemberDev &m, const double *R64, const double *I64,
                              int precision, int buf, cudaStream_t s);
 // Trilinear interpolation of a periodic cell potential onto the grid (FP64, unpadded).
