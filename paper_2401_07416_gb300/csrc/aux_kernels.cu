@@ -30,6 +30,19 @@ __device__ __forceinline__ double value(const MemberDev &m, const Real *f, const
     return v;
 }
 
+// Visit every node: blocks take (y, z) rows through a 2-D grid, threads take x, so no
+// index is split with a 64-bit division (a long software routine on the GPU).  f gets
+// (x, y, z) and the unpadded linear index.
+template <typename F>
+__device__ __forceinline__ void for_each_node(int nx, int ny, int nz, F &&f)
+{
+    for (int z = blockIdx.y; z < nz; z += gridDim.y)
+        for (int y = blockIdx.x; y < ny; y += gridDim.x) {
+            const long long base = (static_cast<long long>(z) * ny + y) * nx;
+            for (int x = threadIdx.x; x < nx; x += blockDim.x) f(x, y, z, base + x);
+        }
+}
+
 // Field value at unpadded (x, y, z) with |x - x0|, |y - y0| <= 1 of an interior
 // node: x/y come from the ghost zones, z wraps (periodic) or reads zero (wall).
 template <typename Real>
@@ -45,27 +58,35 @@ __device__ __forceinline__ double nbr(const MemberDev &m, const Real *f, const R
 
 // ---------------------------------------------------------------- ghost zones
 
+// Ghost cells of each z plane (blocks take planes): the G rows below and above the
+// interior (full padded width) and the G columns left and right of each interior row.
+// A ghost takes the periodic image's interior value, or 0 beyond a wall.
 template <typename Real>
 __global__ void fill_ghosts_kernel(MemberDev m, Real *f)
 {
-    const int wx = m.nx + 2 * m.G, wy = m.ny + 2 * m.G;
-    const long long n = static_cast<long long>(wx) * wy * m.nz;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int px = static_cast<int>(t % wx);
-        const int py = static_cast<int>((t / wx) % wy);
-        const int z = static_cast<int>(t / (static_cast<long long>(wx) * wy));
-        int x = px - m.G, y = py - m.G;
-        const bool gx = x < 0 || x >= m.nx, gy = y < 0 || y >= m.ny;
-        if (!gx && !gy) continue;
-        Real v = Real(0);
-        if ((!gx || m.per_x) && (!gy || m.per_y)) {
-            x = (x % m.nx + m.nx) % m.nx;
-            y = (y % m.ny + m.ny) % m.ny;
-            v = f[pidx(m, x, y, z)];
+    const int G = m.G, wx = m.nx + 2 * G;
+    const int band = 2 * G * wx;                 // ghost rows of one plane
+    const int ng = band + 2 * G * m.ny;          // + ghost columns
+    for (int z = blockIdx.x; z < m.nz; z += gridDim.x)
+        for (int e = threadIdx.x; e < ng; e += blockDim.x) {
+            int x, y;
+            if (e < band) {
+                const int row = e / wx;          // 0 .. 2G-1
+                x = e - row * wx - G;
+                y = row < G ? row - G : m.ny + row - G;
+            } else {
+                const int c = e - band, row = c / (2 * G), k = c - row * 2 * G;
+                y = row;
+                x = k < G ? k - G : m.nx + k - G;
+            }
+            const bool gx = x < 0 || x >= m.nx, gy = y < 0 || y >= m.ny;
+            Real v = Real(0);
+            if ((!gx || m.per_x) && (!gy || m.per_y)) {
+                const int sx = (x % m.nx + m.nx) % m.nx, sy = (y % m.ny + m.ny) % m.ny;
+                v = f[pidx(m, sx, sy, z)];
+            }
+            f[pidx(m, x, y, z)] = v;
         }
-        f[pidx(m, px - m.G, py - m.G, z)] = v;
-    }
 }
 
 // ---------------------------------------------------------------- potential
@@ -199,22 +220,17 @@ __global__ void potential_kernel(MemberDev m, const AtomCell *__restrict__ atoms
     if (t < cells) V[t] = static_cast<double>(acc) - static_cast<double>(comp);
 }
 
-// d = -2 (cx + cy + cz) - cv V into the padded Real array; V kept in FP64.
+// d = -2 (cx + cy + cz) - cv V into the padded Real array; V kept in FP64 (V may be
+// V64 itself: the potential was written there directly).
 template <typename Real>
-__global__ void build_d_kernel(MemberDev m, const double *__restrict__ V, Real *d,
-                               double *__restrict__ V64)
+__global__ void build_d_kernel(MemberDev m, const double *V, Real *d, double *V64)
 {
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
     const double c0 = -2.0 * (m.cx + m.cy + m.cz);
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(t % m.nx);
-        const int y = static_cast<int>((t / m.nx) % m.ny);
-        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+    for_each_node(m.nx, m.ny, m.nz, [&](int x, int y, int z, long long t) {
         const double v = V ? V[t] : 0.0;
-        V64[t] = v;
+        if (V != V64) V64[t] = v;
         d[pidx(m, x, y, z)] = static_cast<Real>(c0 - m.cv * v);
-    }
+    });
 }
 
 // ---------------------------------------------------------------- wave packet
@@ -238,16 +254,23 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 
 // Eq. 3 factorises over the axes: psi0(r) = prod_a g_a(r_a) exp(i k_a (r_a - r0_a)) with
 // g_a = exp(-(r_a - r0_a)^2 / (2 sigma_a^2)) (1 on a plane-wave axis, sigma_a <= 0).
-// One block per axis writes that axis' complex factors and the sum of their squared
-// moduli; the product of the three sums times h^3 is the discrete norm of psi0.
+// So does the kinetic part of A psi0 (Eq. 7): the second difference along axis a acts
+// on that axis' factor alone, c_a (f_a(i+1) + f_a(i-1)) times the other two factors,
+// with the neighbour wrapped on a periodic axis and zero beyond a wall.
+// One block per axis writes the axis' complex factors f_a, its neighbour sums
+// c_a (f_a(i+1) + f_a(i-1)) and the sum of |f_a|^2; the product of the three sums
+// times h^3 is the discrete norm of psi0.
 __global__ void packet_axes_kernel(MemberDev m, PacketArgs P, double2 *__restrict__ fac,
-                                   double *__restrict__ sums)
+                                   double2 *__restrict__ nsum, double *__restrict__ sums)
 {
     __shared__ double sh[32];
     const int a = blockIdx.x;
     const int n = a == 0 ? m.nx : a == 1 ? m.ny : m.nz;
     const double h = a == 0 ? m.hx : a == 1 ? m.hy : m.hz;
-    double2 *f = fac + (a == 0 ? 0 : a == 1 ? m.nx : m.nx + m.ny);
+    const double c = a == 0 ? m.cx : a == 1 ? m.cy : m.cz;
+    const bool per = a == 0 ? m.per_x : a == 1 ? m.per_y : m.per_z;
+    const int off = a == 0 ? 0 : a == 1 ? m.nx : m.nx + m.ny;
+    double2 *f = fac + off;
     double acc = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double d = i * h - P.r0[a];
@@ -257,68 +280,73 @@ __global__ void packet_axes_kernel(MemberDev m, PacketArgs P, double2 *__restric
         f[i] = make_double2(amp * cs, amp * sn);
         acc += amp * amp;
     }
-    const double s = block_sum(acc, sh);
+    const double s = block_sum(acc, sh);   // its barriers order the f[] writes before the reads below
     if (threadIdx.x == 0) sums[a] = s;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double2 lo = make_double2(0.0, 0.0), hi = make_double2(0.0, 0.0);
+        if (i > 0) lo = f[i - 1];
+        else if (per) lo = f[n - 1];
+        if (i + 1 < n) hi = f[i + 1];
+        else if (per) hi = f[0];
+        nsum[off + i] = make_double2(c * (lo.x + hi.x), c * (lo.y + hi.y));
+    }
 }
 
-// R^0 = s Re psi0 and I^{-1/2} = s (Im psi0 - A[Re psi0] / 2), stored as Real (+ the
-// compensation terms), with psi0 at a node and its neighbours formed from the axis
-// factors (x factor times y factor, times z factor) and s = 1 / sqrt(h^3 Sx Sy Sz).
-// Blocks take z planes, threads the cells of a plane.
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Row factors of the packet: for every (y, z) row, gh = f_y f_z and
+// u = n_y f_z + f_y n_z (n: the neighbour sums above), so that at (x, y, z)
+//   psi0 = f_x gh   and   kinetic part of A psi0 = n_x gh + f_x u.
+__global__ void packet_rows_kernel(MemberDev m, const double2 *__restrict__ fac,
+                                   const double2 *__restrict__ nsum, double2 *__restrict__ rows)
+{
+    for (int z = blockIdx.x; z < m.nz; z += gridDim.x)
+        for (int y = threadIdx.x; y < m.ny; y += blockDim.x) {
+        const long long r = static_cast<long long>(z) * m.ny + y;
+        const double2 fy = fac[m.nx + y], fz = fac[m.nx + m.ny + z];
+        const double2 ny = nsum[m.nx + y], nz = nsum[m.nx + m.ny + z];
+        const double2 a = cmul(ny, fz), b = cmul(fy, nz);
+        rows[2 * r] = cmul(fy, fz);
+        rows[2 * r + 1] = make_double2(a.x + b.x, a.y + b.y);
+    }
+}
+
+// R^0 = s Re psi0 and I^{-1/2} = s (Im psi0 - A[Re psi0] / 2) (Sec. 2.1), stored as
+// Real (+ the compensation terms), s = 1 / sqrt(h^3 Sx Sy Sz).  A is real, so
+// A[Re psi0] = Re(kinetic part of A psi0) + (d - cv V) Re psi0 with d = -2 (cx+cy+cz).
 template <typename Real>
 __global__ void packet_start_kernel(MemberDev m, const double *__restrict__ V64,
-                                    const double2 *__restrict__ fac, const double *__restrict__ sums,
+                                    const double2 *__restrict__ fac, const double2 *__restrict__ nsum,
+                                    const double2 *__restrict__ rows, const double *__restrict__ sums,
                                     int kahan, int buf)
 {
     const double s = 1.0 / sqrt(m.hx * m.hy * m.hz * sums[0] * sums[1] * sums[2]);
-    const double2 *fx = fac, *fy = fac + m.nx, *fz = fac + m.nx + m.ny;
-    auto psi = [&](int x, int y, int z) {
-        const double2 a = fx[x], b = fy[y], c = fz[z];
-        const double re = a.x * b.x - a.y * b.y, im = a.x * b.y + a.y * b.x;
-        return make_double2(re * c.x - im * c.y, re * c.y + im * c.x);
-    };
-    // Re psi0 one node away: wrap on a periodic axis, zero beyond a wall
-    auto re_nb = [&](int x, int y, int z) -> double {
-        if (x < 0 || x >= m.nx) {
-            if (!m.per_x) return 0.0;
-            x = x < 0 ? x + m.nx : x - m.nx;
-        }
-        if (y < 0 || y >= m.ny) {
-            if (!m.per_y) return 0.0;
-            y = y < 0 ? y + m.ny : y - m.ny;
-        }
-        if (z < 0 || z >= m.nz) {
-            if (!m.per_z) return 0.0;
-            z = z < 0 ? z + m.nz : z - m.nz;
-        }
-        return psi(x, y, z).x;
-    };
     Real *oR = reinterpret_cast<Real *>(m.R[buf]);
     Real *oI = reinterpret_cast<Real *>(m.I[buf]);
     Real *oCR = reinterpret_cast<Real *>(m.cR[buf]);
     Real *oCI = reinterpret_cast<Real *>(m.cI[buf]);
-    const int plane = m.nx * m.ny;
     const double c0 = -2.0 * (m.cx + m.cy + m.cz);
-    for (int z = blockIdx.x; z < m.nz; z += gridDim.x)
-        for (int xy = threadIdx.x; xy < plane; xy += blockDim.x) {
-            const int x = xy % m.nx, y = xy / m.nx;
-            const double2 p0 = psi(x, y, z);
-            const double r0 = p0.x;
-            const double ar = m.cx * (re_nb(x + 1, y, z) + re_nb(x - 1, y, z)) +
-                              m.cy * (re_nb(x, y + 1, z) + re_nb(x, y - 1, z)) +
-                              m.cz * (re_nb(x, y, z + 1) + re_nb(x, y, z - 1)) +
-                              (c0 - m.cv * V64[static_cast<long long>(z) * plane + xy]) * r0;
-            const double rv = s * r0;
-            const double iv = s * (p0.y - 0.5 * ar);
-            const long long o = pidx(m, x, y, z);
-            const Real rs = static_cast<Real>(rv), is = static_cast<Real>(iv);
-            oR[o] = rs;
-            oI[o] = is;
-            if (kahan) {
-                oCR[o] = static_cast<Real>(static_cast<double>(rs) - rv);
-                oCI[o] = static_cast<Real>(static_cast<double>(is) - iv);
-            }
+    for_each_node(m.nx, m.ny, m.nz, [&](int x, int y, int z, long long t) {
+        const long long r = static_cast<long long>(z) * m.ny + y;
+        const double2 f = fac[x], n = nsum[x], gh = rows[2 * r], u = rows[2 * r + 1];
+        const double re = f.x * gh.x - f.y * gh.y;
+        const double im = f.x * gh.y + f.y * gh.x;
+        const double kin = (n.x * gh.x - n.y * gh.y) + (f.x * u.x - f.y * u.y);
+        const double ar = kin + (c0 - m.cv * V64[t]) * re;
+        const double rv = s * re;
+        const double iv = s * (im - 0.5 * ar);
+        const long long o = pidx(m, x, y, z);
+        const Real rs = static_cast<Real>(rv), is = static_cast<Real>(iv);
+        oR[o] = rs;
+        oI[o] = is;
+        if (kahan) {
+            oCR[o] = static_cast<Real>(static_cast<double>(rs) - rv);
+            oCI[o] = static_cast<Real>(static_cast<double>(is) - iv);
         }
+    });
 }
 
 // ---------------------------------------------------------------- state copies
@@ -327,16 +355,11 @@ template <typename Real>
 __global__ void set_state_kernel(MemberDev m, const double *__restrict__ R,
                                  const double *__restrict__ I, int kahan, int buf)
 {
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
     Real *oR = reinterpret_cast<Real *>(m.R[buf]);
     Real *oI = reinterpret_cast<Real *>(m.I[buf]);
     Real *oCR = reinterpret_cast<Real *>(m.cR[buf]);
     Real *oCI = reinterpret_cast<Real *>(m.cI[buf]);
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(t % m.nx);
-        const int y = static_cast<int>((t / m.nx) % m.ny);
-        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+    for_each_node(m.nx, m.ny, m.nz, [&](int x, int y, int z, long long t) {
         const long long o = pidx(m, x, y, z);
         const Real rs = static_cast<Real>(R[t]), is = static_cast<Real>(I[t]);
         oR[o] = rs;
@@ -345,27 +368,22 @@ __global__ void set_state_kernel(MemberDev m, const double *__restrict__ R,
             oCR[o] = static_cast<Real>(static_cast<double>(rs) - R[t]);
             oCI[o] = static_cast<Real>(static_cast<double>(is) - I[t]);
         }
-    }
+    });
 }
 
 template <typename Real>
 __global__ void get_state_kernel(MemberDev m, double *__restrict__ R, double *__restrict__ I,
                                  int kahan, int buf)
 {
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
     const Real *iR = reinterpret_cast<const Real *>(m.R[buf]);
     const Real *iI = reinterpret_cast<const Real *>(m.I[buf]);
     const Real *iCR = kahan ? reinterpret_cast<const Real *>(m.cR[buf]) : nullptr;
     const Real *iCI = kahan ? reinterpret_cast<const Real *>(m.cI[buf]) : nullptr;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(t % m.nx);
-        const int y = static_cast<int>((t / m.nx) % m.ny);
-        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+    for_each_node(m.nx, m.ny, m.nz, [&](int x, int y, int z, long long t) {
         const long long o = pidx(m, x, y, z);
         if (R) R[t] = value<Real>(m, iR, iCR, o);
         if (I) I[t] = value<Real>(m, iI, iCI, o);
-    }
+    });
 }
 
 // Interior of a padded Real field <-> unpadded FP64 array (exact in both directions
@@ -373,18 +391,13 @@ __global__ void get_state_kernel(MemberDev m, double *__restrict__ R, double *__
 template <typename Real>
 __global__ void field_io_kernel(MemberDev m, Real *field, double *host_side, int to_field)
 {
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(t % m.nx);
-        const int y = static_cast<int>((t / m.nx) % m.ny);
-        const int z = static_cast<int>(t / (static_cast<long long>(m.nx) * m.ny));
+    for_each_node(m.nx, m.ny, m.nz, [&](int x, int y, int z, long long t) {
         const long long o = pidx(m, x, y, z);
         if (to_field)
             field[o] = static_cast<Real>(host_side[t]);
         else
             host_side[t] = static_cast<double>(field[o]);
-    }
+    });
 }
 
 // ---------------------------------------------------------------- observables
@@ -596,15 +609,33 @@ int grid_for(long long n)
     return static_cast<int>(g);
 }
 
+// Launch shape of a for_each_node kernel: a warp multiple of threads up to kThreads
+// along x, and about two waves of blocks over the (y, z) rows.
+struct NodeLaunch {
+    dim3 grid;
+    int threads;
+};
+
+NodeLaunch node_launch(int nx, int ny, int nz)
+{
+    const int threads = nx >= kThreads ? kThreads : std::max(32, (nx + 31) / 32 * 32);
+    const int target = 2 * 152 * (2048 / threads);
+    const int gx = std::min(ny, 64);
+    const int gy = std::max(1, std::min({nz, 65535, std::max(1, target / gx)}));
+    return {dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy)), threads};
+}
+
+NodeLaunch node_launch(const MemberDev &m) { return node_launch(m.nx, m.ny, m.nz); }
+
 }  // namespace
 
 cudaError_t launch_fill_ghosts(const MemberDev &m, void *field, int elem, cudaStream_t s)
 {
-    const long long n = static_cast<long long>(m.nx + 2 * m.G) * (m.ny + 2 * m.G) * m.nz;
+    const int planes = std::min(m.nz, 152 * 16);
     if (elem == 8)
-        fill_ghosts_kernel<double><<<grid_for(n), kThreads, 0, s>>>(m, static_cast<double *>(field));
+        fill_ghosts_kernel<double><<<planes, kThreads, 0, s>>>(m, static_cast<double *>(field));
     else
-        fill_ghosts_kernel<float><<<grid_for(n), kThreads, 0, s>>>(m, static_cast<float *>(field));
+        fill_ghosts_kernel<float><<<planes, kThreads, 0, s>>>(m, static_cast<float *>(field));
     return cudaGetLastError();
 }
 
@@ -628,17 +659,19 @@ size_t atom_cell_bytes(int n) { return static_cast<size_t>(n > 0 ? n : 1) * size
 cudaError_t launch_build_d(const MemberDev &m, int elem, const double *V, double *V64,
                            cudaStream_t s)
 {
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const NodeLaunch L = node_launch(m);
     if (elem == 8)
-        build_d_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, V, static_cast<double *>(m.d), V64);
+        build_d_kernel<double><<<L.grid, L.threads, 0, s>>>(m, V, static_cast<double *>(m.d), V64);
     else
-        build_d_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, V, static_cast<float *>(m.d), V64);
+        build_d_kernel<float><<<L.grid, L.threads, 0, s>>>(m, V, static_cast<float *>(m.d), V64);
     return cudaGetLastError();
 }
 
 size_t packet_scratch_bytes(const MemberDev &m)
 {
-    return (static_cast<size_t>(m.nx) + m.ny + m.nz) * sizeof(double2) + 4 * sizeof(double);
+    const size_t axes = static_cast<size_t>(m.nx) + m.ny + m.nz;
+    const size_t rows = static_cast<size_t>(m.ny) * m.nz;
+    return (2 * axes + 2 * rows) * sizeof(double2) + 4 * sizeof(double);
 }
 
 cudaError_t launch_packet_start(const MemberDev &m, const double *V64, const double *r0,
@@ -651,97 +684,132 @@ cudaError_t launch_packet_start(const MemberDev &m, const double *V64, const dou
         P.sigma[a] = sigma[a];
         P.k0[a] = k0[a];
     }
+    const size_t axes = static_cast<size_t>(m.nx) + m.ny + m.nz;
+    const long long nrows = static_cast<long long>(m.ny) * m.nz;
+    const NodeLaunch L = node_launch(m);
     double2 *fac = static_cast<double2 *>(scratch);
-    double *sums = reinterpret_cast<double *>(fac + m.nx + m.ny + m.nz);
-    packet_axes_kernel<<<3, kThreads, 0, s>>>(m, P, fac, sums);
-    const int blocks = std::min(m.nz, 8192);
+    double2 *nsum = fac + axes;
+    double2 *rows = nsum + axes;
+    double *sums = reinterpret_cast<double *>(rows + 2 * nrows);
+    packet_axes_kernel<<<3, kThreads, 0, s>>>(m, P, fac, nsum, sums);
+    packet_rows_kernel<<<std::min(m.nz, 152 * 16), kThreads, 0, s>>>(m, fac, nsum, rows);
     if (precision == 0)
-        packet_start_kernel<double><<<blocks, kThreads, 0, s>>>(m, V64, fac, sums, 0, buf);
+        packet_start_kernel<double><<<L.grid, L.threads, 0, s>>>(m, V64, fac, nsum, rows, sums, 0, buf);
     else
-        packet_start_kernel<float><<<blocks, kThreads, 0, s>>>(m, V64, fac, sums, precision == 2, buf);
+        packet_start_kernel<float><<<L.grid, L.threads, 0, s>>>(m, V64, fac, nsum, rows, sums,
+                                                                precision == 2, buf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_state(const MemberDev &m, const double *R64, const double *I64,
                              int precision, int buf, cudaStream_t s)
 {
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const NodeLaunch L = node_launch(m);
     if (precision == 0)
-        set_state_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, R64, I64, 0, buf);
+        set_state_kernel<double><<<L.grid, L.threads, 0, s>>>(m, R64, I64, 0, buf);
     else
-        set_state_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, R64, I64, precision == 2, buf);
+        set_state_kernel<float><<<L.grid, L.threads, 0, s>>>(m, R64, I64, precision == 2, buf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_get_state(const MemberDev &m, double *R64, double *I64, int precision,
                              int buf, cudaStream_t s)
 {
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const NodeLaunch L = node_launch(m);
     if (precision == 0)
-        get_state_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, R64, I64, 0, buf);
+        get_state_kernel<double><<<L.grid, L.threads, 0, s>>>(m, R64, I64, 0, buf);
     else
-        get_state_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, R64, I64, precision == 2, buf);
+        get_state_kernel<float><<<L.grid, L.threads, 0, s>>>(m, R64, I64, precision == 2, buf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_field_io(const MemberDev &m, void *field, int elem, double *array, int to_field,
                             cudaStream_t s)
 {
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
+    const NodeLaunch L = node_launch(m);
     if (elem == 8)
-        field_io_kernel<double><<<grid_for(cells), kThreads, 0, s>>>(m, static_cast<double *>(field), array, to_field);
+        field_io_kernel<double><<<L.grid, L.threads, 0, s>>>(m, static_cast<double *>(field), array, to_field);
     else
-        field_io_kernel<float><<<grid_for(cells), kThreads, 0, s>>>(m, static_cast<float *>(field), array, to_field);
+        field_io_kernel<float><<<L.grid, L.threads, 0, s>>>(m, static_cast<float *>(field), array, to_field);
     return cudaGetLastError();
 }
 
 // Trilinear interpolation of a periodic cell lattice Vc[cnz][cny][cnx] (cell lengths L,
 // lattice origin o) at every grid node (i hx, j hy, k hz) into V[nz][ny][nx] (FP64).
-__global__ void interp_kernel(int nx, int ny, int nz, double hx, double hy, double hz,
-                              const double *__restrict__ Vc, int cnx, int cny, int cnz, double Lx,
-                              double Ly, double Lz, double ox, double oy, double oz,
-                              double *__restrict__ V)
+// The lattice position of a node separates over the axes: interp_axes_kernel
+// tabulates, per axis, the two bracketing lattice indices (wrapped) and the fraction.
+struct AxisPos {
+    int i0, i1;
+    double f;
+};
+
+struct InterpArgs {
+    double h[3], L[3], o[3];
+    int n[3], c[3];
+};
+
+__global__ void interp_axes_kernel(InterpArgs A, AxisPos *__restrict__ tab)
 {
-    const long long cells = static_cast<long long>(nx) * ny * nz;
-    auto locate = [](double pos, double o, double L, int n, int &i0, int &i1, double &f) {
-        const double u = (pos - o) / L * n;
+    const int total = A.n[0] + A.n[1] + A.n[2];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int a = t < A.n[0] ? 0 : t < A.n[0] + A.n[1] ? 1 : 2;
+        const int i = t - (a == 0 ? 0 : a == 1 ? A.n[0] : A.n[0] + A.n[1]);
+        const int n = A.c[a];
+        const double u = (i * A.h[a] - A.o[a]) / A.L[a] * n;
         const double fl = floor(u);
-        f = u - fl;
         long long k = static_cast<long long>(fl) % n;
         if (k < 0) k += n;
-        i0 = static_cast<int>(k);
-        i1 = i0 + 1 == n ? 0 : i0 + 1;
-    };
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < cells;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(t % nx);
-        const int y = static_cast<int>((t / nx) % ny);
-        const int z = static_cast<int>(t / (static_cast<long long>(nx) * ny));
-        int x0, x1, y0, y1, z0, z1;
-        double fx, fy, fz;
-        locate(x * hx, ox, Lx, cnx, x0, x1, fx);
-        locate(y * hy, oy, Ly, cny, y0, y1, fy);
-        locate(z * hz, oz, Lz, cnz, z0, z1, fz);
-        auto at = [&](int k, int j, int i) {
-            return Vc[(static_cast<long long>(k) * cny + j) * cnx + i];
-        };
-        const double c00 = at(z0, y0, x0) * (1 - fx) + at(z0, y0, x1) * fx;
-        const double c01 = at(z0, y1, x0) * (1 - fx) + at(z0, y1, x1) * fx;
-        const double c10 = at(z1, y0, x0) * (1 - fx) + at(z1, y0, x1) * fx;
-        const double c11 = at(z1, y1, x0) * (1 - fx) + at(z1, y1, x1) * fx;
-        const double c0 = c00 * (1 - fy) + c01 * fy;
-        const double c1 = c10 * (1 - fy) + c11 * fy;
-        V[t] = c0 * (1 - fz) + c1 * fz;
+        AxisPos p;
+        p.f = u - fl;
+        p.i0 = static_cast<int>(k);
+        p.i1 = p.i0 + 1 == n ? 0 : p.i0 + 1;
+        tab[t] = p;
     }
 }
 
-cudaError_t launch_interp(const MemberDev &m, double hx, double hy, double hz, const double *Vc,
-                          int cnx, int cny, int cnz, const double L[3], const double o[3], double *V,
-                          cudaStream_t s)
+__global__ void interp_kernel(int nx, int ny, int nz, const double *__restrict__ Vc, int cnx,
+                              int cny, const AxisPos *__restrict__ tab, double *__restrict__ V)
 {
-    const long long cells = static_cast<long long>(m.nx) * m.ny * m.nz;
-    interp_kernel<<<grid_for(cells), kThreads, 0, s>>>(m.nx, m.ny, m.nz, hx, hy, hz, Vc, cnx, cny,
-                                                       cnz, L[0], L[1], L[2], o[0], o[1], o[2], V);
+    for_each_node(nx, ny, nz, [&](int x, int y, int z, long long t) {
+        const AxisPos px = tab[x], py = tab[nx + y], pz = tab[nx + ny + z];
+        auto at = [&](int k, int j, int i) {
+            return Vc[(static_cast<long long>(k) * cny + j) * cnx + i];
+        };
+        const double fx = px.f, fy = py.f, fz = pz.f;
+        const double c00 = at(pz.i0, py.i0, px.i0) * (1 - fx) + at(pz.i0, py.i0, px.i1) * fx;
+        const double c01 = at(pz.i0, py.i1, px.i0) * (1 - fx) + at(pz.i0, py.i1, px.i1) * fx;
+        const double c10 = at(pz.i1, py.i0, px.i0) * (1 - fx) + at(pz.i1, py.i0, px.i1) * fx;
+        const double c11 = at(pz.i1, py.i1, px.i0) * (1 - fx) + at(pz.i1, py.i1, px.i1) * fx;
+        const double c0 = c00 * (1 - fy) + c01 * fy;
+        const double c1 = c10 * (1 - fy) + c11 * fy;
+        V[t] = c0 * (1 - fz) + c1 * fz;
+    });
+}
+
+size_t interp_scratch_bytes(const MemberDev &m)
+{
+    return (static_cast<size_t>(m.nx) + m.ny + m.nz) * sizeof(AxisPos);
+}
+
+cudaError_t launch_interp(const MemberDev &m, double hx, double hy, double hz, const double *Vc,
+                          int cnx, int cny, int cnz, const double L[3], const double o[3],
+                          void *scratch, double *V, cudaStream_t s)
+{
+    InterpArgs A;
+    const double h[3] = {hx, hy, hz};
+    const int n[3] = {m.nx, m.ny, m.nz}, c[3] = {cnx, cny, cnz};
+    for (int a = 0; a < 3; ++a) {
+        A.h[a] = h[a];
+        A.L[a] = L[a];
+        A.o[a] = o[a];
+        A.n[a] = n[a];
+        A.c[a] = c[a];
+    }
+    AxisPos *tab = static_cast<AxisPos *>(scratch);
+    const int total = m.nx + m.ny + m.nz;
+    interp_axes_kernel<<<(total + kThreads - 1) / kThreads, kThreads, 0, s>>>(A, tab);
+    const NodeLaunch Ln = node_launch(m);
+    interp_kernel<<<Ln.grid, Ln.threads, 0, s>>>(m.nx, m.ny, m.nz, Vc, cnx, cny, tab, V);
     return cudaGetLastError();
 }
 

@@ -791,17 +791,12 @@ tdse_status tdse_set_potential(tdse_ctx *c, int member, const double *V, int on_
     Member &mb = c->m[member];
     const size_t bytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz * sizeof(double);
     const double *Vd = V;
-    void *tmp = nullptr;
-    if (!on_device) {
-        TRY(dalloc(c, bytes, &tmp));
-        CUDA_TRY(c, cudaMemcpyAsync(tmp, V, bytes, cudaMemcpyHostToDevice, c->stream));
-        Vd = static_cast<const double *>(tmp);
+    if (!on_device) {   // host V lands in the resident FP64 copy; d is built from it in place
+        CUDA_TRY(c, cudaMemcpyAsync(mb.V64, V, bytes, cudaMemcpyHostToDevice, c->stream));
+        Vd = mb.V64;
     }
     tdse_status st = potential_to_d(c, mb, Vd);
-    if (tmp) {
-        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-        dfree(c, tmp);
-    }
+    if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // the host buffer is free again
     mb.atoms.clear();
     return st;
 }
@@ -819,12 +814,11 @@ tdse_status tdse_set_potential_grid(tdse_ctx *c, int member, const double *Vc, i
     TRY(ensure_device(c));
     Member &mb = c->m[member];
     const size_t cbytes = static_cast<size_t>(cnx) * cny * cnz * sizeof(double);
-    const size_t bytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz * sizeof(double);
-    void *tmpc = nullptr, *tmpv = nullptr;
+    void *tmpc = nullptr, *tab = nullptr;
     auto release = [&]() {
         cudaStreamSynchronize(c->stream);
         dfree(c, tmpc);
-        dfree(c, tmpv);
+        dfree(c, tab);
     };
     const double *Vcd = Vc;
     tdse_status st = TDSE_OK;
@@ -836,16 +830,17 @@ tdse_status tdse_set_potential_grid(tdse_ctx *c, int member, const double *Vc, i
         }
         Vcd = static_cast<const double *>(tmpc);
     }
-    if ((st = dalloc(c, bytes, &tmpv)) != TDSE_OK) {
+    if ((st = dalloc(c, interp_scratch_bytes(mb.dev), &tab)) != TDSE_OK) {
         release();
         return st;
     }
-    if (launch_interp(mb.dev, mb.p.hx, mb.p.hy, mb.p.hz, Vcd, cnx, cny, cnz, cell, origin,
-                      static_cast<double *>(tmpv), c->stream) != cudaSuccess) {
+    // the interpolated V is written straight into the resident FP64 copy
+    if (launch_interp(mb.dev, mb.p.hx, mb.p.hy, mb.p.hz, Vcd, cnx, cny, cnz, cell, origin, tab,
+                      mb.V64, c->stream) != cudaSuccess) {
         release();
         return fail(c, TDSE_ECUDA, "interpolation kernel failed");
     }
-    st = potential_to_d(c, mb, static_cast<const double *>(tmpv));
+    st = potential_to_d(c, mb, mb.V64);
     release();
     mb.atoms.clear();
     return st;
@@ -872,18 +867,16 @@ tdse_status tdse_set_atoms(tdse_ctx *c, int member, int n, const double *xyzZ, d
             }
         r_cut = rc;
     }
-    const size_t cells = static_cast<size_t>(d.nx) * d.ny * d.nz;
-    void *V = nullptr, *A = nullptr, *AC = nullptr;
-    TRY(dalloc(c, cells * sizeof(double), &V));
+    void *A = nullptr, *AC = nullptr;
     TRY(dalloc(c, std::max<size_t>(1, 4 * static_cast<size_t>(n)) * sizeof(double), &A));
     TRY(dalloc(c, atom_cell_bytes(n), &AC));
     if (n > 0)
         CUDA_TRY(c, cudaMemcpyAsync(A, xyzZ, 4 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, launch_potential_atoms(d, static_cast<double *>(A), n, soft_a2, r_cut,
-                                       static_cast<double *>(V), AC, c->precision, c->stream));
-    tdse_status st = potential_to_d(c, mb, static_cast<double *>(V));
+    // every node's V is written straight into the resident FP64 copy
+    CUDA_TRY(c, launch_potential_atoms(d, static_cast<double *>(A), n, soft_a2, r_cut, mb.V64, AC,
+                                       c->precision, c->stream));
+    tdse_status st = potential_to_d(c, mb, mb.V64);
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    dfree(c, V);
     dfree(c, A);
     dfree(c, AC);
     TRY(st);

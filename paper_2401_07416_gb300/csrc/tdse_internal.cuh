@@ -92,7 +92,6 @@ size_t atom_cell_bytes(int n);
 // d (padded, Real) from V (unpadded FP64, NULL: V = 0); V copied into V64
 cudaError_t launch_build_d(const MemberDev &m, int elem, const double *V, double *V64,
                            cudaStream_t s);
-// psi0 of Eq. 3 into R64/I64 (unpadded FP64) and the normalisation factor into *scale
 // Eq. 3 packet and the half-step start I^{-1/2} = Im psi0 - A[Re psi0]/2 written straight
 // into the state (scratch: packet_scratch_bytes, device memory).
 size_t packet_scratch_bytes(const MemberDev &m);
@@ -101,10 +100,12 @@ cudaError_t launch_packet_start(const MemberDev &m, const double *V64, const dou
                                 int precision, int buf, cudaStream_t s);
 cudaError_t launch_set_state(const MemberDev &m, const double *R64, const double *I64,
                              int precision, int buf, cudaStream_t s);
-// Trilinear interpolation of a periodic cell potential onto the grid (FP64, unpadded).
+// Trilinear interpolation of a periodic cell potential onto the grid (FP64, unpadded;
+// scratch: interp_scratch_bytes, device memory).
+size_t interp_scratch_bytes(const MemberDev &m);
 cudaError_t launch_interp(const MemberDev &m, double hx, double hy, double hz, const double *Vc,
-                          int cnx, int cny, int cnz, const double L[3], const double o[3], double *V,
-                          cudaStream_t s);
+                          int cnx, int cny, int cnz, const double L[3], const double o[3],
+                          void *scratch, double *V, cudaStream_t s);
 // Eq. 15 density of plane det_k at the current time level into out[ny][nx] (FP64).
 cudaError_t launch_frame(const MemberDev &m, int precision, int buf, double *out, cudaStream_t s);
 cudaError_t launch_get_state(const MemberDev &m, double *R64, double *I64, int precision,
