@@ -199,23 +199,38 @@ def oracle_sample_state():
     return sub, V, R0, oracle.init_half(sub, V, R0, I0)
 
 
-def time_oracle(seconds: float):
-    """FP64 oracle steps on the bounded sample until `seconds` of wall time."""
+def time_oracle(seconds: float, serial_seconds: float = 4.0):
+    """FP64 oracle steps on the bounded sample until `seconds` of wall time on all
+    host cores, then `serial_seconds` on one thread (the paper's serial comparison)."""
     import oracle
-    sub, V, R, I = oracle_sample_state()
-    steps = 0
-    t0 = time.perf_counter()
-    while True:
-        R, I, _, _ = oracle.run(sub, V, R, I, 2, use_mask=False, flux=False)
-        steps += 2
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
+    sub, V, R0, I0 = oracle_sample_state()
+
+    def timed(limit):
+        R, I = R0, I0
+        steps = 0
+        t0 = time.perf_counter()
+        while True:
+            R, I, _, _ = oracle.run(sub, V, R, I, 2, use_mask=False, flux=False)
+            steps += 2
+            el = time.perf_counter() - t0
+            if el >= limit:
+                return steps, el
+
     cores = oracle_cores()
-    return {"value": sub.cells * steps / el, "unit": "cell-updates/s", "cores": cores,
-            "kind": "oracle",
+    oracle.set_threads(cores)
+    steps, el = timed(seconds)
+    value = sub.cells * steps / el
+    oracle.set_threads(1)
+    s1, e1 = timed(serial_seconds)
+    oracle.set_threads(cores)
+    v1 = sub.cells * s1 / e1
+    return {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+            "ns_per_cell_update": 1e9 / value,
             "sample": f"{steps} FP64 oracle steps on a 512x512x16 z-slab of the 512x512x1024 "
-                      f"workload ({sub.cells} nodes), {el:.1f} s wall, OpenMP {cores} threads"}
+                      f"workload ({sub.cells} nodes), {el:.1f} s wall, OpenMP {cores} threads",
+            "serial": {"value": v1, "unit": "cell-updates/s", "cores": 1,
+                       "ns_per_cell_update": 1e9 / v1,
+                       "sample": f"{s1} steps of the same sample on one thread, {e1:.1f} s wall"}}
 
 
 def reference_arm(args):

@@ -72,12 +72,23 @@ def lib():
             "orc_run": (None, [g, p, i, p, p, ctypes.c_long, p, p]),
             "orc_observables": (None, [g, p, p, p, p]),
             "orc_adjoint": (None, [g, p, i, p, p, ctypes.c_long, p, p]),
+            "orc_set_threads": (None, [i]),
+            "orc_max_threads": (i, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
             fn.restype = res
             fn.argtypes = args
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's loops (timing only)."""
+    lib().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
 
 
 def _grid(g) -> OrcGrid:

@@ -29,9 +29,16 @@
  *     image in periodic axes; r_c <= 0 means phi = 1/rho (no cut-off).
  */
 #include <math.h>
+#include <omp.h>
 #include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Thread count of the OpenMP loops below, for timing the oracle serially or on all
+ * cores.  The per-node loops give the same results at any count; only the summation
+ * order of the atom-gradient reduction depends on it. */
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int orc_max_threads(void) { return omp_get_max_threads(); }
 
 typedef struct {
     int nx, ny, nz;

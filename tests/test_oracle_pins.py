@@ -623,3 +623,23 @@ def test_interpolation_matches_scipy_on_a_padded_lattice():
                             ((i * h[0] - origin[0]) % cell[0])])
     ref = f(np.array(pts)).reshape(10, 7, 12)
     assert np.abs(V - ref).max() < 1e-12
+
+
+def test_oracle_steps_independent_of_thread_count():
+    """The step, packet and flux loops write per node: one thread and several give
+    bit-identical results (so the serial and all-core timings run the same program)."""
+    g = W.small_grid(12, 10, 16, h=(0.3, 0.35, 0.25), dt=0.01, bc=(0, 0, 1), mask=3, det_k=7)
+    V = W.random_potential(g, 11, 1.5)
+    p = W.Packet((1.8, 1.7, 2.0), (0.8, 0.9, 0.7), (0.4, -0.3, 1.1))
+    n = oracle.max_threads()
+    out = []
+    try:
+        for threads in (1, max(2, n)):
+            oracle.set_threads(threads)
+            R, I = oracle.initial_state(g, p, V)
+            out.append(oracle.run(g, V, R, I, 9, use_mask=True, flux=True))
+    finally:
+        oracle.set_threads(n)
+    for a, b in zip(out[0], out[1]):
+        if isinstance(a, np.ndarray):
+            assert np.array_equal(a, b)
