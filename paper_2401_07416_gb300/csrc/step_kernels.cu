@@ -37,6 +37,10 @@ TDSE_TMEM_DECL(tmem_f32_t2_r32x2_pf2)
 TDSE_TMEM_DECL(tmem_f32_t2_r32x1_pf3)
 TDSE_TMEM_DECL(tmem_f32_t2_r32x1_pf4)
 TDSE_TMEM_DECL(tmem_k32_t2_r28x1_pf3)
+TDSE_TMEM_DECL(tmem_k32_t2_w32_r28x1_pf2_b2)
+TDSE_TMEM_DECL(tmem_k32_t2_w32_r32x1_pf2_b2)
+TDSE_TMEM_DECL(tmem_f32_t2_w32_r32x1_pf4_b2)
+TDSE_TMEM_DECL(tmem_f32_t2_w32_r32x1_pf3_b2)
 #undef TDSE_TMEM_DECL
 
 namespace {
@@ -511,11 +515,15 @@ const Variant kVariants[] = {
     Variant{1, 2, "f32_t2_tmem_r32x1_pf3", &fill_tmem_f32_t2_r32x1_pf3, &launch_tmem_f32_t2_r32x1_pf3},
     Variant{1, 2, "f32_t2_tmem_r32x2_pf2", &fill_tmem_f32_t2_r32x2_pf2, &launch_tmem_f32_t2_r32x2_pf2},
     TDSE_VARIANT(1, 2, "f32_t2_w64_r32x2_pf2", float, 4, 16, 32, 2, false, 2),
+    Variant{1, 2, "f32_t2_tmem_w32_r32x1_pf4_b2", &fill_tmem_f32_t2_w32_r32x1_pf4_b2, &launch_tmem_f32_t2_w32_r32x1_pf4_b2},
+    Variant{1, 2, "f32_t2_tmem_w32_r32x1_pf3_b2", &fill_tmem_f32_t2_w32_r32x1_pf3_b2, &launch_tmem_f32_t2_w32_r32x1_pf3_b2},
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x2_pf2", float, 2, 16, 32, 2, true, 2),
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x1_pf2", float, 2, 16, 32, 1, true, 2),
+    Variant{2, 2, "k32_t2_tmem_w32_r32x1_pf2_b2", &fill_tmem_k32_t2_w32_r32x1_pf2_b2, &launch_tmem_k32_t2_w32_r32x1_pf2_b2},
     Variant{2, 2, "k32_t2_tmem_r28x1_pf2", &fill_tmem_k32_t2_r28x1_pf2, &launch_tmem_k32_t2_r28x1_pf2},
-    Variant{2, 2, "k32_t2_tmem_r32x1_pf2", &fill_tmem_k32_t2_r32x1_pf2, &launch_tmem_k32_t2_r32x1_pf2},
     Variant{2, 2, "k32_t2_tmem_r28x1_pf3", &fill_tmem_k32_t2_r28x1_pf3, &launch_tmem_k32_t2_r28x1_pf3},
+    Variant{2, 2, "k32_t2_tmem_w32_r28x1_pf2_b2", &fill_tmem_k32_t2_w32_r28x1_pf2_b2, &launch_tmem_k32_t2_w32_r28x1_pf2_b2},
+    Variant{2, 2, "k32_t2_tmem_r32x1_pf2", &fill_tmem_k32_t2_r32x1_pf2, &launch_tmem_k32_t2_r32x1_pf2},
     TDSE_VARIANT(2, 2, "k32_t2_w64_r32x2_pf1", float, 4, 16, 32, 2, true, 1),
     TDSE_VARIANT(0, 1, "f64_t1_w64_r16x2_pf1_b2", double, 2, 32, 16, 2, false, 1, 2),
     TDSE_VARIANT(0, 1, "f64_t1_w64_r16x1_pf2", double, 2, 32, 16, 1, false, 2),

@@ -575,5 +575,10 @@ TDSE_TMEM_VARIANT(tmem_f32_t2_r32x2_pf2, float, 4, 16, 32, 2, false, 2, 1, true)
 TDSE_TMEM_VARIANT(tmem_f32_t2_r32x1_pf3, float, 4, 16, 32, 1, false, 3, 1, true)
 TDSE_TMEM_VARIANT(tmem_f32_t2_r32x1_pf4, float, 4, 16, 32, 1, false, 4, 1, true)
 TDSE_TMEM_VARIANT(tmem_k32_t2_r28x1_pf3, float, 4, 16, 28, 1, true, 3, 1, true)
+// 32-wide boxes, two CTAs per SM: each CTA's per-plane barrier runs independently
+TDSE_TMEM_VARIANT(tmem_k32_t2_w32_r28x1_pf2_b2, float, 4, 8, 28, 1, true, 2, 2, true)
+TDSE_TMEM_VARIANT(tmem_k32_t2_w32_r32x1_pf2_b2, float, 4, 8, 32, 1, true, 2, 2, true)
+TDSE_TMEM_VARIANT(tmem_f32_t2_w32_r32x1_pf4_b2, float, 4, 8, 32, 1, false, 4, 2, true)
+TDSE_TMEM_VARIANT(tmem_f32_t2_w32_r32x1_pf3_b2, float, 4, 8, 32, 1, false, 3, 2, true)
 
 }  // namespace tdse
