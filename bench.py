@@ -60,6 +60,8 @@ def parse():
                     help="kernel variant (with --tblock) instead of the autotuner's pick; "
                          "--ncu-case default 0")
     ap.add_argument("--no-extras", action="store_true", help="skip variants, e2e and CPU baseline")
+    ap.add_argument("--adjoint-case", action="store_true",
+                    help="one FP32+Kahan forward and adjoint of the 96x96x192 case (--steps steps) for ncu")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -470,12 +472,39 @@ def adjoint_cost(torch, T):
     return out
 
 
+def adjoint_case(args):
+    """The adjoint of adjoint_cost's 96x96x192 FP32+Kahan case over --steps steps
+    (checkpoints every 100), for profiling its kernels."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2401_07416_gb300 import build, tdse as T
+    build.build()
+    from paper_2401_07416_gb300.sim import Sim
+    wl = W.config4(W.FP32_KAHAN)
+    g = wl.grid
+    with Sim(g, precision=W.FP32_KAHAN, ckpt_every=100) as s:
+        s.set_atoms(0, wl.atoms)
+        s.set_packet(0, wl.packet)
+        s.step(args.steps)
+        gF = 2 * s.flux_map(0)
+        gV = np.zeros((g.nz, g.ny, g.nx))
+        ga = np.zeros_like(wl.atoms)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T.tdse_adjoint(s.ctx, 0, gF, gV, ga)
+        el = time.perf_counter() - t0
+    print(json.dumps({"adjoint_case": True, "cells": g.cells, "steps": args.steps,
+                      "adjoint_s": el, "us_per_step": el / args.steps * 1e6}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.ncu_case:
         return ncu_case(args)
+    if args.adjoint_case:
+        return adjoint_case(args)
 
     import torch
     rank, world, local = dist_info()

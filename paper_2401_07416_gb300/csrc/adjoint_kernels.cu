@@ -5,13 +5,18 @@
 // detector flux j): It = I + A R; j = cj (R_kd It_kd+1 - R_kd+1 It_kd);
 // Rt = R - A It; R' = M Rt; I' = M It.  A is symmetric, so one backward step,
 // with (P, Q) the adjoints of (R', I') and w = dL/dF * dt * cj per pixel, is
-//   a. It = I'/M, Rt = R'/M, Pt = M P                         (pointwise)
+//   a. It = I'/M, Rt = R'/M, Pt = M P                         (per plane)
 //   b. R = Rt + A It,  Qt = M Q - A Pt                        (undo Eq. 8; adjoint of Eq. 8)
 //   c. Qt[kd+1] += w R[kd],  Qt[kd] -= w R[kd+1]              (flux w.r.t. It)
 //   d. gV -= cv (Qt R - Pt It);  P = Pt + A Qt + dj/dR        (adjoint of Eq. 9, V terms)
 //   e. I = It - A R,  Q = Qt                                  (undo Eq. 9)
-// after which (R, I) = (R^n, I^{n-1/2}) and (P, Q) their adjoints.  Arrays are
-// unpadded [nz][ny][nx]; neighbours wrap on periodic axes and read zero on walls.
+// after which (R, I) = (R^n, I^{n-1/2}) and (P, Q) their adjoints.  Step a is not a
+// pass of its own: the kernels of b, d and e scale what they read by the plane's
+// factor (M, or its reciprocal, in the context's number format: the forward
+// multiplied by exactly that M; 1 outside the absorbing layers).  FP32 contexts
+// form every product, including the dL/dV term, in FP32 and only accumulate gV in
+// FP64.  Arrays are unpadded [nz][ny][nx]; neighbours wrap on periodic axes and read
+// zero on walls.
 #include <algorithm>
 #include <cmath>
 
@@ -61,20 +66,44 @@ __device__ __forceinline__ Real dval(const Real *__restrict__ D, const Geo &g, i
     return D[static_cast<long long>(z) * g.pplane + static_cast<long long>(y + g.G) * g.pitch + (x + g.G)];
 }
 
-// (A f)(x, y, z), cell offset o: interior neighbours by offset, boundary ones through nb().
+// Plane z's factor sc[z], with the z index wrapped (periodic) or any value beyond a
+// wall (the neighbour reads zero there).
+template <typename Real>
+__device__ __forceinline__ Real plane_factor(const Real *sc, const Geo &g, int z)
+{
+    if (z < 0 || z >= g.nz) {
+        if (!g.per[2]) return Real(1);
+        z = (z % g.nz + g.nz) % g.nz;
+    }
+    return sc[z];
+}
+
+// (A (s f))(x, y, z) with s a per-plane factor (NULL: 1), cell offset o: interior
+// neighbours by offset, boundary ones through nb().
 template <typename Real>
 __device__ __forceinline__ Real apply_A(const Real *f, Real d, const Geo &g, int x, int y, int z,
-                                        long long o)
+                                        long long o, const Real *sc = nullptr)
 {
     const long long plane = static_cast<long long>(g.nx) * g.ny;
-    const Real xm = x > 0 ? f[o - 1] : nb(f, g, x - 1, y, z);
-    const Real xp = x + 1 < g.nx ? f[o + 1] : nb(f, g, x + 1, y, z);
-    const Real ym = y > 0 ? f[o - g.nx] : nb(f, g, x, y - 1, z);
-    const Real yp = y + 1 < g.ny ? f[o + g.nx] : nb(f, g, x, y + 1, z);
-    const Real zm = z > 0 ? f[o - plane] : nb(f, g, x, y, z - 1);
-    const Real zp = z + 1 < g.nz ? f[o + plane] : nb(f, g, x, y, z + 1);
+    Real xm = x > 0 ? f[o - 1] : nb(f, g, x - 1, y, z);
+    Real xp = x + 1 < g.nx ? f[o + 1] : nb(f, g, x + 1, y, z);
+    Real ym = y > 0 ? f[o - g.nx] : nb(f, g, x, y - 1, z);
+    Real yp = y + 1 < g.ny ? f[o + g.nx] : nb(f, g, x, y + 1, z);
+    Real zm = z > 0 ? f[o - plane] : nb(f, g, x, y, z - 1);
+    Real zp = z + 1 < g.nz ? f[o + plane] : nb(f, g, x, y, z + 1);
+    Real c = f[o];
+    if (sc) {
+        const Real s0 = sc[z], sm = plane_factor(sc, g, z - 1), sp = plane_factor(sc, g, z + 1);
+        xm *= s0;
+        xp *= s0;
+        ym *= s0;
+        yp *= s0;
+        c *= s0;
+        zm *= sm;
+        zp *= sp;
+    }
     return fma(static_cast<Real>(g.cx), xp + xm,
-               fma(static_cast<Real>(g.cy), yp + ym, fma(static_cast<Real>(g.cz), zp + zm, d * f[o])));
+               fma(static_cast<Real>(g.cy), yp + ym, fma(static_cast<Real>(g.cz), zp + zm, d * c)));
 }
 
 // The step kernels below run a 2-D grid: blockIdx.x * blockDim.x + threadIdx.x
@@ -85,31 +114,12 @@ __device__ __forceinline__ Real apply_A(const Real *f, Real d, const Geo &g, int
     for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < (n); \
          t += static_cast<long long>(gridDim.x) * blockDim.x)
 
-// a. It = I'/M, Rt = R'/M, Pt = M P on the absorbing planes (M = 1 elsewhere):
-// blockIdx.y enumerates the mask_lo bottom and the mask_hi top planes.
+// b. R = Rt + A It (undo Eq. 8), Qt = M Q - A Pt (adjoint of Eq. 8); Mk is M per
+// plane, Mi its reciprocal
 template <typename Real>
-__global__ void adj_unmask_kernel(Geo g, int mask_lo, int mask_hi, const double *__restrict__ M,
-                                  Real *R, Real *I, Real *P)
-{
-    const int xy = blockIdx.x * blockDim.x + threadIdx.x;
-    if (xy >= g.nx * g.ny) return;
-    const long long plane = static_cast<long long>(g.nx) * g.ny;
-    for (int j = blockIdx.y; j < mask_lo + mask_hi; j += gridDim.y) {
-        const int z = j < mask_lo ? j : g.nz - mask_hi + (j - mask_lo);
-        const double m = M[z];
-        if (m != 1.0) {
-            const long long t = z * plane + xy;
-            R[t] = static_cast<Real>(R[t] / m);
-            I[t] = static_cast<Real>(I[t] / m);
-            P[t] = static_cast<Real>(P[t] * m);
-        }
-    }
-}
-
-// b. R = Rt + A It (undo Eq. 8), Qt = M Q - A Pt (adjoint of Eq. 8)
-template <typename Real>
-__global__ void adj_b_kernel(Geo g, const double *__restrict__ M, const Real *__restrict__ D,
-                             Real *R, const Real *__restrict__ I, const Real *__restrict__ P, Real *Q)
+__global__ void adj_b_kernel(Geo g, const Real *__restrict__ Mk, const Real *__restrict__ Mi,
+                             const Real *__restrict__ D, Real *R, const Real *__restrict__ I,
+                             const Real *__restrict__ P, Real *Q)
 {
     const int xy = blockIdx.x * blockDim.x + threadIdx.x;
     if (xy >= g.nx * g.ny) return;
@@ -117,8 +127,8 @@ __global__ void adj_b_kernel(Geo g, const double *__restrict__ M, const Real *__
     for (int z = blockIdx.y; z < g.nz; z += gridDim.y) {
         const long long o = cell(g, x, y, z);
         const Real d = dval(D, g, x, y, z);
-        R[o] = R[o] + apply_A(I, d, g, x, y, z, o);
-        Q[o] = static_cast<Real>(M[z] * Q[o]) - apply_A(P, d, g, x, y, z, o);
+        R[o] = R[o] * Mi[z] + apply_A(I, d, g, x, y, z, o, Mi);
+        Q[o] = Q[o] * Mk[z] - apply_A(P, d, g, x, y, z, o, Mk);
     }
 }
 
@@ -135,9 +145,11 @@ __global__ void adj_flux_q_kernel(Geo g, int kd, const double *__restrict__ w, c
     }
 }
 
-// d. gV -= cv (Qt R - Pt It), P = Pt + A Qt + dj/dR (adjoint of Eq. 9)
+// d. gV -= cv (Qt R - Pt It), P = Pt + A Qt + dj/dR (adjoint of Eq. 9); Pt = M P and
+// It = I' / M at the plane
 template <typename Real>
-__global__ void adj_d_kernel(Geo g, const Real *__restrict__ D, int kd, const double *__restrict__ w,
+__global__ void adj_d_kernel(Geo g, const Real *__restrict__ Mk, const Real *__restrict__ Mi,
+                             const Real *__restrict__ D, int kd, const double *__restrict__ w,
                              const Real *__restrict__ R, const Real *__restrict__ I, Real *P,
                              const Real *__restrict__ Q, double *gV)
 {
@@ -147,12 +159,14 @@ __global__ void adj_d_kernel(Geo g, const Real *__restrict__ D, int kd, const do
     const int x = xy % g.nx, y = xy / g.nx;
     for (int z = blockIdx.y; z < g.nz; z += gridDim.y) {
         const long long o = cell(g, x, y, z);
-        const Real pt = P[o];
-        gV[o] -= g.cv * (static_cast<double>(Q[o]) * R[o] - static_cast<double>(pt) * I[o]);
+        const Real pt = P[o] * Mk[z];
+        const Real it = I[o] * Mi[z];
+        const Real v = Q[o] * R[o] - pt * it;
+        gV[o] -= g.cv * static_cast<double>(v);
         Real pn = pt + apply_A(Q, dval(D, g, x, y, z), g, x, y, z, o);
         if (kd >= 0) {
-            if (z == kd) pn += static_cast<Real>(w[xy]) * I[o + plane];
-            else if (z == kd + 1) pn -= static_cast<Real>(w[xy]) * I[o - plane];
+            if (z == kd) pn += static_cast<Real>(w[xy]) * (I[o + plane] * Mi[kd + 1]);
+            else if (z == kd + 1) pn -= static_cast<Real>(w[xy]) * (I[o - plane] * Mi[kd]);
         }
         P[o] = pn;
     }
@@ -160,14 +174,15 @@ __global__ void adj_d_kernel(Geo g, const Real *__restrict__ D, int kd, const do
 
 // e. I = It - A R (undo Eq. 9)
 template <typename Real>
-__global__ void adj_e_kernel(Geo g, const Real *__restrict__ D, const Real *__restrict__ R, Real *I)
+__global__ void adj_e_kernel(Geo g, const Real *__restrict__ Mi, const Real *__restrict__ D,
+                             const Real *__restrict__ R, Real *I)
 {
     const int xy = blockIdx.x * blockDim.x + threadIdx.x;
     if (xy >= g.nx * g.ny) return;
     const int x = xy % g.nx, y = xy / g.nx;
     for (int z = blockIdx.y; z < g.nz; z += gridDim.y) {
         const long long o = cell(g, x, y, z);
-        I[o] = I[o] - apply_A(R, dval(D, g, x, y, z), g, x, y, z, o);
+        I[o] = I[o] * Mi[z] - apply_A(R, dval(D, g, x, y, z), g, x, y, z, o);
     }
 }
 
@@ -318,18 +333,12 @@ cudaError_t backward_step_t(const MemberDev &m, const AdjointBuffers &b, cudaStr
     Real *R = static_cast<Real *>(b.R), *I = static_cast<Real *>(b.I);
     Real *P = static_cast<Real *>(b.P), *Q = static_cast<Real *>(b.Q);
     const Real *D = static_cast<const Real *>(m.d);
-    // absorbing planes only (all planes, each once, if the layers overlap)
-    int lo = m.mask_lo, hi = m.mask_hi;
-    if (lo + hi > m.nz) lo = m.nz, hi = 0;
-    if (lo + hi > 0) {
-        const dim3 ug(grid.x, static_cast<unsigned>(std::min(lo + hi, 65535)));
-        adj_unmask_kernel<Real><<<ug, kThreads, 0, s>>>(g, lo, hi, b.M, R, I, P);
-    }
-    adj_b_kernel<Real><<<grid, kThreads, 0, s>>>(g, b.M, D, R, I, P, Q);
+    const Real *Mk = static_cast<const Real *>(m.mask), *Mi = static_cast<const Real *>(b.Minv);
+    adj_b_kernel<Real><<<grid, kThreads, 0, s>>>(g, Mk, Mi, D, R, I, P, Q);
     const int kd = m.det_k;
     if (kd >= 0) adj_flux_q_kernel<Real><<<grid_for(plane), kThreads, 0, s>>>(g, kd, b.w, R, Q);
-    adj_d_kernel<Real><<<grid, kThreads, 0, s>>>(g, D, kd, b.w, R, I, P, Q, b.gV);
-    adj_e_kernel<Real><<<grid, kThreads, 0, s>>>(g, D, R, I);
+    adj_d_kernel<Real><<<grid, kThreads, 0, s>>>(g, Mk, Mi, D, kd, b.w, R, I, P, Q, b.gV);
+    adj_e_kernel<Real><<<grid, kThreads, 0, s>>>(g, Mi, D, R, I);
     return cudaGetLastError();
 }
 

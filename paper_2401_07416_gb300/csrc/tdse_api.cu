@@ -31,7 +31,7 @@ struct Member {
     double soft_a2 = 0.25, r_cut = 0.0;
     double q0 = 0.0;                // Q at the last set_wavepacket / set_state
     std::vector<double> hist;       // 4 per record: step, Q, norm_paper, energy
-    double *mask64 = nullptr;       // absorbing factor per plane, FP64 (adjoint)
+    void *mask_inv = nullptr;       // reciprocal of the absorbing factor per plane (adjoint)
     bool from_packet = false;       // the run started with tdse_set_wavepacket
     std::vector<std::pair<long long, double *>> ckpts;   // (step, FP64 R then I)
     double *frames = nullptr;       // detector density frames [frame_cap][ny][nx] (Eq. 15)
@@ -359,12 +359,19 @@ tdse_status ensure_device(tdse_ctx *c)
             if (q.mask_hi > 0 && k >= d.nz - q.mask_hi)
                 M[k] = factor(k - (d.nz - q.mask_hi) + 1, q.mask_hi);
         }
-        TRY(dalloc(c, d.nz * sizeof(double), &p)); mb.mask64 = static_cast<double *>(p);
-        CUDA_TRY(c, cudaMemcpyAsync(mb.mask64, M.data(), d.nz * sizeof(double),
-                                    cudaMemcpyHostToDevice, c->stream));
         TRY(dalloc(c, d.nz * es, &p)); d.mask = p;
-        std::vector<float> Mf(M.begin(), M.end());
+        TRY(dalloc(c, d.nz * es, &p)); mb.mask_inv = p;
+        // the factor in the step's number format, and its reciprocal (rounded once
+        // from the exact reciprocal of that factor)
+        std::vector<float> Mf(M.begin(), M.end()), Mfi(d.nz);
+        std::vector<double> Mi(d.nz);
+        for (int k = 0; k < d.nz; ++k) {
+            Mi[k] = 1.0 / M[k];
+            Mfi[k] = static_cast<float>(1.0 / static_cast<double>(Mf[k]));
+        }
         CUDA_TRY(c, cudaMemcpyAsync(d.mask, es == 8 ? static_cast<const void *>(M.data()) : Mf.data(),
+                                    d.nz * es, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(mb.mask_inv, es == 8 ? static_cast<const void *>(Mi.data()) : Mfi.data(),
                                     d.nz * es, cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     }
@@ -1113,7 +1120,7 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
         cleanup();
         return st;
     }
-    AdjointBuffers b{R, I, P, Q, static_cast<double *>(gV), static_cast<double *>(w), mb.mask64,
+    AdjointBuffers b{R, I, P, Q, static_cast<double *>(gV), static_cast<double *>(w), mb.mask_inv,
                      mb.V64};
     // backward steps of one checkpoint segment, replayed from a CUDA graph per
     // segment length (the buffers are this call's, so the graphs are too)

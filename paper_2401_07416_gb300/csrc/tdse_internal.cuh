@@ -131,7 +131,8 @@ struct AdjointBuffers {
     void *P, *Q;          // their adjoints
     double *gV;           // dL/dV accumulator
     double *w;            // dL/dF * dt * cj per detector pixel
-    const double *M;      // absorbing factor per plane (FP64)
+    const void *Minv;     // reciprocal of the absorbing factor per plane (the context's
+                          // number format, like MemberDev::mask)
     const double *V;      // potential (FP64)
 };
 cudaError_t adjoint_backward_step(const MemberDev &m, int elem, const AdjointBuffers &b,
