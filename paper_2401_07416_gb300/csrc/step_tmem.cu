@@ -511,6 +511,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             ++dj;   // slots are taken modulo NDT
         }
 
+        __syncthreads();   // every thread has left the z-march: all read the same s_abort
         if (s_abort) {
             // wait (bounded) for the loads still in flight, then leave (freeing TMEM below)
             if (tid == 0) {
