@@ -347,9 +347,23 @@ def batch_throughput(torch, T, steps, warmup):
         ms, prof = timed_steps(torch, T, s, steps, warmup, lambda: None)
         tun = s.tuning()
     cells = sum(m.grid.cells for m in members)
+    # the same members one at a time, each in its own autotuned context: the batch's
+    # gain over running them back to back
+    solo_steps = max(10, steps // 2 // 2 * 2)
+    solo_ms = 0.0
+    for m in members:
+        with Sim(m.grid, precision=W.FP32_KAHAN) as s1:
+            s1.set_atoms(0, m.atoms)
+            s1.autotune(2)
+            s1.set_packet(0, m.packet)
+            ms1, _ = timed_steps(torch, T, s1, solo_steps, warmup, lambda: None)
+        solo_ms += ms1 * steps / solo_steps
     return {"value": cells * steps / (ms * 1e-3), "unit": "cell-updates/s", "members": 48,
             "cells": cells, "steps": steps, "precision": "f32+kahan", "tuning": tun,
-            "graphs": "profiling pass (direct launches)"}
+            "graphs": "profiling pass (direct launches)",
+            "solo_sum_value": cells * steps / (solo_ms * 1e-3),
+            "batch_over_solo": solo_ms / ms,
+            "solo": f"each member alone, {solo_steps} steps, autotuned, same timing method"}
 
 
 def absorber_reflection(torch, T):

@@ -40,20 +40,22 @@ __device__ __forceinline__ long long cell(const Geo &g, int x, int y, int z)
     return (static_cast<long long>(z) * g.ny + y) * g.nx + x;
 }
 
+// Neighbour value one cell beyond the grid on some axis: the periodic image (one
+// wrap, as the offset is at most one cell) or zero beyond a wall.
 template <typename Real>
 __device__ __forceinline__ Real nb(const Real *f, const Geo &g, int x, int y, int z)
 {
     if (x < 0 || x >= g.nx) {
         if (!g.per[0]) return Real(0);
-        x = (x % g.nx + g.nx) % g.nx;
+        x += x < 0 ? g.nx : -g.nx;
     }
     if (y < 0 || y >= g.ny) {
         if (!g.per[1]) return Real(0);
-        y = (y % g.ny + g.ny) % g.ny;
+        y += y < 0 ? g.ny : -g.ny;
     }
     if (z < 0 || z >= g.nz) {
         if (!g.per[2]) return Real(0);
-        z = (z % g.nz + g.nz) % g.nz;
+        z += z < 0 ? g.nz : -g.nz;
     }
     return f[cell(g, x, y, z)];
 }
@@ -66,14 +68,14 @@ __device__ __forceinline__ Real dval(const Real *__restrict__ D, const Geo &g, i
     return D[static_cast<long long>(z) * g.pplane + static_cast<long long>(y + g.G) * g.pitch + (x + g.G)];
 }
 
-// Plane z's factor sc[z], with the z index wrapped (periodic) or any value beyond a
-// wall (the neighbour reads zero there).
+// Plane z's factor sc[z] for z at most one plane outside the grid: wrapped on a
+// periodic axis, any value beyond a wall (the neighbour reads zero there).
 template <typename Real>
 __device__ __forceinline__ Real plane_factor(const Real *sc, const Geo &g, int z)
 {
     if (z < 0 || z >= g.nz) {
         if (!g.per[2]) return Real(1);
-        z = (z % g.nz + g.nz) % g.nz;
+        z += z < 0 ? g.nz : -g.nz;
     }
     return sc[z];
 }
