@@ -198,7 +198,7 @@ __global__ void potential_kernel(MemberDev m, const AtomCell *__restrict__ atoms
             if (cut && u >= cuc) continue;   // beyond the cut-off the profile is zero
             Compute phi;
             if constexpr (sizeof(Compute) == 8) {
-                phi = 1.0 / sqrt(u + ca2);
+                phi = rsqrt(u + ca2);   // library reciprocal square root (within 1 ulp)
             } else {
                 phi = rsqrtf(u + ca2);
             }
