@@ -7,8 +7,10 @@ Tolerances (written here, used by every case):
                    |Q_gpu - Q_oracle| / Q_oracle <= 1e-5;
   fused vs unfused and batched vs solo: bitwise equal (same arithmetic, same order).
 Small grids span several tiles with ragged tails in x, y and z (default tiles are
-56 x 20 in FP32 T=1, 56 x 24 in FP32 and Kahan T=2, 60 x 12 in FP64;
-z-chunks are chosen per launch).
+56 x 20 in FP32 T=1, 24 x 24 in FP32 and Kahan T=2, 60 x 12 in FP64;
+z-chunks are chosen per launch), and the degenerate cases: the smallest legal grid
+(4 x 1 x 3, walls) and a grid whose periodic z axis (3 planes) is shorter than the
+z halo of a two-step launch.
 """
 import math
 
@@ -57,6 +59,11 @@ CASES = {
     "mixed": (36, 28, 33, (0, 1, 0), 4, 9),
     # periodic axes shorter than twice the ghost width: both ghost zones are copies
     "short": (12, 9, 26, (0, 0, 1), 3, 8),
+    # the smallest legal grid (nx >= 4, ny >= 1, nz >= 3), walls everywhere
+    "minimal": (4, 1, 3, (1, 1, 1), 0, -1),
+    # periodic everywhere at the shortest periodic lengths, 3 z planes (the z halo
+    # of a two-step launch wraps around the axis more than once)
+    "thin": (8, 8, 3, (0, 0, 0), 0, 0),
 }
 
 
@@ -129,6 +136,22 @@ def test_fused_two_steps_bitwise_equal_to_one_step_launches(T, name, precision):
     b = gpu_run(g, V, p, 18, getattr(T, precision), tblock=1)
     for x, y in zip(a[1], b[1]):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32_KAHAN"])
+def test_zero_steps_leave_the_state(T, precision):
+    g, V, p = case("slab")
+    s = make_sim(g, getattr(T, precision))
+    s.set_potential(0, V)
+    s.set_packet(0, p)
+    R0, I0 = s.state(0)
+    q0 = s.observables(0)
+    s.step(0)
+    R1, I1 = s.state(0)
+    q1 = s.observables(0)
+    s.close()
+    assert np.array_equal(R0, R1) and np.array_equal(I0, I1)
+    assert q1["step"] == q0["step"] and q1["Q"] == q0["Q"]
 
 
 def test_potential_from_atoms_matches_oracle(T):
@@ -230,7 +253,7 @@ def test_unstable_run_reports_status(T):
 
 
 @pytest.mark.parametrize("precision", ["FP32", "FP32_KAHAN"])
-@pytest.mark.parametrize("name", ["walls", "mixed", "short"])
+@pytest.mark.parametrize("name", ["walls", "mixed", "short", "minimal", "thin"])
 def test_every_two_step_variant_bitwise_equal(T, name, precision):
     """Register-window and tensor-memory-window kernels, every tile shape: the same
     arithmetic in the same order, so states and flux maps agree bit for bit."""
