@@ -11,7 +11,7 @@
 //   d. gV -= cv (Qt R - Pt It);  P = Pt + A Qt + dj/dR        (adjoint of Eq. 9, V terms)
 //   e. I = It - A R,  Q = Qt                                  (undo Eq. 9)
 // after which (R, I) = (R^n, I^{n-1/2}) and (P, Q) their adjoints.  Step a is not a
-// pass of its own: the kernels of b, d and e scale what they read by the plane's
+// pass of its own, and d and e share one: the kernels scale what they read by the plane's
 // factor (M, or its reciprocal, in the context's number format: the forward
 // multiplied by exactly that M; 1 outside the absorbing layers).  FP32 contexts
 // form every product, including the dL/dV term, in FP32 and only accumulate gV in
@@ -134,26 +134,35 @@ __global__ void adj_b_kernel(Geo g, const Real *__restrict__ Mk, const Real *__r
     }
 }
 
-// c. the detector flux w.r.t. It
+// c. the detector flux w.r.t. It; also keeps It of the two detector planes (Ist[0..plane)
+// = plane kd, Ist[plane..2 plane) = plane kd+1) for dj/dR in the pass below, which
+// overwrites I
 template <typename Real>
-__global__ void adj_flux_q_kernel(Geo g, int kd, const double *__restrict__ w, const Real *R, Real *Q)
+__global__ void adj_flux_q_kernel(Geo g, int kd, const double *__restrict__ w,
+                                  const Real *__restrict__ Mi, const Real *R,
+                                  const Real *__restrict__ I, Real *Q, Real *__restrict__ Ist)
 {
     const long long plane = static_cast<long long>(g.nx) * g.ny;
     GRID_STRIDE(p, plane)
     {
         const Real wp = static_cast<Real>(w[p]);
+        Ist[p] = I[kd * plane + p] * Mi[kd];
+        Ist[plane + p] = I[(kd + 1) * plane + p] * Mi[kd + 1];
         Q[(kd + 1) * plane + p] += wp * R[kd * plane + p];
         Q[kd * plane + p] -= wp * R[(kd + 1) * plane + p];
     }
 }
 
-// d. gV -= cv (Qt R - Pt It), P = Pt + A Qt + dj/dR (adjoint of Eq. 9); Pt = M P and
-// It = I' / M at the plane
+// d and e in one pass, with Pt = M P and It = I' / M at the plane:
+//   gV -= cv (Qt R - Pt It), P = Pt + A Qt + dj/dR   (adjoint of Eq. 9)
+//   I = It - A R                                      (undo Eq. 9)
+// Neither reads as a stencil what the other writes (Q and R are read, P and I written
+// at the cell itself); dj/dR reads It of the other detector plane from Ist.
 template <typename Real>
-__global__ void adj_d_kernel(Geo g, const Real *__restrict__ Mk, const Real *__restrict__ Mi,
-                             const Real *__restrict__ D, int kd, const double *__restrict__ w,
-                             const Real *__restrict__ R, const Real *__restrict__ I, Real *P,
-                             const Real *__restrict__ Q, double *gV)
+__global__ void adj_de_kernel(Geo g, const Real *__restrict__ Mk, const Real *__restrict__ Mi,
+                              const Real *__restrict__ D, int kd, const double *__restrict__ w,
+                              const Real *__restrict__ Ist, const Real *__restrict__ R, Real *I,
+                              Real *P, const Real *__restrict__ Q, double *gV)
 {
     const long long plane = static_cast<long long>(g.nx) * g.ny;
     const int xy = blockIdx.x * blockDim.x + threadIdx.x;
@@ -161,30 +170,18 @@ __global__ void adj_d_kernel(Geo g, const Real *__restrict__ Mk, const Real *__r
     const int x = xy % g.nx, y = xy / g.nx;
     for (int z = blockIdx.y; z < g.nz; z += gridDim.y) {
         const long long o = cell(g, x, y, z);
+        const Real d = dval(D, g, x, y, z);
         const Real pt = P[o] * Mk[z];
         const Real it = I[o] * Mi[z];
         const Real v = Q[o] * R[o] - pt * it;
         gV[o] -= g.cv * static_cast<double>(v);
-        Real pn = pt + apply_A(Q, dval(D, g, x, y, z), g, x, y, z, o);
+        Real pn = pt + apply_A(Q, d, g, x, y, z, o);
         if (kd >= 0) {
-            if (z == kd) pn += static_cast<Real>(w[xy]) * (I[o + plane] * Mi[kd + 1]);
-            else if (z == kd + 1) pn -= static_cast<Real>(w[xy]) * (I[o - plane] * Mi[kd]);
+            if (z == kd) pn += static_cast<Real>(w[xy]) * Ist[plane + xy];
+            else if (z == kd + 1) pn -= static_cast<Real>(w[xy]) * Ist[xy];
         }
         P[o] = pn;
-    }
-}
-
-// e. I = It - A R (undo Eq. 9)
-template <typename Real>
-__global__ void adj_e_kernel(Geo g, const Real *__restrict__ Mi, const Real *__restrict__ D,
-                             const Real *__restrict__ R, Real *I)
-{
-    const int xy = blockIdx.x * blockDim.x + threadIdx.x;
-    if (xy >= g.nx * g.ny) return;
-    const int x = xy % g.nx, y = xy / g.nx;
-    for (int z = blockIdx.y; z < g.nz; z += gridDim.y) {
-        const long long o = cell(g, x, y, z);
-        I[o] = I[o] * Mi[z] - apply_A(R, dval(D, g, x, y, z), g, x, y, z, o);
+        I[o] = it - apply_A(R, d, g, x, y, z, o);
     }
 }
 
@@ -336,11 +333,12 @@ cudaError_t backward_step_t(const MemberDev &m, const AdjointBuffers &b, cudaStr
     Real *P = static_cast<Real *>(b.P), *Q = static_cast<Real *>(b.Q);
     const Real *D = static_cast<const Real *>(m.d);
     const Real *Mk = static_cast<const Real *>(m.mask), *Mi = static_cast<const Real *>(b.Minv);
+    Real *Ist = static_cast<Real *>(b.Ist);
     adj_b_kernel<Real><<<grid, kThreads, 0, s>>>(g, Mk, Mi, D, R, I, P, Q);
     const int kd = m.det_k;
-    if (kd >= 0) adj_flux_q_kernel<Real><<<grid_for(plane), kThreads, 0, s>>>(g, kd, b.w, R, Q);
-    adj_d_kernel<Real><<<grid, kThreads, 0, s>>>(g, Mk, Mi, D, kd, b.w, R, I, P, Q, b.gV);
-    adj_e_kernel<Real><<<grid, kThreads, 0, s>>>(g, Mi, D, R, I);
+    if (kd >= 0)
+        adj_flux_q_kernel<Real><<<grid_for(plane), kThreads, 0, s>>>(g, kd, b.w, Mi, R, I, Q, Ist);
+    adj_de_kernel<Real><<<grid, kThreads, 0, s>>>(g, Mk, Mi, D, kd, b.w, Ist, R, I, P, Q, b.gV);
     return cudaGetLastError();
 }
 

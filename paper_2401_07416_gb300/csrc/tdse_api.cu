@@ -1111,17 +1111,17 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
         cudaStreamSynchronize(c->stream);
         for (void *p : tmp) dfree(c, p);
     };
-    void *R, *I, *P, *Q, *gV, *w, *gF, *cur;
+    void *R, *I, *P, *Q, *gV, *w, *gF, *cur, *Ist;
     tdse_status st = TDSE_OK;
     if ((st = alloc(cells * elem, &R)) || (st = alloc(cells * elem, &I)) ||
         (st = alloc(cells * elem, &P)) || (st = alloc(cells * elem, &Q)) ||
         (st = alloc(cells * 8, &gV)) || (st = alloc(npix * 8, &w)) || (st = alloc(npix * 8, &gF)) ||
-        (st = alloc(2 * cells * 8, &cur))) {
+        (st = alloc(2 * cells * 8, &cur)) || (st = alloc(2 * npix * elem, &Ist))) {
         cleanup();
         return st;
     }
     AdjointBuffers b{R, I, P, Q, static_cast<double *>(gV), static_cast<double *>(w), mb.mask_inv,
-                     mb.V64};
+                     Ist, mb.V64};
     // backward steps of one checkpoint segment, replayed from a CUDA graph per
     // segment length (the buffers are this call's, so the graphs are too)
     std::vector<std::pair<long long, cudaGraphExec_t>> graphs;

@@ -133,6 +133,7 @@ struct AdjointBuffers {
     double *w;            // dL/dF * dt * cj per detector pixel
     const void *Minv;     // reciprocal of the absorbing factor per plane (the context's
                           // number format, like MemberDev::mask)
+    void *Ist;            // It of the two detector planes (2 nx ny values, that format)
     const double *V;      // potential (FP64)
 };
 cudaError_t adjoint_backward_step(const MemberDev &m, int elem, const AdjointBuffers &b,
