@@ -240,7 +240,11 @@ TDSE_API tdse_status tdse_dissimilarity(const double *frames, int K, int M, long
  * invertible: R^n = R~ + A I~, I^{n-1/2} = I~ - A R^n with R~ = R^{n+1}/M,
  * I~ = I^{n+1/2}/M), re-anchored at every FP64 checkpoint; the adjoint
  * recursion is the transpose of the forward step.  The forward state is left
- * unchanged. */
+ * unchanged.  ESTATE: no state, no checkpoints, or dL_datoms without atoms;
+ * EINVAL: dL_dF NULL, or an absorbing factor M that is 0 in the step's number format
+ * (a CAP with W dt / hbar beyond about 745 in FP64 or 103 in FP32 underflows), which
+ * the backward steps cannot divide out.  A small M is accepted, but the reversal
+ * amplifies rounding by up to (1 / M_min)^ckpt_every between checkpoints. */
 TDSE_API tdse_status tdse_adjoint(tdse_ctx *ctx, int member, const double *dL_dF, double *dL_dV,
                          double *dL_datoms, int on_device);
 

@@ -32,6 +32,7 @@ struct Member {
     double q0 = 0.0;                // Q at the last set_wavepacket / set_state
     std::vector<double> hist;       // 4 per record: step, Q, norm_paper, energy
     void *mask_inv = nullptr;       // reciprocal of the absorbing factor per plane (adjoint)
+    double mask_min = 1.0;          // smallest factor, in the step's number format
     bool from_packet = false;       // the run started with tdse_set_wavepacket
     std::vector<std::pair<long long, double *>> ckpts;   // (step, FP64 R then I)
     double *frames = nullptr;       // detector density frames [frame_cap][ny][nx] (Eq. 15)
@@ -368,6 +369,7 @@ tdse_status ensure_device(tdse_ctx *c)
         for (int k = 0; k < d.nz; ++k) {
             Mi[k] = 1.0 / M[k];
             Mfi[k] = static_cast<float>(1.0 / static_cast<double>(Mf[k]));
+            mb.mask_min = std::min(mb.mask_min, es == 8 ? M[k] : static_cast<double>(Mf[k]));
         }
         CUDA_TRY(c, cudaMemcpyAsync(d.mask, es == 8 ? static_cast<const void *>(M.data()) : Mf.data(),
                                     d.nz * es, cudaMemcpyHostToDevice, c->stream));
@@ -1097,6 +1099,9 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
         return fail(c, TDSE_ESTATE, "no checkpoints: create the context with ckpt_every > 0");
     if (dL_datoms && mb.atoms.empty())
         return fail(c, TDSE_ESTATE, "dL_datoms requested but the potential did not come from atoms");
+    if (!(mb.mask_min > 0.0))
+        return fail(c, TDSE_EINVAL, "an absorbing factor is 0 (in the step's number format): "
+                                    "the backward steps cannot undo it");
     const MemberDev &d = mb.dev;
     const size_t cells = static_cast<size_t>(d.nx) * d.ny * d.nz;
     const size_t npix = static_cast<size_t>(d.nx) * d.ny;

@@ -109,3 +109,19 @@ def test_config4_adjoint_vs_finite_differences_and_autograd(T):
     fd = np.array(fd)
     ad = np.array([grad[a, k] for a, k in checks])
     assert np.linalg.norm(ad - fd) <= 1e-6 * np.linalg.norm(fd)
+
+
+def test_adjoint_rejects_a_zero_absorbing_factor(T):
+    """A CAP layer so strong that exp(-W dt / hbar) underflows to 0 on its outer planes:
+    the forward runs, the adjoint cannot divide the factor out and reports EINVAL."""
+    import dataclasses
+    from paper_2401_07416_gb300.sim import Sim
+    g = W.small_grid(16, 12, 24, h=(0.2, 0.2, 0.2), dt=0.004, bc=(0, 0, 1), mask=4, det_k=10)
+    g = dataclasses.replace(g, obs_every=5, mask_kind=W.MASK_CAP, mask_eta=1e6)
+    with Sim(g, precision=T.FP64, ckpt_every=5) as s:
+        s.set_potential(0, W.random_potential(g, 3, 1.0))
+        s.set_packet(0, W.Packet((1.6, 1.2, 2.4), (0.6, 0.6, 0.6), (0.0, 0.0, 1.0)))
+        s.step(10)
+        with pytest.raises(T.TdseError) as e:
+            T.tdse_adjoint(s.ctx, 0, np.ones((g.ny, g.nx)), None, None)
+        assert e.value.status == T.EINVAL
