@@ -12,7 +12,8 @@ Also reported: the FP64 unfused GPU step on the same grid and the FP32 variants,
 the roofline of the dominant kernel (HBM bytes of the algorithm per launch over
 the launch's CUDA-event time, against the measured HBM copy bandwidth), the FP64
 oracle timed on this host's cores (a baseline, not the target), and the same
-metric end to end through the C ABI from pinned host buffers.
+metric end to end through the C ABI from pinned host buffers, over complete
+runs of the workload (1000 steps each, set-up and result read-back included).
 
 Multi-GPU (torchrun): each rank advances its own replica (weak scaling, no data
 exchange), the time is the max over ranks.  `--impl reference` times the FP64
@@ -616,7 +617,9 @@ def main():
         extras["paper_cu111_240x240x520"] = paper_cu111_throughput(torch, T)
 
         # end to end through the C ABI from pinned host buffers: potential in,
-        # packet set-up, the steps, flux map and observables out
+        # packet set-up, the steps, flux map and observables out, over one complete
+        # run of the workload (its own length, 1000 steps, whatever --steps is)
+        run_steps = wl.steps
         V_host = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, pin_memory=True)
         V_host.copy_(V_dev.cpu())
         F_host = torch.empty((g.ny, g.nx), dtype=torch.float64, pin_memory=True)
@@ -627,11 +630,11 @@ def main():
         se.set_packet(0, wl.packet)
         se.step(4)
         torch.cuda.synchronize()
-        # three complete runs (the host-to-device copy of V shares the host's memory
+        # five complete runs (the host-to-device copy of V shares the host's memory
         # system with other work on this machine and varies run to run); the median
         # run is reported, every run is listed
         runs = []
-        for _ in range(3):
+        for _ in range(5):
             barrier()
             t0 = time.perf_counter()
             T.tdse_set_potential(se.ctx, 0, V_host)
@@ -639,28 +642,30 @@ def main():
             t1 = time.perf_counter()
             se.set_packet(0, wl.packet)
             t2 = time.perf_counter()
-            se.step(args.steps)
+            se.step(run_steps)
             torch.cuda.synchronize()
             t3 = time.perf_counter()
             T.tdse_get_flux_map(se.ctx, 0, F_host)
             se.observables(0)
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
-            runs.append({"value": world * cells * args.steps / el,
+            runs.append({"value": world * cells * run_steps / el,
                          "phases_ms": {"set_potential_h2d": (t1 - t0) * 1e3,
                                        "set_wavepacket": (t2 - t1) * 1e3,
                                        "steps": (t3 - t2) * 1e3,
                                        "flux_and_observables_d2h": (time.perf_counter() - t3) * 1e3}})
         barrier()
         se.close()
-        med = sorted(runs, key=lambda r: r["value"])[1]
+        med = sorted(runs, key=lambda r: r["value"])[len(runs) // 2]
         e2e = {"value": med["value"], "unit": "cell-updates/s",
-               "h2d_bytes_per_step": V_host.numel() * 8 / args.steps,
-               "d2h_bytes_per_step": (F_host.numel() * 8 + 64) / args.steps,
+               "steps": run_steps,
+               "h2d_bytes_per_step": V_host.numel() * 8 / run_steps,
+               "d2h_bytes_per_step": (F_host.numel() * 8 + 64) / run_steps,
                "includes": "tdse_set_potential (pinned host V, FP64), tdse_set_wavepacket, "
                            "tdse_step (CUDA-graph replay), tdse_get_flux_map, tdse_observables",
                "phases_ms": med["phases_ms"], "runs": [r["value"] for r in runs],
-               "statistic": "median of 3 complete runs"}
+               "set_potential_h2d_ms_per_run": [r["phases_ms"]["set_potential_h2d"] for r in runs],
+               "statistic": f"median of {len(runs)} complete runs"}
         del V_host
         if rank == 0 and world == 1:
             cpu = time_oracle(args.cpu_seconds)

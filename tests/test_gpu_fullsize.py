@@ -169,7 +169,7 @@ def window_oracle(wl, x0, y0, width, steps):
     return R, I
 
 
-@pytest.mark.parametrize("precision", ["FP32_KAHAN", "FP64"])
+@pytest.mark.parametrize("precision", ["FP32_KAHAN", "FP32", "FP64"])
 def test_config5_light_cone_windows(T, precision):
     import torch
     prec = getattr(T, precision)
