@@ -120,7 +120,8 @@ typedef void (*tdse_free_fn)(void *ptr, void *user);
  * share precision, tblock, obs_every and ckpt_every.  Validates everything
  * (EINVAL: shape, spacing, dt above the leapfrog stability bound of the free
  * part, nx not a multiple of 4, periodic axis shorter than 8, det_k outside
- * [0, nz-2]); allocates no device memory.  *out receives the context. */
+ * [0, nz-2], an xy plane above 2^30 nodes with its ghost zones); allocates no
+ * device memory.  *out receives the context. */
 TDSE_API tdse_status tdse_create(const tdse_params *p, int batch, tdse_ctx **out);
 
 /* Route device allocations through (alloc, free, user), e.g. a framework's

@@ -3,6 +3,9 @@
 // the compile-time kernel shape and the per-item scalars.
 #pragma once
 
+#include <atomic>
+#include <cstdint>
+
 #include "tdse_internal.cuh"
 
 namespace tdse {
@@ -308,4 +311,21 @@ __device__ __forceinline__ void store_output_row(const ItemScalars &S, Real *out
 }
 
 }  // namespace
+
+// Dynamic shared memory above 48 KB must be allowed per kernel, and the setting
+// belongs to the device that is current when it is made: set it once on each
+// device (a process may drive several GPUs, one context on each).
+template <class K>
+cudaError_t allow_dynamic_smem(K *kernel, size_t bytes, std::atomic<uint64_t> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? (uint64_t{1} << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
 }  // namespace tdse

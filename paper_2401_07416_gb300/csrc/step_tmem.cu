@@ -537,14 +537,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 template <class C>
 cudaError_t launch_tmem_cfg(const StepLaunch &L)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fused_step_tmem_kernel<C>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(C::SMEM));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> smem_allowed{0};   // one bit per device
+    cudaError_t e = allow_dynamic_smem(fused_step_tmem_kernel<C>, C::SMEM, smem_allowed);
+    if (e != cudaSuccess) return e;
     fused_step_tmem_kernel<C><<<L.grid, C::NT, C::SMEM, L.stream>>>(L.members, L.work, L.counter,
                                                                     L.status, L.in_buf);
     return cudaGetLastError();

@@ -166,6 +166,10 @@ tdse_status validate(tdse_ctx *c, const tdse_params &q, int idx)
         return fail(c, TDSE_EINVAL, "member %d: grid %dx%dx%d too small (nx >= 4, nz >= 3)", idx,
                     q.nx, q.ny, q.nz);
     if (q.nx % 4 != 0) return fail(c, TDSE_EINVAL, "member %d: nx=%d is not a multiple of 4", idx, q.nx);
+    // per-plane indices (pixels, ghost cells, plane offsets inside a kernel) are 32-bit
+    if (static_cast<long long>(q.nx + 2 * kGhost + 32) * (q.ny + 2 * kGhost) > (1LL << 30))
+        return fail(c, TDSE_EINVAL, "member %d: an xy plane of %dx%d nodes exceeds 2^30 (padded)", idx,
+                    q.nx, q.ny);
     if (!(q.hx > 0 && q.hy > 0 && q.hz > 0))
         return fail(c, TDSE_EINVAL, "member %d: spacings must be positive", idx);
     for (int a = 0; a < 3; ++a)

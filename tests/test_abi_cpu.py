@@ -80,6 +80,7 @@ def _params(**kw):
     ("precision", 7),
     ("tblock", 5),
     ("mask_kind", 2),      # neither cos^2 nor the Eq. 10 absorbing potential
+    ("ny", 1 << 25),       # xy plane above 2^30 nodes (32-bit per-plane indices)
 ])
 def test_create_rejects_bad_parameters(lib, field, value):
     with pytest.raises(T.TdseError) as e:
