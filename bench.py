@@ -594,28 +594,6 @@ def main():
     e2e = None
     cpu = None
     if not args.no_extras:
-        # FP64 unfused step and the FP32 variants on the same grid (same potential)
-        variants = [(W.FP64, 1)] + [(p, t) for p in (W.FP32, W.FP32_KAHAN) for t in (1, 2)]
-        for vp, vt in variants:
-            steps_v = max(10, args.steps // (8 if vp == W.FP64 else 2))
-            sv = make_ctx(T, W.config5(vp), vp, vt, V_dev)
-            vname = sv.tuning()["name"][vt]
-            vms, vprof = timed_steps(torch, T, sv, steps_v, min(args.warmup, 6), barrier)
-            sv.close()
-            vlaunch = vprof["step_ms"] / max(1, vprof["step_launches"])
-            extras[f"{PREC_NAME[vp]}_t{vt}"] = {
-                "value": cells * steps_v / (vms * 1e-3), "unit": "cell-updates/s",
-                "steps": steps_v, "variant": vname, "avg_launch_ms": vlaunch,
-                "hbm_frac_of_algorithmic_bytes": BYTES_PER_NODE[vp] * cells / (vlaunch * 1e-3) / 1e9 / hbm_peak}
-        extras["speedup_vs_fp64_plain"] = value / world / extras["f64_t1"]["value"]
-        extras["batched_48_films"] = batch_throughput(torch, T, max(20, args.steps // 2),
-                                                      min(args.warmup, 6))
-        extras["adjoint_96x96x192_3000"] = adjoint_cost(torch, T)
-        extras["dissimilarity_48x100x128x128"] = dissimilarity_cost(torch, T)
-        extras["absorbing_layer_reflection"] = absorber_reflection(torch, T)
-        extras["potential_interp_240x240x520"] = interpolation_cost(torch, T)
-        extras["paper_cu111_240x240x520"] = paper_cu111_throughput(torch, T)
-
         # end to end through the C ABI from pinned host buffers: potential in,
         # packet set-up, the steps, flux map and observables out, over one complete
         # run of the workload (its own length, 1000 steps, whatever --steps is)
@@ -667,6 +645,28 @@ def main():
                "set_potential_h2d_ms_per_run": [r["phases_ms"]["set_potential_h2d"] for r in runs],
                "statistic": f"median of {len(runs)} complete runs"}
         del V_host
+        # FP64 unfused step and the FP32 variants on the same grid (same potential)
+        variants = [(W.FP64, 1)] + [(p, t) for p in (W.FP32, W.FP32_KAHAN) for t in (1, 2)]
+        for vp, vt in variants:
+            steps_v = max(10, args.steps // (8 if vp == W.FP64 else 2))
+            sv = make_ctx(T, W.config5(vp), vp, vt, V_dev)
+            vname = sv.tuning()["name"][vt]
+            vms, vprof = timed_steps(torch, T, sv, steps_v, min(args.warmup, 6), barrier)
+            sv.close()
+            vlaunch = vprof["step_ms"] / max(1, vprof["step_launches"])
+            extras[f"{PREC_NAME[vp]}_t{vt}"] = {
+                "value": cells * steps_v / (vms * 1e-3), "unit": "cell-updates/s",
+                "steps": steps_v, "variant": vname, "avg_launch_ms": vlaunch,
+                "hbm_frac_of_algorithmic_bytes": BYTES_PER_NODE[vp] * cells / (vlaunch * 1e-3) / 1e9 / hbm_peak}
+        extras["speedup_vs_fp64_plain"] = value / world / extras["f64_t1"]["value"]
+        extras["batched_48_films"] = batch_throughput(torch, T, max(20, args.steps // 2),
+                                                      min(args.warmup, 6))
+        extras["adjoint_96x96x192_3000"] = adjoint_cost(torch, T)
+        extras["dissimilarity_48x100x128x128"] = dissimilarity_cost(torch, T)
+        extras["absorbing_layer_reflection"] = absorber_reflection(torch, T)
+        extras["potential_interp_240x240x520"] = interpolation_cost(torch, T)
+        extras["paper_cu111_240x240x520"] = paper_cu111_throughput(torch, T)
+
         if rank == 0 and world == 1:
             cpu = time_oracle(args.cpu_seconds)
 
