@@ -458,22 +458,23 @@ __device__ __forceinline__ void write_partials(double *partials, double *sh, dou
 }
 
 // Q, paper norm and energy numerator over (column group, z-chunk) items: each
-// thread marches a chunk of kObsZ planes of V adjacent (x, y) columns (one 16-byte
+// thread marches a chunk of zch planes of V adjacent (x, y) columns (one 16-byte
 // vector per field and plane) with a three-plane window and accumulates the chunk
 // in ColumnSum.  Items go to threads in a fixed order and the block count is fixed
 // by the grid shape, so the sums are reproducible.  V = 1 is the scalar form for
 // rows whose length is not a multiple of the vector width.
-template <typename Real, int V>
+template <typename Real, int V, int ZC>
 __global__ void __launch_bounds__(kObsThreads)
-    observables_kernel(MemberDev m, int buf, double *__restrict__ partials)
+    observables_kernel(MemberDev m, int buf, double *__restrict__ partials, int zch_arg)
 {
+    const int zch = ZC > 0 ? ZC : zch_arg;   // ZC > 0: the chunk is a compile-time constant
     __shared__ double sh[32];
     const Real *__restrict__ R = reinterpret_cast<const Real *>(m.R[buf]);
     const Real *__restrict__ I = reinterpret_cast<const Real *>(m.I[buf]);
     const Real *__restrict__ D = reinterpret_cast<const Real *>(m.d);
     const int ngx = m.nx / V;
     const long long ngrp = static_cast<long long>(ngx) * m.ny;
-    const int nch = (m.nz + kObsZ - 1) / kObsZ;
+    const int nch = (m.nz + zch - 1) / zch;
     const long long nitems = ngrp * nch;
     const Real cx = static_cast<Real>(m.cx), cy = static_cast<Real>(m.cy),
                cz = static_cast<Real>(m.cz);
@@ -496,8 +497,8 @@ __global__ void __launch_bounds__(kObsThreads)
     for (long long item = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
          item < nitems; item += static_cast<long long>(gridDim.x) * blockDim.x) {
         const long long grp = item % ngrp;
-        const int z0 = static_cast<int>(item / ngrp) * kObsZ;
-        const int z1 = min(z0 + kObsZ, m.nz);
+        const int z0 = static_cast<int>(item / ngrp) * zch;
+        const int z1 = min(z0 + zch, m.nz);
         const int x0 = static_cast<int>(grp % ngx) * V, y = static_cast<int>(grp / ngx);
         const long long base = static_cast<long long>(y + m.G) * pitch + (x0 + m.G);
         const long long last = base + static_cast<long long>(m.nz - 1) * plane;
@@ -820,15 +821,25 @@ cudaError_t launch_observables(const MemberDev &m, int precision, int buf, doubl
     const int vec = precision == 0 ? 2 : 4;          // one 16-byte vector per field and plane
     const bool vector = m.nx % vec == 0;
     const long long groups = static_cast<long long>(vector ? m.nx / vec : m.nx) * m.ny;
-    const long long nitems = groups * ((m.nz + kObsZ - 1) / kObsZ);
+    // z planes per work item: kObsZ on large grids; fewer (down to 4) where that
+    // would leave less than about one item per thread of kObsParts blocks, since a
+    // thread marches its planes one after the other (a 96 x 96 x 192 member: 4)
+    const long long want = (static_cast<long long>(kObsParts) * kObsThreads + groups - 1) / groups;
+    const int zch = static_cast<int>(
+        std::min<long long>(kObsZ, std::max<long long>(4, (m.nz + want - 1) / want)));
+    const long long nitems = groups * ((m.nz + zch - 1) / zch);
     const int nparts = static_cast<int>(
         std::max<long long>(1, std::min<long long>((nitems + kObsThreads - 1) / kObsThreads, kObsParts)));
+    auto run = [&](auto kernel_full, auto kernel_short) {
+        if (zch == kObsZ) kernel_full<<<nparts, kObsThreads, 0, s>>>(m, buf, partials, zch);
+        else kernel_short<<<nparts, kObsThreads, 0, s>>>(m, buf, partials, zch);
+    };
     if (precision == 0) {
-        if (vector) observables_kernel<double, 2><<<nparts, kObsThreads, 0, s>>>(m, buf, partials);
-        else observables_kernel<double, 1><<<nparts, kObsThreads, 0, s>>>(m, buf, partials);
+        if (vector) run(observables_kernel<double, 2, kObsZ>, observables_kernel<double, 2, 0>);
+        else run(observables_kernel<double, 1, kObsZ>, observables_kernel<double, 1, 0>);
     } else {
-        if (vector) observables_kernel<float, 4><<<nparts, kObsThreads, 0, s>>>(m, buf, partials);
-        else observables_kernel<float, 1><<<nparts, kObsThreads, 0, s>>>(m, buf, partials);
+        if (vector) run(observables_kernel<float, 4, kObsZ>, observables_kernel<float, 4, 0>);
+        else run(observables_kernel<float, 1, kObsZ>, observables_kernel<float, 1, 0>);
     }
     observables_finalize_kernel<<<1, kThreads, 0, s>>>(m, partials, nparts, record, status, q_ref,
                                                        step);

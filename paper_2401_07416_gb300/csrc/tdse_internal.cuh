@@ -120,7 +120,7 @@ cudaError_t launch_observables(const MemberDev &m, int precision, int buf, doubl
                                double *record, int *status, double q_ref, long long step,
                                cudaStream_t s);
 constexpr int kObsParts = 1216;     // fixed block count: the reduction order never changes
-constexpr int kObsZ = 64;           // planes per observables work item (column chunk)
+constexpr int kObsZ = 64;           // largest z-chunk of an observables work item
 constexpr int kObsThreads = 256;    // observables block size (8 blocks per SM fill an SM)
 constexpr int kObsPartialsPerBlock = 5;   // Q, paper norm, energy, flux (last step, integrated)
 
