@@ -13,6 +13,8 @@
   windows: a 40x40 column of the full grid around each sample, periodic images of
   the full grid's potential, walls at the window edges; after N steps and the
   half-step start only nodes more than 2N + 1 cells inside a window are exact.
+  Q, the paper norm and the energy of the whole grid are checked against the
+  oracle's reduction of the same state.
 """
 import math
 
@@ -183,6 +185,20 @@ def test_config5_light_cone_windows(T, precision):
         Rd = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
         Id = torch.empty_like(Rd)
         T.tdse_get_state(s.ctx, 0, Rd, Id)
+        obs = s.observables(0)
+        Vd = torch.empty_like(Rd)
+        T.tdse_get_potential(s.ctx, 0, Vd)
+    # Q, paper norm and energy of the whole grid (the reduction's 64-plane z-chunk
+    # form, used on grids this large) against the oracle's on the same state.  FP32
+    # contexts reduce their FP32 fields with FP32 stencils and d = -2 sum c - cv V
+    # stored in FP32: a 2^-24 relative error on |d| ~ 0.6 against |A R| ~ dt E |R|
+    # ~ 1e-3 |R| bounds the energy's bias near 3e-5, hence 1e-3 for E, 1e-5 for Q.
+    oo = oracle.observables(g, Vd.cpu().numpy(), Rd.cpu().numpy(), Id.cpu().numpy())
+    del Vd
+    tol_q, tol_e = (TOL64, TOL64) if prec == T.FP64 else (1e-5, 1e-3)
+    assert obs["Q"] == pytest.approx(oo["Q"], rel=tol_q)
+    assert obs["norm_paper"] == pytest.approx(oo["norm_paper"], rel=tol_q)
+    assert obs["energy"] == pytest.approx(oo["energy"], rel=tol_e)
     width, margin = 40, 2 * steps + 2
     for (x0, y0) in [(-20, -20), (200, 130), (492, 300), (100, 480)]:
         xs = np.arange(x0, x0 + width) % g.nx
