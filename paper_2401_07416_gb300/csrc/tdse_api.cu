@@ -578,8 +578,11 @@ tdse_status run_segment(tdse_ctx *c, long long nsteps)
         c->stream = user;
         c->cur = cur0;
         c->step = step0;
-        TRY(st);
-        if (e != cudaSuccess) return fail(c, TDSE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        if (st != TDSE_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (st != TDSE_OK) return st;
+            return fail(c, TDSE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        }
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return fail(c, TDSE_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
