@@ -311,6 +311,28 @@ def test_flux_equals_probability_crossing_the_face():
     assert phi == pytest.approx(dq, rel=2e-3)
 
 
+def test_plane_wave_is_exact_and_its_flux_has_a_closed_form():
+    """With V = 0 on a periodic z axis, the mode e^{ikz} is an eigenvector of A with
+    eigenvalue -lam, lam = 4 c_z sin^2(kh/2), and Eqs. 8-9 are solved exactly by the
+    unit plane wave R^n = cos(kz - n phi), I^{n+1/2} = sin(kz - (n+1/2) phi) with
+    2 sin(phi/2) = lam (substituting gives that condition and unit amplitudes for
+    both parts).  The face flux j = hbar/(m h)(R_k I_k+1 - R_k+1 I_k) of that
+    solution is hbar sin(kh) cos(phi/2) / (m h) at every pixel and step."""
+    h, dt, nz, mode, N = 0.2, 0.004, 32, 3, 37
+    g = W.small_grid(4, 4, nz, h=(0.3, 0.25, h), dt=dt, bc=(0, 0, 0), det_k=10)
+    k = 2.0 * math.pi * mode / (nz * h)
+    lam = 4.0 * (g.hbar * dt / (2.0 * g.mass * h * h)) * math.sin(0.5 * k * h) ** 2
+    phi = 2.0 * math.asin(0.5 * lam)
+    kz = np.broadcast_to((k * h * np.arange(nz))[:, None, None], (nz, g.ny, g.nx))
+    R, I, F, jl = oracle.run(g, None, np.cos(kz), np.sin(kz + 0.5 * phi), N,
+                             use_mask=False, flux=True)
+    assert np.abs(R - np.cos(kz - N * phi)).max() < 1e-12
+    assert np.abs(I - np.sin(kz - (N - 0.5) * phi)).max() < 1e-12
+    j = g.hbar * math.sin(k * h) * math.cos(0.5 * phi) / (g.mass * h)
+    assert np.abs(jl - j).max() < 1e-12 * j
+    assert np.abs(F - N * dt * j).max() < 1e-12 * N * dt * j
+
+
 # --------------------------------------------------------------------------- potential
 
 def test_single_atom_potential_closed_form():
