@@ -315,8 +315,9 @@ TDSE_API const char *tdse_last_error(const tdse_ctx *ctx);
  * calls on the same device share the array: calls that overlap on the GPU
  * (other streams, other host threads) race.  Work runs on `stream` (a
  * cudaStream_t; NULL: legacy default stream), which is synchronised before the
- * host results are written to out.  EINVAL: NULL pointer, bad spacing, or nz
- * above 8192 (one scratch slot per z plane); ECUDA: a CUDA call failed. */
+ * host results are written to out.  EINVAL: NULL pointer, bad spacing, nz
+ * above 8192 (one scratch slot per z plane), or an xy plane above 2^30 nodes;
+ * ECUDA: a CUDA call failed. */
 TDSE_API tdse_status tdse_observables_static(const tdse_params *p, const double *R,
                                              const double *I, const double *V, double out[3],
                                              void *stream);

@@ -143,6 +143,7 @@ extern "C" tdse_status tdse_observables_static(const tdse_params *p, const doubl
 {
     if (!p || !R || !I || !out) return TDSE_EINVAL;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nz > kMaxPlanes) return TDSE_EINVAL;
+    if (static_cast<long long>(p->nx) * p->ny > (1LL << 30)) return TDSE_EINVAL;   // 32-bit plane index
     if (!(p->hx > 0 && p->hy > 0 && p->hz > 0)) return TDSE_EINVAL;
     const double hbar = p->hbar > 0 ? p->hbar : 1.0;
     const double mass = p->mass > 0 ? p->mass : 1.0;

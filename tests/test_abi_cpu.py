@@ -144,5 +144,20 @@ def test_new_entry_points_validate_before_device_work(lib):
         assert e.value.status == T.EINVAL
 
 
+def test_static_observables_validate_before_device_work(lib):
+    """tdse_observables_static rejects a bad geometry with EINVAL before any CUDA
+    call: the dummy host pointers below are never dereferenced."""
+    import numpy as np
+    buf = np.zeros(4)
+    out = np.zeros(3)
+    ptr = buf.ctypes.data_as(ctypes.c_void_p)
+    optr = out.ctypes.data_as(ctypes.c_void_p)
+    for field, value in (("nz", 8193), ("ny", 1 << 27), ("hz", 0.0)):
+        p = _params(**{field: value})
+        assert T.lib().tdse_observables_static(ctypes.byref(p), ptr, ptr, None, optr, None) == T.EINVAL
+    p = _params()
+    assert T.lib().tdse_observables_static(ctypes.byref(p), None, ptr, None, optr, None) == T.EINVAL
+
+
 def test_version_string(lib):
     assert "sm_103a" in T.tdse_version()
