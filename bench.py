@@ -287,10 +287,26 @@ def make_ctx(T, wl, precision, tblock, V_dev=None, autotune=True):
     return s
 
 
+def align_to_depth(T, s):
+    """Untimed single steps until the step counter is a multiple of the fused depth in
+    use: every step sequence between two reductions (the reduction period is a
+    multiple of the depth) then consists of launches of that depth only, whatever
+    warm-up count came before."""
+    tb = s.tuning()["tblock"]
+    extra = (-int(T.tdse_observables(s.ctx, 0)["step"])) % tb
+    if extra:
+        s.step(extra)
+    return extra
+
+
 def timed_steps(torch, T, s, steps, warmup, barrier):
-    """W untimed steps, then K steps between CUDA events on the library's stream with
-    per-launch event timing of the fused kernel enabled (events only, no host sync)."""
+    """W untimed steps (plus up to T-1 to align the step counter to the fused depth
+    T), then K steps between CUDA events on the library's stream.  The steps are
+    replayed from their CUDA graphs; the library's profiling records events around
+    each replay (one depth per replay), which gives the device time per launch of
+    every depth without host synchronisation inside the timed region."""
     s.step(warmup)
+    align_to_depth(T, s)
     torch.cuda.synchronize()
     barrier()
     T.tdse_set_profiling(s.ctx, True)
@@ -307,6 +323,12 @@ def timed_steps(torch, T, s, steps, warmup, barrier):
     prof = T.tdse_get_profile(s.ctx)
     T.tdse_set_profiling(s.ctx, False)
     return ms, prof
+
+
+def launch_stats(prof, depth):
+    """(launches, mean device ms per launch) of the fused step at the given depth."""
+    n = prof["launches_at_depth"].get(depth, 0)
+    return n, (prof["ms_at_depth"][depth] / n if n else float("nan"))
 
 
 def ncu_case(args):
@@ -348,6 +370,8 @@ def batch_throughput(torch, T, steps, warmup):
         ms, prof = timed_steps(torch, T, s, steps, warmup, lambda: None)
         tun = s.tuning()
     cells = sum(m.grid.cells for m in members)
+    tb = tun["tblock"]
+    nl, lms = launch_stats(prof, tb)
     # the same members one at a time, each in its own autotuned context: the batch's
     # gain over running them back to back
     solo_steps = max(10, steps // 2 // 2 * 2)
@@ -361,7 +385,9 @@ def batch_throughput(torch, T, steps, warmup):
         solo_ms += ms1 * steps / solo_steps
     return {"value": cells * steps / (ms * 1e-3), "unit": "cell-updates/s", "members": 48,
             "cells": cells, "steps": steps, "precision": "f32+kahan", "tuning": tun,
-            "graphs": "profiling pass (direct launches)",
+            "graphs": True, "steps_per_launch": tb, "launches": nl, "avg_launch_ms": lms,
+            "hbm_frac_of_algorithmic_bytes": BYTES_PER_NODE[W.FP32_KAHAN] * cells / (lms * 1e-3) / 1e9
+                                             / measured_peaks()[0],
             "solo_sum_value": cells * steps / (solo_ms * 1e-3),
             "batch_over_solo": solo_ms / ms,
             "solo": f"each member alone, {solo_steps} steps, autotuned, same timing method"}
@@ -409,8 +435,7 @@ def paper_cu111_throughput(torch, T, steps=400, warmup=8):
     s.close()
     return {"nodes": g.cells, "steps": steps, "value": g.cells * steps / (ms * 1e-3),
             "unit": "cell-updates/s", "ns_per_node_step": ms * 1e6 / (g.cells * steps),
-            "variant": tun["name"][prof["steps_per_launch"]],
-            "steps_per_launch": prof["steps_per_launch"]}
+            "variant": tun["name"][tun["tblock"]], "steps_per_launch": tun["tblock"]}
 
 
 def interpolation_cost(torch, T):
@@ -573,8 +598,10 @@ def main():
 
     t_max, value = job_time_and_value(ms, cells, args.steps, world, reduce_max)
 
-    tb = prof["steps_per_launch"]
-    launch_ms = prof["step_ms"] / max(1, prof["step_launches"])
+    # the dominant kernel: the fused step at the depth in use (launches of other
+    # depths, if K is not a multiple of it, are left out of its roofline)
+    tb = tuning["tblock"]
+    nlaunch, launch_ms = launch_stats(prof, tb)
     bytes_launch = BYTES_PER_NODE[prec] * cells
     achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
     variant = tuning["name"][tb]
@@ -586,7 +613,10 @@ def main():
                           f"{variant} ({tb} steps per launch)",
                 "algorithmic_bytes_per_launch": bytes_launch,
                 "bytes_per_node_per_launch": BYTES_PER_NODE[prec],
-                "avg_launch_ms": launch_ms, "launches": prof["step_launches"],
+                "avg_launch_ms": launch_ms, "launches": nlaunch,
+                "launches_other_depths": int(prof["step_launches"] - nlaunch),
+                "timing": "CUDA events on the library's stream around each CUDA-graph replay "
+                          "(one reduction period of launches of one depth) inside the timed region",
                 "reduce_ms_total": prof["reduce_ms"],
                 "effective_frac_vs_unfused_fp32": value / world * 20 / 1e9 / hbm_peak}
 
@@ -653,7 +683,7 @@ def main():
             vname = sv.tuning()["name"][vt]
             vms, vprof = timed_steps(torch, T, sv, steps_v, min(args.warmup, 6), barrier)
             sv.close()
-            vlaunch = vprof["step_ms"] / max(1, vprof["step_launches"])
+            _, vlaunch = launch_stats(vprof, vt)
             extras[f"{PREC_NAME[vp]}_t{vt}"] = {
                 "value": cells * steps_v / (vms * 1e-3), "unit": "cell-updates/s",
                 "steps": steps_v, "variant": vname, "avg_launch_ms": vlaunch,

@@ -22,7 +22,10 @@
  *   - Arrays are [nz][ny][nx] with x fastest, unpadded, FP64, unless stated.
  *   - Every call returns a tdse_status; nothing throws across the ABI.  On an
  *     error, tdse_last_error() describes it; the context stays usable unless
- *     the status is TDSE_ECUDA or TDSE_EUNSTABLE.
+ *     the status is TDSE_ECUDA, TDSE_EUNSTABLE or TDSE_ETIMEOUT.  After the last
+ *     two its state is not a result of the scheme: tdse_step, tdse_adjoint,
+ *     tdse_autotune and tdse_save_state then return TDSE_ESTATE, while the
+ *     calls that read the state still work (for inspection).
  *   - The context owns all device memory it allocates (through the allocator
  *     callbacks, cudaMalloc/cudaFree by default) and frees it in tdse_destroy.
  *     Caller pointers are borrowed for the duration of the call only.
@@ -181,7 +184,13 @@ TDSE_API tdse_status tdse_set_state(tdse_ctx *ctx, int member, const double *R, 
 /* Advance every member by nsteps leapfrog steps (Eqs. 8-9 + absorbing layer),
  * accumulating the detector flux, reducing Q and E every obs_every steps and
  * recording checkpoints every ckpt_every steps.  Returns EUNSTABLE if a
- * reduction saw non-finite values or Q above (1 + 1e-3) times its first value. */
+ * reduction saw non-finite values or Q above (1 + 1e-3) times its first value,
+ * and ETIMEOUT if a step kernel's bounded wait for a tile's data expired (see
+ * tdse_set_wait_limit).  Each observation point copies the kernels' status word
+ * to the host without stalling the GPU; the host reads these copies as they
+ * complete, so a failure ends the call at most two observation intervals after
+ * the observation point that recorded it (the message names that step), with
+ * the issued work finished and the step counter at the last step run. */
 TDSE_API tdse_status tdse_step(tdse_ctx *ctx, long long nsteps);
 
 /* Observables of member m at the current step (computed now, FP64). */
@@ -258,43 +267,63 @@ TDSE_API tdse_status tdse_adjoint(tdse_ctx *ctx, int member, const double *dL_dF
 TDSE_API tdse_status tdse_save_state(tdse_ctx *ctx, const char *path);
 TDSE_API tdse_status tdse_load_state(tdse_ctx *ctx, const char *path);
 
-/* Kernel timing, for benchmarks.  While enabled, every fused-step launch is
- * bracketed by CUDA events (no CUDA graphs); tdse_get_profile returns the
- * launches and total device milliseconds of the step kernels and of the
- * reduction kernels since the last reset, and the cells and time steps per
- * step launch (all members). */
+/* Largest number of time steps fused into one kernel launch (temporal blocking). */
+#define TDSE_MAX_TBLOCK 4
+
+/* Kernel timing, for benchmarks.  While enabled, the fused-step launches are
+ * timed with CUDA events on the context's stream: a step sequence between two
+ * reductions whose launches all fuse the same number of steps is replayed from
+ * its CUDA graph (when graphs are on) and timed as a whole, its time divided
+ * evenly over its launches; any other sequence is issued as direct launches,
+ * each bracketed by its own events.  tdse_get_profile returns, since the last
+ * reset, the launches and device milliseconds of the step kernels (in total and
+ * per fused depth T) and of the reduction kernels, and the grid nodes per step
+ * launch (all members). */
 typedef struct tdse_profile {
-    long long step_launches;
-    double step_ms;
+    long long step_launches;        /* fused-step launches, every depth */
+    double step_ms;                 /* their device time */
     long long reduce_launches;
     double reduce_ms;
     long long cells_per_launch;     /* grid nodes updated by one step launch */
-    int steps_per_launch;           /* temporal depth of the last step launch */
+    int steps_per_launch;           /* fused depth of the last step launch */
     int reserved;
+    long long launches_at_depth[TDSE_MAX_TBLOCK + 1];   /* [T]: launches fusing T steps */
+    double ms_at_depth[TDSE_MAX_TBLOCK + 1];            /* [T]: their device time */
 } tdse_profile;
 TDSE_API tdse_status tdse_set_profiling(tdse_ctx *ctx, int enable);
 TDSE_API tdse_status tdse_get_profile(tdse_ctx *ctx, tdse_profile *out);
 
 /* Kernel variants and fused depth.  The fused step exists in several variants
  * (tile shape, planes loaded ahead, CTAs per SM) for each precision and number
- * of steps per launch (1 or 2; FP64 fuses 1).  tdse_autotune times every variant
- * on this context's own grids (`launches` launches each, after one warm-up),
- * keeps the fastest for each depth and, if the context was created with
- * tblock = 0, the depth with the lower time per step.  The state, flux integral
- * and step counter are saved before and restored after the trials.  Step
- * sequences between two reductions are replayed from captured CUDA graphs
- * unless profiling is on or tdse_set_graphs(ctx, 0) was called. */
+ * of steps per launch T (tdse_variant_count(precision, T) of them; a depth
+ * without variants is not available for that precision).  tdse_autotune times
+ * every variant on this context's own grids (`launches` launches each, after one
+ * warm-up), keeps the fastest for each depth and, if the context was created
+ * with tblock = 0, the depth with the lowest time per step.  The state, flux
+ * integral and step counter are saved before and restored after the trials.
+ * Step sequences between two reductions are replayed from captured CUDA graphs
+ * unless tdse_set_graphs(ctx, 0) was called (with profiling on, only sequences
+ * whose launches all have one depth are replayed). */
 typedef struct tdse_tuning {
-    int tblock;                 /* steps fused per launch in use */
-    int variant[3];             /* variant index for 1 and 2 fused steps (index 0 unused) */
-    double ms_per_step[3];      /* measured by tdse_autotune, 0 if not measured */
-    char name[3][48];           /* variant names */
+    int tblock;                                 /* steps fused per launch in use */
+    int variant[TDSE_MAX_TBLOCK + 1];           /* [T]: variant index for T fused steps ([0] unused) */
+    double ms_per_step[TDSE_MAX_TBLOCK + 1];    /* [T]: measured by tdse_autotune, 0 if not measured */
+    char name[TDSE_MAX_TBLOCK + 1][48];         /* [T]: variant names ("" without variants) */
 } tdse_tuning;
 TDSE_API int tdse_variant_count(int precision, int tsteps);
 TDSE_API tdse_status tdse_set_variant(tdse_ctx *ctx, int tsteps, int variant);
 TDSE_API tdse_status tdse_autotune(tdse_ctx *ctx, int launches);
 TDSE_API tdse_status tdse_get_tuning(tdse_ctx *ctx, tdse_tuning *out);
 TDSE_API tdse_status tdse_set_graphs(tdse_ctx *ctx, int enable);
+
+/* Limit, in nanoseconds, of each wait of a step kernel for a tile's data to land
+ * in shared memory (default 2e9 = 2 s; no correct launch comes near it).  When a
+ * wait expires, the CTA sets the status word, waits (bounded, 2 s) for its own
+ * loads still in flight, releases its tensor memory and leaves; tdse_step
+ * returns ETIMEOUT and the context is failed.  ns = 0 makes every wait test its
+ * data once without waiting, so any wait whose data is still in flight expires:
+ * a way to exercise that path with every load valid.  EINVAL: ns < 0. */
+TDSE_API tdse_status tdse_set_wait_limit(tdse_ctx *ctx, long long ns);
 
 /* Description of the last error on this context (static storage, never NULL). */
 TDSE_API const char *tdse_last_error(const tdse_ctx *ctx);
@@ -313,11 +342,15 @@ TDSE_API const char *tdse_last_error(const tdse_ctx *ctx);
  * before any stream capture.  Each call overwrites the nz per-plane sums it
  * reads and the result slot, so nothing has to be cleared between calls, but
  * calls on the same device share the array: calls that overlap on the GPU
- * (other streams, other host threads) race.  Work runs on `stream` (a
- * cudaStream_t; NULL: legacy default stream), which is synchronised before the
- * host results are written to out.  EINVAL: NULL pointer, bad spacing, nz
- * above 8192 (one scratch slot per z plane), or an xy plane above 2^30 nodes;
- * ECUDA: a CUDA call failed. */
+ * (other streams, other host threads) race.  The call is synchronous: its two
+ * kernels run on `stream` (a cudaStream_t; NULL: legacy default stream), the
+ * results are copied into the caller's host array out, and the stream is
+ * synchronised before the call returns.  R, I and V must each hold nx ny nz
+ * doubles on the current device (not checked here: a shorter array is read out
+ * of bounds).  EINVAL: NULL pointer, bad spacing, a boundary flag other than
+ * TDSE_BC_PERIODIC / TDSE_BC_DIRICHLET, nz above 8192 (one scratch slot per z
+ * plane), or an xy plane above 2^30 nodes; ECUDA: a CUDA call failed (its own
+ * launches or copies; an error left by earlier, unrelated work is not reported). */
 TDSE_API tdse_status tdse_observables_static(const tdse_params *p, const double *R,
                                              const double *I, const double *V, double out[3],
                                              void *stream);

@@ -2,8 +2,9 @@
 
 The translation units under ``csrc/`` are compiled in parallel, each with
 ``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo``, and linked into
-``paper_2401_07416_gb300/libtdse.so``.  No CMake: a rebuild happens only when a
-source or header is newer than the library.
+``paper_2401_07416_gb300/libtdse.so``.  No CMake: a rebuild happens when a
+source or header is newer than the library, or when the compiler flags differ
+from those the library was built with (recorded beside the objects).
 """
 from __future__ import annotations
 
@@ -35,8 +36,22 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def _flags_record() -> str:
+    """The flags the library is compiled and linked with, one per line."""
+    return "\n".join(ARCH + FLAGS + ["-lcudart"]) + "\n"
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    try:
+        with open(STAMP) as f:
+            if f.read() != _flags_record():
+                return True
+    except OSError:
         return True
     t = os.path.getmtime(LIB)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "tdse.h")]
@@ -67,6 +82,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(_flags_record())
     return LIB
 
 

@@ -145,6 +145,8 @@ extern "C" tdse_status tdse_observables_static(const tdse_params *p, const doubl
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nz > kMaxPlanes) return TDSE_EINVAL;
     if (static_cast<long long>(p->nx) * p->ny > (1LL << 30)) return TDSE_EINVAL;   // 32-bit plane index
     if (!(p->hx > 0 && p->hy > 0 && p->hz > 0)) return TDSE_EINVAL;
+    for (int a = 0; a < 3; ++a)   // the same boundary flags tdse_create accepts
+        if (p->bc[a] != TDSE_BC_PERIODIC && p->bc[a] != TDSE_BC_DIRICHLET) return TDSE_EINVAL;
     const double hbar = p->hbar > 0 ? p->hbar : 1.0;
     const double mass = p->mass > 0 ? p->mass : 1.0;
     double dt = p->dt;
@@ -168,9 +170,16 @@ extern "C" tdse_status tdse_observables_static(const tdse_params *p, const doubl
     double *scratch = nullptr;
     if (scratch_address(&scratch) != cudaSuccess) return TDSE_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    plane_sums_kernel<<<g.nz, kThreads, 0, s>>>(R, I, V, g, scratch);
-    finalize_kernel<<<1, kThreads, 0, s>>>(g, scratch);
-    if (cudaGetLastError() != cudaSuccess) return TDSE_ECUDA;
+    // launched through cudaLaunchKernel, whose status is this launch's own (an
+    // error left by unrelated earlier work is neither reported nor cleared here)
+    void *sum_args[] = {&R, &I, &V, &g, &scratch};
+    if (cudaLaunchKernel(reinterpret_cast<const void *>(&plane_sums_kernel), dim3(g.nz), dim3(kThreads),
+                         sum_args, 0, s) != cudaSuccess)
+        return TDSE_ECUDA;
+    void *fin_args[] = {&g, &scratch};
+    if (cudaLaunchKernel(reinterpret_cast<const void *>(&finalize_kernel), dim3(1), dim3(kThreads),
+                         fin_args, 0, s) != cudaSuccess)
+        return TDSE_ECUDA;
     if (cudaMemcpyAsync(out, scratch + 4 * kMaxPlanes, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                         s) != cudaSuccess)
         return TDSE_ECUDA;

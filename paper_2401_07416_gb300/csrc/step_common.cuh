@@ -12,7 +12,7 @@ namespace tdse {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per barrier wait
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s: drain of loads in flight
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -52,13 +52,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return done != 0;
 }
 
-// Bounded wait: false if the phase did not complete within kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Non-blocking test of the phase.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity)
 {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait: false if the phase did not complete within limit_ns.  A limit of
+// 0 tests the phase once without waiting, so that a wait for a load still in
+// flight expires (the host's way of exercising the expiry path with valid loads).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs)
+{
+    if (limit_ns == 0) return mbar_test_wait(bar, parity);
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
     return true;
 }

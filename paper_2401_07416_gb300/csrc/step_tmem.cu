@@ -111,7 +111,8 @@ struct TmemShape {
 template <class C>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fused_step_tmem_kernel(const MemberDev *__restrict__ members, const WorkDev *__restrict__ work,
-                           int *counter, int *status, int in_buf)
+                           int *counter, int *status, int in_buf,
+                           unsigned long long wait_ns)
 {
     typedef float Real;
     typedef TmemShape<C> TS;
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         for (int it = 0; it < nit; ++it) {
             const int p = L0 + it;
             if (tid == 0) {
-                if (mbar_wait_bounded(&bars[headB], phase)) {
+                if (mbar_wait_bounded(&bars[headB], phase, wait_ns)) {
                     waited = it + 1;
                 } else {
                     atomicOr(status, 1);
@@ -517,7 +518,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             if (tid == 0) {
                 for (int l = waited; l < issued; ++l) {
                     const long long g = gbase + l;
-                    mbar_wait_bounded(&bars[g % NB], static_cast<uint32_t>((g / NB) & 1));
+                    if (!mbar_wait_bounded(&bars[g % NB], static_cast<uint32_t>((g / NB) & 1)))
+                        atomicOr(status, 4);   // the CTA leaves with a load still in flight
                 }
             }
             __syncthreads();
@@ -541,7 +543,7 @@ cudaError_t launch_tmem_cfg(const StepLaunch &L)
     cudaError_t e = allow_dynamic_smem(fused_step_tmem_kernel<C>, C::SMEM, smem_allowed);
     if (e != cudaSuccess) return e;
     fused_step_tmem_kernel<C><<<L.grid, C::NT, C::SMEM, L.stream>>>(L.members, L.work, L.counter,
-                                                                    L.status, L.in_buf);
+                                                                    L.status, L.in_buf, L.wait_ns);
     return cudaGetLastError();
 }
 

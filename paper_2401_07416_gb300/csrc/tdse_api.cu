@@ -20,6 +20,8 @@ namespace {
 
 constexpr int kRecCap = 256;        // observation records buffered on the device per member
 constexpr int kRecLen = 6;
+constexpr int kStatusLag = 2;       // observation points whose status copies may be outstanding
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;   // 2 s per wait for a tile's data
 
 struct Member {
     tdse_params p;                  // resolved parameters
@@ -64,6 +66,14 @@ struct tdse_ctx {
     StepPlan plans[kMaxTblock + 1];
     int *d_counter = nullptr;
     int *d_status = nullptr;
+    // Status word copies taken at observation points (pinned host slots, one event
+    // each), read by the host without stalling the stream.
+    int *h_status = nullptr;
+    cudaEvent_t status_ev[kStatusLag] = {};
+    long long status_step[kStatusLag] = {};
+    int status_head = 0, status_pending = 0;
+    bool failed = false;                           // a step kernel timed out or the run diverged
+    unsigned long long wait_ns = kDefaultWaitNs;   // limit of each wait for a tile's data
     double *d_partials = nullptr;
     double *d_records = nullptr;    // [B][kRecCap][kRecLen]
     int cur = 0;                    // ping-pong buffer holding the state
@@ -72,8 +82,12 @@ struct tdse_ctx {
     bool profiling = false;
     tdse_profile prof{};
     std::vector<cudaEvent_t> event_pool;           // reused timing events
-    std::vector<std::pair<int, int>> pending;      // (start, stop) indices into event_pool
-    std::vector<int> pending_kind;                 // 0: step launch, 1: reductions
+    struct Interval {
+        int start, stop;                           // indices into event_pool
+        int kind;                                  // 0: step launches, 1: reductions
+        int launches, depth;                       // step launches timed together, their depth
+    };
+    std::vector<Interval> pending;
     size_t events_used = 0;
     bool graphs = true;                            // replay step segments as CUDA graphs
     cudaStream_t gstream = nullptr;                // capture/replay stream
@@ -83,7 +97,7 @@ struct tdse_ctx {
         cudaGraphExec_t exec;
     };
     std::vector<GraphEntry> graph_cache;
-    double tuned_ms_per_step[kMaxTblock + 1] = {0, 0, 0};
+    double tuned_ms_per_step[kMaxTblock + 1] = {};
     std::string err;
 };
 
@@ -314,10 +328,11 @@ tdse_status build_plan(tdse_ctx *c, int T, int variant)
     return TDSE_OK;
 }
 
+// Plans of every fused depth that has kernel variants for the context's precision.
 tdse_status build_plans(tdse_ctx *c)
 {
-    TRY(build_plan(c, 1, 0));
-    if (c->precision != TDSE_FP64) TRY(build_plan(c, 2, 0));
+    for (int T = 1; T <= kMaxTblock; ++T)
+        if (step_variant_count(c->precision, T) > 0) TRY(build_plan(c, T, 0));
     return TDSE_OK;
 }
 
@@ -384,6 +399,10 @@ tdse_status ensure_device(tdse_ctx *c)
     void *p;
     TRY(dalloc(c, sizeof(int), &p)); c->d_counter = static_cast<int *>(p);
     TRY(dalloc(c, sizeof(int), &p)); c->d_status = static_cast<int *>(p);
+    CUDA_TRY(c, cudaHostAlloc(reinterpret_cast<void **>(&c->h_status), kStatusLag * sizeof(int),
+                              cudaHostAllocDefault));
+    for (int k = 0; k < kStatusLag; ++k)
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->status_ev[k], cudaEventDisableTiming));
     TRY(dalloc(c, kObsParts * kObsPartialsPerBlock * sizeof(double), &p));
     c->d_partials = static_cast<double *>(p);
     TRY(dalloc(c, c->m.size() * kRecCap * kRecLen * sizeof(double), &p));
@@ -431,13 +450,67 @@ tdse_status drain_records(tdse_ctx *c, int nrec)
     return TDSE_OK;
 }
 
+// Status word -> status code.  A set word leaves the context failed: the state
+// is not a result of the scheme any more.
+tdse_status status_error(tdse_ctx *c, int st, long long step)
+{
+    if (st == 0) return TDSE_OK;
+    c->failed = true;
+    if (st & 5)
+        return fail(c, TDSE_ETIMEOUT, "a bounded wait for a tile's data in the step kernel expired "
+                    "(seen by step %lld)%s", step,
+                    (st & 4) ? "; a load was still in flight when its CTA left" : "");
+    return fail(c, TDSE_EUNSTABLE, "non-finite values or growth of Q detected (seen at the "
+                "observation of step %lld)", step);
+}
+
 tdse_status check_status(tdse_ctx *c)
 {
     int st = 0;
     CUDA_TRY(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    if (st & 1) return fail(c, TDSE_ETIMEOUT, "a bounded wait in the step kernel expired");
-    if (st & 2) return fail(c, TDSE_EUNSTABLE, "non-finite values or growth of Q detected");
+    c->status_pending = 0;   // every outstanding copy is older than this read
+    return status_error(c, st, c->step);
+}
+
+// Look at the status copies of earlier observation points whose events have
+// completed (oldest first); with `wait_oldest`, wait for the oldest one.
+tdse_status poll_status(tdse_ctx *c, bool wait_oldest)
+{
+    while (c->status_pending > 0) {
+        const int k = (c->status_head - c->status_pending + kStatusLag) % kStatusLag;
+        const cudaError_t q = wait_oldest ? cudaEventSynchronize(c->status_ev[k])
+                                          : cudaEventQuery(c->status_ev[k]);
+        if (q == cudaErrorNotReady) return TDSE_OK;
+        if (q != cudaSuccess) return fail(c, TDSE_ECUDA, "status event: %s", cudaGetErrorString(q));
+        wait_oldest = false;
+        --c->status_pending;
+        TRY(status_error(c, c->h_status[k], c->status_step[k]));
+    }
+    return TDSE_OK;
+}
+
+// Copy the status word at this observation point into the next pinned slot; at
+// most kStatusLag copies stay outstanding, so the host learns of a failure at
+// most kStatusLag observation intervals after the point that recorded it.
+tdse_status post_status(tdse_ctx *c)
+{
+    if (c->status_pending == kStatusLag) TRY(poll_status(c, true));
+    const int k = c->status_head;
+    CUDA_TRY(c, cudaMemcpyAsync(&c->h_status[k], c->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaEventRecord(c->status_ev[k], c->stream));
+    c->status_step[k] = c->step;
+    c->status_head = (k + 1) % kStatusLag;
+    ++c->status_pending;
+    return TDSE_OK;
+}
+
+tdse_status check_usable(tdse_ctx *c)
+{
+    if (c->failed)
+        return fail(c, TDSE_ESTATE, "the context failed earlier (a step kernel timed out or the run "
+                    "diverged); its state is not a result of the scheme: destroy it");
     return TDSE_OK;
 }
 
@@ -462,39 +535,53 @@ tdse_status timer_start(tdse_ctx *c, int *start)
     return TDSE_OK;
 }
 
-tdse_status timer_stop(tdse_ctx *c, int start, int kind)
+// Close the interval: `launches` step launches of `depth` fused steps (kind 0),
+// or one round of reductions (kind 1).
+tdse_status timer_stop(tdse_ctx *c, int start, int kind, int launches = 1, int depth = 0)
 {
     if (start < 0) return TDSE_OK;
     int stop;
     TRY(next_event(c, &stop));
     CUDA_TRY(c, cudaEventRecord(c->event_pool[stop], c->stream));
-    c->pending.push_back({start, stop});
-    c->pending_kind.push_back(kind);
+    c->pending.push_back({start, stop, kind, launches, depth});
     return TDSE_OK;
 }
 
 // Accumulate the recorded intervals (call after the stream has been synchronised).
 tdse_status resolve_timers(tdse_ctx *c)
 {
-    for (size_t i = 0; i < c->pending.size(); ++i) {
+    for (const tdse_ctx::Interval &iv : c->pending) {
         float ms = 0.f;
-        CUDA_TRY(c, cudaEventElapsedTime(&ms, c->event_pool[c->pending[i].first],
-                                         c->event_pool[c->pending[i].second]));
-        if (c->pending_kind[i] == 0) {
-            c->prof.step_launches += 1;
+        CUDA_TRY(c, cudaEventElapsedTime(&ms, c->event_pool[iv.start], c->event_pool[iv.stop]));
+        if (iv.kind == 0) {
+            c->prof.step_launches += iv.launches;
             c->prof.step_ms += ms;
+            if (iv.depth >= 1 && iv.depth <= TDSE_MAX_TBLOCK) {
+                c->prof.launches_at_depth[iv.depth] += iv.launches;
+                c->prof.ms_at_depth[iv.depth] += ms;
+            }
         } else {
             c->prof.reduce_launches += 2 * static_cast<long long>(c->m.size());
             c->prof.reduce_ms += ms;
         }
     }
     c->pending.clear();
-    c->pending_kind.clear();
     c->events_used = 0;
     return TDSE_OK;
 }
 
-tdse_status launch_fused(tdse_ctx *c, int T)
+// Profile bookkeeping of one step launch of depth T (nodes per launch, last depth).
+void note_launch(tdse_ctx *c, int T)
+{
+    if (!c->profiling) return;
+    long long cells = 0;
+    for (const Member &mb : c->m) cells += static_cast<long long>(mb.dev.nx) * mb.dev.ny * mb.dev.nz;
+    c->prof.cells_per_launch = cells;
+    c->prof.steps_per_launch = T;
+}
+
+// One fused launch of T steps; with profiling on and `timed`, bracketed by events.
+tdse_status launch_fused(tdse_ctx *c, int T, bool timed = true)
 {
     StepPlan &pl = c->plans[T];
     StepLaunch L;
@@ -503,32 +590,33 @@ tdse_status launch_fused(tdse_ctx *c, int T)
     L.counter = c->d_counter;
     L.status = c->d_status;
     L.in_buf = c->cur;
+    L.wait_ns = c->wait_ns;
     L.grid = pl.grid;
     L.block = pl.cfg.threads;
     L.smem = pl.cfg.smem;
     L.stream = c->stream;
     CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream));
-    int t0;
-    TRY(timer_start(c, &t0));
+    int t0 = -1;
+    if (timed) TRY(timer_start(c, &t0));
     CUDA_TRY(c, launch_step(c->precision, T, pl.variant, L));
-    TRY(timer_stop(c, t0, 0));
-    if (c->profiling) {
-        long long cells = 0;
-        for (const Member &mb : c->m) cells += static_cast<long long>(mb.dev.nx) * mb.dev.ny * mb.dev.nz;
-        c->prof.cells_per_launch = cells;
-        c->prof.steps_per_launch = T;
-    }
+    TRY(timer_stop(c, t0, 0, 1, T));
+    note_launch(c, T);
     c->cur ^= 1;
     c->step += T;
     return TDSE_OK;
 }
 
-// Issue the fused launches of `nsteps` steps (no observation in between).
-tdse_status issue_segment(tdse_ctx *c, long long nsteps)
+// Depth of the launches of an n-step segment: T = tblock while at least T steps
+// remain, then single steps.
+int segment_depth(const tdse_ctx *c, long long left) { return left >= c->tblock ? c->tblock : 1; }
+
+// Issue the fused launches of `nsteps` steps (no observation in between); with
+// profiling on, each launch is timed by its own events.
+tdse_status issue_segment(tdse_ctx *c, long long nsteps, bool timed = true)
 {
     while (nsteps > 0) {
-        const int T = (nsteps >= c->tblock) ? c->tblock : 1;
-        TRY(launch_fused(c, T));
+        const int T = segment_depth(c, nsteps);
+        TRY(launch_fused(c, T, timed));
         nsteps -= T;
     }
     return TDSE_OK;
@@ -561,7 +649,10 @@ tdse_status replay_graph(tdse_ctx *c, cudaGraphExec_t exec)
 
 tdse_status run_segment(tdse_ctx *c, long long nsteps)
 {
-    if (!c->graphs || c->profiling || nsteps <= 0) return issue_segment(c, nsteps);
+    // profiled segments are replayed (and timed as a whole) only when all their
+    // launches have one depth, so that the time can be attributed to it
+    const bool uniform = nsteps % c->tblock == 0;
+    if (!c->graphs || nsteps <= 0 || (c->profiling && !uniform)) return issue_segment(c, nsteps);
     TRY(ensure_gstream(c));
     cudaGraphExec_t exec = nullptr;
     for (auto &g : c->graph_cache)
@@ -573,7 +664,7 @@ tdse_status run_segment(tdse_ctx *c, long long nsteps)
         c->stream = c->gstream;
         cudaGraph_t graph = nullptr;
         CUDA_TRY(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
-        tdse_status st = issue_segment(c, nsteps);
+        tdse_status st = issue_segment(c, nsteps, false);
         cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
         c->stream = user;
         c->cur = cur0;
@@ -588,11 +679,15 @@ tdse_status run_segment(tdse_ctx *c, long long nsteps)
         if (e != cudaSuccess) return fail(c, TDSE_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
         c->graph_cache.push_back({static_cast<int>(nsteps), cur0, c->tblock, exec});
     }
+    int t0 = -1;
+    TRY(timer_start(c, &t0));
     TRY(replay_graph(c, exec));
+    TRY(timer_stop(c, t0, 0, static_cast<int>(nsteps / c->tblock), c->tblock));
     // the replay advanced the state exactly like issue_segment would have
     long long left = nsteps;
     while (left > 0) {
-        const int T = (left >= c->tblock) ? c->tblock : 1;
+        const int T = segment_depth(c, left);
+        note_launch(c, T);
         c->cur ^= 1;
         c->step += T;
         left -= T;
@@ -721,7 +816,7 @@ tdse_status tdse_create(const tdse_params *p, int batch, tdse_ctx **out)
     }
     int tb = p[0].tblock;
     if (tb <= 0) tb = (c->precision == TDSE_FP64) ? 1 : 2;
-    if (tb > kMaxTblock || (c->precision == TDSE_FP64 && tb != 1)) {
+    if (tb > kMaxTblock || step_variant_count(c->precision, tb) == 0) {
         delete c;
         return TDSE_EINVAL;
     }
@@ -951,13 +1046,15 @@ tdse_status tdse_set_state(tdse_ctx *c, int member, const double *R, const doubl
 tdse_status tdse_step(tdse_ctx *c, long long nsteps)
 {
     if (!c || nsteps < 0) return TDSE_EINVAL;
+    TRY(check_usable(c));
     for (size_t i = 0; i < c->m.size(); ++i)
         if (!c->m[i].have_state)
             return fail(c, TDSE_ESTATE, "member %zu has no state (call tdse_set_wavepacket)", i);
     TRY(ensure_device(c));
     int nrec = 0;
     long long left = nsteps;
-    while (left > 0) {
+    tdse_status st = TDSE_OK;
+    while (left > 0 && st == TDSE_OK) {
         long long seg = std::min(left, c->obs_every - (c->step % c->obs_every));
         if (c->ckpt_every > 0) seg = std::min(seg, c->ckpt_every - (c->step % c->ckpt_every));
         TRY(run_segment(c, seg));
@@ -965,6 +1062,7 @@ tdse_status tdse_step(tdse_ctx *c, long long nsteps)
         if (c->step % c->obs_every == 0) {
             TRY(observe_all(c, nrec));
             for (size_t i = 0; i < c->m.size(); ++i) TRY(capture_frame(c, static_cast<int>(i)));
+            TRY(post_status(c));
             if (++nrec == kRecCap) {
                 TRY(drain_records(c, nrec));
                 nrec = 0;
@@ -972,6 +1070,18 @@ tdse_status tdse_step(tdse_ctx *c, long long nsteps)
         }
         if (c->ckpt_every > 0 && c->step % c->ckpt_every == 0)
             for (Member &mb : c->m) TRY(save_checkpoint(c, mb));
+        // a failure seen at an earlier observation point ends the call there
+        // (at most kStatusLag observation intervals later), not after nsteps
+        st = poll_status(c, false);
+    }
+    if (st != TDSE_OK) {
+        cudaStreamSynchronize(c->stream);
+        const std::string why = c->err;
+        drain_records(c, nrec);
+        resolve_timers(c);
+        c->status_pending = 0;
+        c->err = why;
+        return st;
     }
     TRY(drain_records(c, nrec));
     TRY(check_status(c));
@@ -1099,6 +1209,7 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
                          double *dL_datoms, int on_device)
 {
     TRY(check_member(c, member));
+    TRY(check_usable(c));
     if (!dL_dF) return fail(c, TDSE_EINVAL, "dL_dF is NULL");
     Member &mb = c->m[member];
     if (!mb.have_state) return fail(c, TDSE_ESTATE, "member has no state");
@@ -1219,6 +1330,7 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
 tdse_status tdse_save_state(tdse_ctx *c, const char *path)
 {
     if (!c || !path) return TDSE_EINVAL;
+    TRY(check_usable(c));
     for (const Member &mb : c->m)
         if (!mb.have_state) return fail(c, TDSE_ESTATE, "every member needs a state to be saved");
     FILE *f = fopen(path, "wb");
@@ -1347,11 +1459,20 @@ int tdse_variant_count(int precision, int tsteps) { return step_variant_count(pr
 tdse_status tdse_set_variant(tdse_ctx *c, int tsteps, int variant)
 {
     if (!c) return TDSE_EINVAL;
-    if (tsteps < 1 || tsteps > kMaxTblock || (c->precision == TDSE_FP64 && tsteps != 1) ||
-        variant < 0 || variant >= step_variant_count(c->precision, tsteps))
+    if (tsteps < 1 || tsteps > kMaxTblock || variant < 0 ||
+        variant >= step_variant_count(c->precision, tsteps))
         return fail(c, TDSE_EINVAL, "no variant %d for %d fused steps", variant, tsteps);
     TRY(ensure_device(c));
     return build_plan(c, tsteps, variant);
+}
+
+tdse_status tdse_set_wait_limit(tdse_ctx *c, long long ns)
+{
+    if (!c) return TDSE_EINVAL;
+    if (ns < 0) return fail(c, TDSE_EINVAL, "negative wait limit");
+    c->wait_ns = static_cast<unsigned long long>(ns);
+    drop_graphs(c);   // captured launches carry the limit as an argument
+    return TDSE_OK;
 }
 
 tdse_status tdse_set_graphs(tdse_ctx *c, int enable)
@@ -1367,7 +1488,7 @@ tdse_status tdse_get_tuning(tdse_ctx *c, tdse_tuning *out)
     memset(out, 0, sizeof *out);
     out->tblock = c->tblock;
     for (int T = 1; T <= kMaxTblock; ++T) {
-        if (c->precision == TDSE_FP64 && T != 1) continue;
+        if (step_variant_count(c->precision, T) == 0) continue;
         out->variant[T] = c->plans[T].variant;
         out->ms_per_step[T] = c->tuned_ms_per_step[T];
         const char *n = step_variant_name(c->precision, T, c->plans[T].variant);
@@ -1379,6 +1500,7 @@ tdse_status tdse_get_tuning(tdse_ctx *c, tdse_tuning *out)
 tdse_status tdse_autotune(tdse_ctx *c, int launches)
 {
     if (!c || launches < 1) return TDSE_EINVAL;
+    TRY(check_usable(c));
     TRY(ensure_device(c));
     // save what the trial launches overwrite
     const size_t es = elem_size(c->precision);
@@ -1413,7 +1535,7 @@ tdse_status tdse_autotune(tdse_ctx *c, int launches)
     CUDA_TRY(c, cudaEventCreate(&e1));
     tdse_status st = TDSE_OK;
     for (int T = 1; T <= kMaxTblock && st == TDSE_OK; ++T) {
-        if (c->precision == TDSE_FP64 && T != 1) continue;
+        if (step_variant_count(c->precision, T) == 0) continue;
         c->tblock = T;
         double best = 1e300;
         int bestv = 0;
@@ -1441,8 +1563,11 @@ tdse_status tdse_autotune(tdse_ctx *c, int launches)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->tblock = tb0;
-    if (st == TDSE_OK && c->tblock_auto && c->precision != TDSE_FP64)
-        c->tblock = c->tuned_ms_per_step[2] < c->tuned_ms_per_step[1] ? 2 : 1;
+    if (st == TDSE_OK && c->tblock_auto) {   // the depth with the lowest time per step
+        for (int T = 1; T <= kMaxTblock; ++T)
+            if (c->tuned_ms_per_step[T] > 0 && c->tuned_ms_per_step[T] < c->tuned_ms_per_step[c->tblock])
+                c->tblock = T;
+    }
     // restore the state, the flux integral and the counters
     size_t k = 0;
     for (Member &mb : c->m) {
@@ -1482,6 +1607,9 @@ tdse_status tdse_destroy(tdse_ctx *c)
     if (!c) return TDSE_OK;
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->status_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->h_status) cudaFreeHost(c->h_status);
     drop_graphs(c);
     if (c->gstream) {
         cudaStreamSynchronize(c->gstream);

@@ -19,10 +19,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tdse.h"
+
 namespace tdse {
 
 constexpr int kGhost = 8;          // ghost width on x and y (supports up to 4 fused steps)
-constexpr int kMaxTblock = 2;      // largest number of steps fused per launch
+constexpr int kMaxTblock = TDSE_MAX_TBLOCK;   // largest number of steps fused per launch
 
 struct alignas(128) MemberDev {
     CUtensorMap tm_R[2], tm_I[2], tm_cR[2], tm_cI[2], tm_d;
@@ -58,8 +60,10 @@ struct StepLaunch {
     const MemberDev *members;
     const WorkDev *work;
     int *counter;          // dynamic work counter, zeroed before the launch
-    int *status;           // error word (bit 0: barrier timeout)
+    int *status;           // error word (bit 0: a wait for a tile's data expired; bit 2: a
+                           // CTA left with a load in flight after its drain wait expired)
     int in_buf;            // ping-pong index read by this launch
+    unsigned long long wait_ns;   // limit of each wait for a tile's data (0: test once)
     int grid, block;
     size_t smem;
     cudaStream_t stream;

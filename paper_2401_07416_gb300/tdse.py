@@ -53,16 +53,22 @@ class Obs(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+MAX_TBLOCK = 4   # TDSE_MAX_TBLOCK
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("step_launches", ctypes.c_longlong), ("step_ms", ctypes.c_double),
                 ("reduce_launches", ctypes.c_longlong), ("reduce_ms", ctypes.c_double),
                 ("cells_per_launch", ctypes.c_longlong), ("steps_per_launch", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("reserved", ctypes.c_int),
+                ("launches_at_depth", ctypes.c_longlong * (MAX_TBLOCK + 1)),
+                ("ms_at_depth", ctypes.c_double * (MAX_TBLOCK + 1))]
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("tblock", ctypes.c_int), ("variant", ctypes.c_int * 3),
-                ("ms_per_step", ctypes.c_double * 3), ("name", (ctypes.c_char * 48) * 3)]
+    _fields_ = [("tblock", ctypes.c_int), ("variant", ctypes.c_int * (MAX_TBLOCK + 1)),
+                ("ms_per_step", ctypes.c_double * (MAX_TBLOCK + 1)),
+                ("name", (ctypes.c_char * 48) * (MAX_TBLOCK + 1))]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -97,6 +103,7 @@ SIGNATURES = {
     "tdse_autotune": (_I, [_VP, _I]),
     "tdse_get_tuning": (_I, [_VP, ctypes.POINTER(Tuning)]),
     "tdse_set_graphs": (_I, [_VP, _I]),
+    "tdse_set_wait_limit": (_I, [_VP, _LL]),
     "tdse_set_profiling": (_I, [_VP, _I]),
     "tdse_get_profile": (_I, [_VP, ctypes.POINTER(Profile)]),
     "tdse_observables_static": (_I, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP]),
@@ -339,14 +346,19 @@ def tdse_autotune(ctx, launches: int = 4):
 def tdse_get_tuning(ctx) -> dict:
     t = Tuning()
     _check(ctx, lib().tdse_get_tuning(ctx, ctypes.byref(t)))
+    depths = [T for T in range(1, MAX_TBLOCK + 1) if t.name[T].value]
     return {"tblock": t.tblock,
-            "variant": {1: t.variant[1], 2: t.variant[2]},
-            "ms_per_step": {1: t.ms_per_step[1], 2: t.ms_per_step[2]},
-            "name": {1: t.name[1].value.decode(), 2: t.name[2].value.decode()}}
+            "variant": {T: t.variant[T] for T in depths},
+            "ms_per_step": {T: t.ms_per_step[T] for T in depths},
+            "name": {T: t.name[T].value.decode() for T in depths}}
 
 
 def tdse_set_graphs(ctx, enable: bool):
     _check(ctx, lib().tdse_set_graphs(ctx, int(bool(enable))))
+
+
+def tdse_set_wait_limit(ctx, ns: int):
+    _check(ctx, lib().tdse_set_wait_limit(ctx, int(ns)))
 
 
 def tdse_set_profiling(ctx, enable: bool):
@@ -356,17 +368,33 @@ def tdse_set_profiling(ctx, enable: bool):
 def tdse_get_profile(ctx) -> dict:
     p = Profile()
     _check(ctx, lib().tdse_get_profile(ctx, ctypes.byref(p)))
-    return {k: getattr(p, k) for k, _ in p._fields_ if k != "reserved"}
+    out = {k: getattr(p, k) for k, _ in p._fields_ if k not in ("reserved", "launches_at_depth",
+                                                                 "ms_at_depth")}
+    out["launches_at_depth"] = {T: p.launches_at_depth[T] for T in range(1, MAX_TBLOCK + 1)}
+    out["ms_at_depth"] = {T: p.ms_at_depth[T] for T in range(1, MAX_TBLOCK + 1)}
+    return out
 
 
 def tdse_observables_static(params: Params, R, I, V=None, stream_ptr: int = 0) -> dict:
     """Q, paper norm and energy of a device-resident FP64 state, computed without
     any device allocation (for callers that cannot allocate)."""
+    import torch
     pr, dr, _ = _arg(R)
     pi, di, _ = _arg(I)
     pv, dv, _ = _arg(V)
     if not (dr and di and (V is None or dv)):
         raise TypeError("R, I and V must be CUDA tensors")
+    # the kernels read nx*ny*nz values of each array (and their neighbours) on the
+    # current device: anything shorter, or elsewhere, is refused here
+    n = params.nx * params.ny * params.nz
+    dev = torch.cuda.current_device()
+    for name, a in (("R", R), ("I", I), ("V", V)):
+        if a is None:
+            continue
+        if a.numel() != n:
+            raise ValueError(f"{name} holds {a.numel()} values, the grid has {n}")
+        if a.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{a.device.index}, the current device is cuda:{dev}")
     out = np.zeros(3)
     st = lib().tdse_observables_static(ctypes.byref(params), pr, pi, pv,
                                        out.ctypes.data_as(ctypes.c_void_p),

@@ -47,9 +47,12 @@ def test_struct_layout_matches_header(tmp_path):
 #include <stddef.h>
 #include "tdse.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(tdse_params), offsetof(tdse_params, hx),
-         offsetof(tdse_params, bc), offsetof(tdse_params, mask_eta), offsetof(tdse_params, det_k),
-         offsetof(tdse_params, tblock), sizeof(tdse_obs), sizeof(tdse_profile));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(tdse_params),
+         offsetof(tdse_params, hx), offsetof(tdse_params, bc), offsetof(tdse_params, mask_eta),
+         offsetof(tdse_params, det_k), offsetof(tdse_params, tblock), sizeof(tdse_obs),
+         sizeof(tdse_profile), offsetof(tdse_profile, launches_at_depth),
+         offsetof(tdse_profile, ms_at_depth), sizeof(tdse_tuning), offsetof(tdse_tuning, ms_per_step),
+         offsetof(tdse_tuning, name), TDSE_MAX_TBLOCK);
   return 0;
 }
 """)
@@ -57,9 +60,11 @@ int main(void) {
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                            check=True).stdout.split()]
-    P = T.Params
+    P, Pr, Tu = T.Params, T.Profile, T.Tuning
     assert vals == [ctypes.sizeof(P), P.hx.offset, P.bc.offset, P.mask_eta.offset,
-                    P.det_k.offset, P.tblock.offset, ctypes.sizeof(T.Obs), ctypes.sizeof(T.Profile)]
+                    P.det_k.offset, P.tblock.offset, ctypes.sizeof(T.Obs), ctypes.sizeof(Pr),
+                    Pr.launches_at_depth.offset, Pr.ms_at_depth.offset, ctypes.sizeof(Tu),
+                    Tu.ms_per_step.offset, Tu.name.offset, T.MAX_TBLOCK]
 
 
 def _params(**kw):
@@ -155,9 +160,24 @@ def test_static_observables_validate_before_device_work(lib):
     for field, value in (("nz", 8193), ("ny", 1 << 27), ("hz", 0.0)):
         p = _params(**{field: value})
         assert T.lib().tdse_observables_static(ctypes.byref(p), ptr, ptr, None, optr, None) == T.EINVAL
+    for axis in range(3):               # boundary flags tdse_create would reject
+        p = _params()
+        p.bc[axis] = 2
+        assert T.lib().tdse_observables_static(ctypes.byref(p), ptr, ptr, None, optr, None) == T.EINVAL
     p = _params()
     assert T.lib().tdse_observables_static(ctypes.byref(p), None, ptr, None, optr, None) == T.EINVAL
 
 
 def test_version_string(lib):
     assert "sm_103a" in T.tdse_version()
+
+
+def test_build_is_stale_when_flags_change(lib, monkeypatch):
+    """The library is rebuilt when the compiler flags differ from those recorded
+    at its build, not only when a source is newer."""
+    from paper_2401_07416_gb300 import build as B
+    assert not B._stale()
+    monkeypatch.setattr(B, "FLAGS", B.FLAGS + ["-DTDSE_FLAG_PROBE"])
+    assert B._stale()
+    monkeypatch.setattr(B, "ARCH", ["-gencode", "arch=compute_100a,code=sm_100a"])
+    assert B._stale()

@@ -1,0 +1,157 @@
+"""Failure paths of the step, made on the host with every device access valid.
+
+- Allocation failure: an allocator callback that returns NULL on its k-th call
+  gives TDSE_ENOMEM, and the context is still destroyed cleanly.
+- Expired waits: tdse_set_wait_limit(ctx, 0) makes every wait of the step kernels
+  for a tile's data test its data once, so waits for loads still in flight
+  expire while every load stays valid.  The kernels then stop, wait for their
+  own loads, release tensor memory and leave; tdse_step returns TDSE_ETIMEOUT and
+  the context refuses further steps.  A fresh context on the same kernels then
+  runs normally (nothing was left held on the device).
+- Divergence: an unstable run ends tdse_step at the observation point that saw
+  it (within two observation intervals), not after all requested steps.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2401_07416_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_07416_gb300 import build
+    build.build()
+    from paper_2401_07416_gb300 import tdse
+    return tdse
+
+
+def small_case():
+    g = W.small_grid(40, 36, 48, h=(0.2, 0.2, 0.2), dt=0.004, bc=(0, 0, 1), mask=6, det_k=20,
+                     eta=0.3)
+    p = W.Packet((4.0, 3.6, 5.0), (1.0, 1.0, 1.0), (0.0, 0.0, -1.5))
+    return g, p
+
+
+class CountingAllocator:
+    """Device memory from torch's caching allocator; returns NULL on call `fail_at`
+    (1-based; 0: never)."""
+
+    def __init__(self, T, fail_at=0):
+        import torch
+        self.calls = 0
+        self.live = set()
+        self.fail_at = fail_at
+        dev = torch.cuda.current_device()
+        stream = torch.cuda.current_stream()
+
+        def alloc(nbytes, user):
+            self.calls += 1
+            if self.calls == self.fail_at:
+                return None
+            ptr = torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+            self.live.add(ptr)
+            return ptr
+
+        def free(ptr, user):
+            self.live.discard(ptr)
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.cbs = (T.ALLOC_FN(alloc), T.FREE_FN(free))
+
+
+def run_with_allocator(T, prec, tblock, alloc):
+    g, p = small_case()
+    ctx = T.tdse_create([T.params_from_grid(g, prec, tblock)])
+    try:
+        T.tdse_set_allocator(ctx, *alloc.cbs)
+        T.tdse_set_wavepacket(ctx, 0, p.r0, p.sigma, p.k0)
+        T.tdse_step(ctx, 4)
+        return T.OK
+    except T.TdseError as e:
+        return e.status
+    finally:
+        T.tdse_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,tblock", [("FP64", 1), ("FP32_KAHAN", 2)])
+def test_allocator_null_gives_enomem(T, prec, tblock):
+    prec = getattr(T, prec)
+    full = CountingAllocator(T)
+    assert run_with_allocator(T, prec, tblock, full) == T.OK
+    n = full.calls
+    assert n > 10 and not full.live        # every allocation was freed by tdse_destroy
+    # the first, a middle and the last allocation of the run fail in turn
+    for k in sorted({1, 2, n // 3, n // 2, n - 1, n}):
+        a = CountingAllocator(T, fail_at=k)
+        assert run_with_allocator(T, prec, tblock, a) == T.ENOMEM, k
+        assert not a.live, k               # destroyed cleanly after the failure
+    # the device is still fine afterwards
+    assert run_with_allocator(T, prec, tblock, CountingAllocator(T)) == T.OK
+
+
+@pytest.mark.parametrize("prec,tblock", [("FP64", 1), ("FP32", 1), ("FP32", 2), ("FP32_KAHAN", 2)])
+def test_expired_wait_gives_etimeout_and_fails_the_context(T, prec, tblock):
+    from paper_2401_07416_gb300.sim import Sim
+    prec = getattr(T, prec)
+    g, p = small_case()
+    s = Sim(g, precision=prec, tblock=tblock)
+    s.set_packet(0, p)
+    s.step(tblock)                        # a normal launch first
+    T.tdse_set_wait_limit(s.ctx, 0)
+    with pytest.raises(T.TdseError) as e:
+        s.step(40)
+    assert e.value.status == T.ETIMEOUT, str(e.value)
+    with pytest.raises(T.TdseError) as e2:
+        s.step(2)
+    assert e2.value.status == T.ESTATE
+    s.state(0)                            # reading the (meaningless) state still works
+    s.close()
+    # the same kernels run normally in a new context: no wait, tensor memory or load
+    # was left behind, and the result equals a run that never saw a timeout
+    ref = None
+    for _ in range(2):
+        with Sim(g, precision=prec, tblock=tblock) as s2:
+            s2.set_packet(0, p)
+            s2.step(20)
+            got = s2.state(0)
+        if ref is not None:
+            assert all(np.array_equal(a, b) for a, b in zip(got, ref))
+        ref = got
+
+
+def test_wait_limit_rejects_negative(T):
+    g, _ = small_case()
+    ctx = T.tdse_create([T.params_from_grid(g, T.FP64, 1)])
+    try:
+        with pytest.raises(T.TdseError) as e:
+            T.tdse_set_wait_limit(ctx, -1)
+        assert e.value.status == T.EINVAL
+    finally:
+        T.tdse_destroy(ctx)
+
+
+def test_divergence_ends_the_call_at_the_failing_observation(T):
+    """dt |V| = 12, far beyond the leapfrog's bound of 2: Q grows by orders of
+    magnitude within the first observation interval (20 steps).  A request of a
+    million steps must end within two observation intervals of that point."""
+    from paper_2401_07416_gb300.sim import Sim
+    g = W.small_grid(16, 16, 16, h=(0.2, 0.2, 0.2), dt=0.004, bc=(1, 1, 1))
+    with Sim(g, precision=T.FP64) as s:
+        s.set_potential(0, np.full((16, 16, 16), 3000.0))
+        s.set_packet(0, W.Packet((1.5, 1.5, 1.5), (0.5, 0.5, 0.5), (0, 0, 1)))
+        with pytest.raises(T.TdseError) as e:
+            s.step(10 ** 6)
+        assert e.value.status == T.EUNSTABLE
+        assert "step 20" in str(e.value)
+        step = s.observables(0)["step"]
+        assert 20 <= step <= 20 * 3, step
+        with pytest.raises(T.TdseError) as e2:
+            s.step(1)
+        assert e2.value.status == T.ESTATE

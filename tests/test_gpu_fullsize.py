@@ -21,6 +21,7 @@ import math
 import numpy as np
 import pytest
 
+import light_cone as LC
 import oracle
 from paper_2401_07416_gb300 import workloads as W
 
@@ -152,25 +153,6 @@ def test_config3_batch_autotuned_equals_solo_and_oracle(T):
     assert rel_l2(got[17][0][0], got[17][0][1], Ro, Io) < 1e-4
 
 
-def window_oracle(wl, x0, y0, width, steps):
-    """Oracle state on a width x width x nz column starting at node (x0, y0)."""
-    g = wl.grid
-    sub = W.Grid(nx=width, ny=width, nz=g.nz, hx=g.hx, hy=g.hy, hz=g.hz, dt=g.dt,
-                 bc=(W.DIRICHLET, W.DIRICHLET, g.bc[2]), mask_lo=g.mask_lo,
-                 mask_hi=g.mask_hi, mask_eta=g.mask_eta, det_k=-1)
-    origin = (x0 * g.hx, y0 * g.hy, 0.0)
-    L = g.lengths
-    period = [l if b == W.PERIODIC else 0.0 for l, b in zip(L, g.bc)]
-    V = oracle.potential_atoms_window(sub, origin, period, wl.atoms, rc=0.5 * min(L[0], L[1]))
-    R0, I0 = oracle.wavepacket_window(sub, origin, wl.packet.r0, wl.packet.sigma, wl.packet.k0)
-    # the packet is a plane wave along x and y: the full grid's normalisation is the
-    # window's times sqrt(window area / grid area)
-    s = math.sqrt((width * width) / (g.nx * g.ny))
-    R0, I0 = R0 * s, I0 * s
-    R, I, _, _ = oracle.run(sub, V, R0, oracle.init_half(sub, V, R0, I0), steps, flux=False)
-    return R, I
-
-
 @pytest.mark.parametrize("precision", ["FP32_KAHAN", "FP32", "FP64"])
 def test_config5_light_cone_windows(T, precision):
     import torch
@@ -199,13 +181,14 @@ def test_config5_light_cone_windows(T, precision):
     assert obs["Q"] == pytest.approx(oo["Q"], rel=tol_q)
     assert obs["norm_paper"] == pytest.approx(oo["norm_paper"], rel=tol_q)
     assert obs["energy"] == pytest.approx(oo["energy"], rel=tol_e)
-    width, margin = 40, 2 * steps + 2
+    # oracle columns (light_cone.py, pinned on the CPU against full-grid runs)
+    width, margin = 40, LC.margin(steps)
     for (x0, y0) in [(-20, -20), (200, 130), (492, 300), (100, 480)]:
         xs = np.arange(x0, x0 + width) % g.nx
         ys = np.arange(y0, y0 + width) % g.ny
         Rg = Rd[:, ys][:, :, xs].cpu().numpy()
         Ig = Id[:, ys][:, :, xs].cpu().numpy()
-        Ro, Io = window_oracle(wl, x0, y0, width, steps)
+        Ro, Io = LC.window_run(g, wl.atoms, wl.packet, x0, y0, width, steps)
         sl = (slice(None), slice(margin, width - margin), slice(margin, width - margin))
         if prec == T.FP64:
             scale = max(np.abs(Ro[sl]).max(), np.abs(Io[sl]).max())

@@ -665,3 +665,84 @@ def test_oracle_steps_independent_of_thread_count():
     for a, b in zip(out[0], out[1]):
         if isinstance(a, np.ndarray):
             assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------------- window forms
+
+def _periodic_slab_case():
+    """A 36 x 28 x 22 grid, periodic in x and y (Eqs. 13-14), walls and absorbing
+    layers in z, a small seeded slab, and a packet that is a plane wave along x
+    (one period of the box) and y (k = 0), Gaussian along z."""
+    g = W.Grid(nx=36, ny=28, nz=22, hx=0.21, hy=0.19, hz=0.23, dt=0.004,
+               bc=(W.PERIODIC, W.PERIODIC, W.DIRICHLET), mask_lo=3, mask_hi=3,
+               mask_eta=0.4, det_k=-1)
+    atoms = W.square_slab(3, 2, 2.1, 0.55 * g.lengths[2], 0.3, 0.7, W.rng_for(77), 0.05)
+    kx = 2 * math.pi / g.lengths[0]
+    packet = W.Packet((1.0, 1.0, 0.5 * g.lengths[2]), (0.0, 0.0, 0.8), (kx, 0.0, -1.2))
+    return g, atoms, packet
+
+
+WINDOWS = [(-5, -3), (20, 15), (0, 0), (29, 25), (-12, 17)]
+
+
+def test_window_potential_equals_full_grid_slices():
+    """The oracle's window form of the atom potential (node (0,0,0) at a non-zero
+    origin, minimum image with the full grid's periods) equals the full-grid
+    potential at the same nodes, including windows that cross the periodic seams
+    or start at negative indices.  The full-grid form is pinned above (closed
+    form, images, cut-off); this pins the window branch to it."""
+    import light_cone as LC
+    g, atoms, packet = _periodic_slab_case()
+    V = oracle.potential_atoms(g, atoms)
+    for x0, y0 in WINDOWS:
+        sub, Vw, _, _ = LC.window_start(g, atoms, packet, x0, y0, 12)
+        ref = LC.full_slice(V, g, x0, y0, 12)
+        assert np.abs(Vw - ref).max() <= 1e-12 * np.abs(ref).max(), (x0, y0)
+
+
+def test_window_packet_equals_full_grid_slices():
+    """The window form of the Eq. 3 packet, rescaled by sqrt(window area / grid
+    area) for a packet that is a plane wave along x and y, equals the full grid's
+    normalised packet on the window's nodes; with a Gaussian along every axis
+    and a window inside the grid, the window packet is the full one times a
+    single constant (its own normalisation)."""
+    import light_cone as LC
+    g, atoms, packet = _periodic_slab_case()
+    R, I = oracle.wavepacket(g, packet.r0, packet.sigma, packet.k0)
+    for x0, y0 in WINDOWS:
+        _, _, Rw, Iw = LC.window_start(g, atoms, packet, x0, y0, 12)
+        Rr, Ir = LC.full_slice(R, g, x0, y0, 12), LC.full_slice(I, g, x0, y0, 12)
+        scale = max(np.abs(Rr).max(), np.abs(Ir).max())
+        assert max(np.abs(Rw - Rr).max(), np.abs(Iw - Ir).max()) <= 1e-12 * scale, (x0, y0)
+    # Gaussian in x and y too: the window's origin enters each factor exactly once
+    r0, sig = (3.5, 2.9, 2.6), (1.1, 0.9, 0.8)
+    R, I = oracle.wavepacket(g, r0, sig, packet.k0)
+    sub = LC.window_grid(g, 12)
+    Rw, Iw = oracle.wavepacket_window(sub, (10 * g.hx, 7 * g.hy, 0.0), r0, sig, packet.k0)
+    Rr, Ir = R[:, 7:19, 10:22], I[:, 7:19, 10:22]
+    c = np.sqrt(np.sum(Rw ** 2 + Iw ** 2) / np.sum(Rr ** 2 + Ir ** 2))
+    assert np.abs(Rw - c * Rr).max() <= 1e-12 * np.abs(Rw).max()
+    assert np.abs(Iw - c * Ir).max() <= 1e-12 * np.abs(Iw).max()
+
+
+@pytest.mark.parametrize("steps", [1, 3])
+def test_light_cone_window_equals_full_periodic_run(steps):
+    """After N steps, window nodes more than 2N + 1 cells inside the window's walls
+    hold the full periodic run's values (the claim the 512 x 512 x 1024 GPU check
+    rests on), while nodes next to the walls do not (the check can fail)."""
+    import light_cone as LC
+    g, atoms, packet = _periodic_slab_case()
+    V = oracle.potential_atoms(g, atoms)
+    R0, I0 = oracle.wavepacket(g, packet.r0, packet.sigma, packet.k0)
+    Rf, If, _, _ = oracle.run(g, V, R0, oracle.init_half(g, V, R0, I0), steps, flux=False)
+    width = 2 * LC.margin(steps) + 6
+    m = LC.margin(steps)
+    inner = (slice(None), slice(m, width - m), slice(m, width - m))
+    for x0, y0 in WINDOWS:
+        Rw, Iw = LC.window_run(g, atoms, packet, x0, y0, width, steps)
+        Rr, Ir = LC.full_slice(Rf, g, x0, y0, width), LC.full_slice(If, g, x0, y0, width)
+        scale = max(np.abs(Rr).max(), np.abs(Ir).max())
+        err = max(np.abs(Rw - Rr)[inner].max(), np.abs(Iw - Ir)[inner].max())
+        assert err <= 1e-12 * scale, (x0, y0, err / scale)
+        edge = max(np.abs(Rw - Rr)[:, :, 0].max(), np.abs(Iw - Ir)[:, :, 0].max())
+        assert edge > 1e-6 * scale, (x0, y0)
