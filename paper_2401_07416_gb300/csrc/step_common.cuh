@@ -81,6 +81,28 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another warp has raised *abort_flag:
+// 1 the phase completed, 0 the limit expired, -1 abandoned (flag raised).  A limit
+// of 0 tests the phase once, as in mbar_wait_bounded.
+__device__ __forceinline__ int mbar_wait_or_abort(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns,
+                                                  const volatile int *abort_flag)
+{
+    if (limit_ns == 0) return mbar_test_wait(bar, parity) ? 1 : 0;
+    if (mbar_try_wait(bar, parity)) return 1;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return -1;
+        if (global_ns() - t0 > limit_ns) return 0;
+    }
+    return 1;
+}
+
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y,
                                             int z, uint64_t *bar)
 {

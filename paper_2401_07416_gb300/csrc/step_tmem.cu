@@ -108,8 +108,28 @@ struct TmemShape {
     static_assert(C::DSTASH, "the tensor-memory kernel keeps d in TMEM");
 };
 
-template <class C>
-__global__ void __launch_bounds__(C::NT, C::MINB)
+// Synchronisation of the z-march, two forms (WS):
+//   false  thread 0 waits for each plane's loads and refills the rings, and one
+//          CTA barrier per plane orders everything;
+//   true   a producer warp (after the C::NT compute threads) issues the loads; a
+//          compute warp waits for its plane's loads (full[]) and for its two
+//          neighbouring warps to finish the previous plane (nbr[], the only
+//          shared-memory exchange between warps: the stage planes of the rows at
+//          its edges), and reports each finished plane (done[]), after which the
+//          producer may refill that plane's ring slots.  No CTA-wide barrier inside
+//          the z-march: warps drift apart by up to the ring depth.
+template <class C, bool WS>
+struct TmemSync {
+    static constexpr int NWC = C::NT / 32;                     // compute warps
+    static constexpr int THREADS = C::NT + (WS ? 32 : 0);
+    static constexpr size_t SMEM = C::SMEM + (WS ? 8u * (C::NB + 2 * NWC) : 0u);
+    static_assert(!WS || NWC >= 2, "neighbour barriers need two compute warps");
+    static_assert(!WS || C::MINB * (SMEM + 1024) <= 233472, "CTAs per SM exceed the shared memory");
+    static_assert(!WS || C::PF >= 1, "the producer needs at least one plane ahead");
+};
+
+template <class C, bool WS>
+__global__ void __launch_bounds__(TmemSync<C, WS>::THREADS, C::MINB)
     fused_step_tmem_kernel(const MemberDev *__restrict__ members, const WorkDev *__restrict__ work,
                            int *counter, int *status, int in_buf,
                            unsigned long long wait_ns)
@@ -120,13 +140,16 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     constexpr int RPT = C::RPT, NB = C::NB, PF = C::PF, NR = C::NR, NI = C::NI, ND = C::ND;
     constexpr int SLOT = C::NFC * PLANE;    // one ring slot: a field (and its compensation)
     constexpr int OFF_C = PLANE;            // compensation term within a slot
+    constexpr int NWC = TmemSync<C, WS>::NWC;
 
     extern __shared__ unsigned char smem_raw[];
     Real *ringA = reinterpret_cast<Real *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     Real *ringI = ringA + NR * SLOT;
     Real *ringD = ringI + NI * SLOT;
     Real *sbuf = ringD + ND * PLANE;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sbuf + C::NSB * PLANE);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sbuf + C::NSB * PLANE);   // full[NB]
+    uint64_t *done = bars + NB;          // WS: done[NB]
+    uint64_t *nbr = done + NB;           // WS: nbr[NWC][2], by iteration parity
     __shared__ int s_item;
     __shared__ int s_abort;
     __shared__ uint32_t s_tmem;
@@ -134,6 +157,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const bool producer = WS && warp == NWC;
+    const volatile int *abort_flag = &s_abort;
     const int qx = tid % C::TPX;
     const int r0 = (tid / C::TPX) * RPT;                 // first region row of this thread
     const int warp_row0 = warp * C::RW;
@@ -144,6 +170,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     if (warp == 0) tmem_alloc(&s_tmem, TS::NCOLS);
     if (tid == 0) {
         for (int b = 0; b < NB; ++b) mbar_init(&bars[b], 1);
+        if constexpr (WS) {
+            for (int b = 0; b < NB; ++b) mbar_init(&done[b], NWC);
+            for (int w = 0; w < NWC; ++w)
+                for (int k = 0; k < 2; ++k) mbar_init(&nbr[2 * w + k], (w > 0) + (w < NWC - 1));
+        }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -196,6 +227,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
             for (int v = 0; v < VEC; ++v) walls |= !inside(r, v);
+        walls = walls && !producer;
         const bool col_in = qx * VEC >= C::HX && qx * VEC < C::HX + C::TX && xs < nx;
         bool store_row[RPT];
         bool any_store = false;
@@ -215,7 +247,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 
         // Windows start at zero (planes before the first computed one), as in the
         // register-window kernel.
-        {
+        if (!producer) {
             float zero[4] = {0.f, 0.f, 0.f, 0.f};
             for (int f = 0; f < TS::NF; ++f)
                 for (int k = 0; k < 3; ++k)
@@ -253,11 +285,29 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             tma_load_3d(ringD + d * PLANE, &M.tm_d, bx, by, zc, bar);
         };
 
-        if (tid == 0) {
+        // The same loads for the producer warp: plane L0 + l into ring slots l mod NR,
+        // NI, ND (the rings restart with each item) and barrier slot (gbase + l) mod NB.
+        auto issue_at = [&](int l) {
+            const int L = L0 + l;
+            const int zc = zper ? ((L % nz) + nz) % nz : L;
+            uint64_t *bar = &bars[(gbase + l) % NB];
+            Real *slotR = ringA + (l % NR) * SLOT;
+            Real *slotI = ringI + (l % NI) * SLOT;
+            mbar_arrive_expect_tx(bar, C::TX_BYTES);
+            tma_load_3d(slotR, &M.tm_R[in_buf], bx, by, zc, bar);
+            tma_load_3d(slotI, &M.tm_I[in_buf], bx, by, zc, bar);
+            if constexpr (C::KAHAN) {
+                tma_load_3d(slotR + OFF_C, &M.tm_cR[in_buf], bx, by, zc, bar);
+                tma_load_3d(slotI + OFF_C, &M.tm_cI[in_buf], bx, by, zc, bar);
+            }
+            tma_load_3d(ringD + (l % ND) * PLANE, &M.tm_d, bx, by, zc, bar);
+        };
+
+        if (!WS && tid == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             for (int l = 0; l < PF && l < nit; ++l) issue(l, l);
         }
-        int issued = min(PF, nit);
+        int issued = WS ? 0 : min(PF, nit);
         int waited = 0;
 
         auto stages = [&](const int it, const int p, const uint32_t K0, const uint32_t K1, const uint32_t K2,
@@ -459,29 +509,14 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 
         int ph = 0;   // it % 3: window slot of the old plane
         int dj = 0;   // TMEM slot of d at plane p (modulo NDT)
-        for (int it = 0; it < nit; ++it) {
+        // One plane of the z-march once its loads have landed: d to TMEM, the stages,
+        // the ring heads.
+        auto plane_body = [&](const int it) {
             const int p = L0 + it;
-            if (tid == 0) {
-                if (mbar_wait_bounded(&bars[headB], phase, wait_ns)) {
-                    waited = it + 1;
-                } else {
-                    atomicOr(status, 1);
-                    s_abort = 1;
-                }
-            }
-            __syncthreads();   // plane p has landed; the previous iteration's reads are done
-            if (s_abort) break;
-            if (it + PF < nit) {
-                if (tid == 0) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue(it + PF, PF);
-                }
-                issued = it + PF + 1;
-            }
             tmem_wait_st();   // the previous iteration's window planes are in TMEM
             {
                 // d at plane p moves to TMEM slot dj; its shared-memory slot is free
-                // again once every thread has copied it (next iteration's barrier)
+                // again once every thread has copied it
                 Real dp[RPT][VEC];
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
@@ -510,13 +545,87 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             if (headB == 0) phase ^= 1u;
             ph = ph == 2 ? 0 : ph + 1;
             ++dj;   // slots are taken modulo NDT
+        };
+
+        if constexpr (!WS) {
+            for (int it = 0; it < nit; ++it) {
+                if (tid == 0) {
+                    if (mbar_wait_bounded(&bars[headB], phase, wait_ns)) {
+                        waited = it + 1;
+                    } else {
+                        atomicOr(status, 1);
+                        s_abort = 1;
+                    }
+                }
+                __syncthreads();   // plane L0 + it has landed; the previous iteration's reads are done
+                if (s_abort) break;
+                if (it + PF < nit) {
+                    if (tid == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(it + PF, PF);
+                    }
+                    issued = it + PF + 1;
+                }
+                plane_body(it);
+            }
+        } else if (producer) {
+            // Plane l goes to ring slots l mod NR / NI / ND and barrier slot
+            // (gbase + l) mod NB.  Those slots last held plane l - NB (the R, I and d
+            // rings are read up to 2, 1 and 0 planes after landing, so their depths
+            // PF + 3, PF + 2, PF + 1 all free their slot after plane l - NB's
+            // iteration): refill only once every compute warp has reported it done.
+            if (lane == 0) {
+                for (int l = 0; l < nit; ++l) {
+                    const long long g = gbase + l;
+                    if (l >= NB) {
+                        const long long gd = g - NB;
+                        const int w = mbar_wait_or_abort(&done[gd % NB], static_cast<uint32_t>((gd / NB) & 1),
+                                                         wait_ns, abort_flag);
+                        if (w <= 0) {
+                            if (w == 0) atomicOr(status, 1);
+                            s_abort = 1;
+                            break;
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue_at(l);
+                    issued = l + 1;
+                }
+            }
+        } else {
+            for (int it = 0; it < nit; ++it) {
+                const long long g = gbase + it;
+                // this plane's loads have landed, and both neighbouring warps are done
+                // with the previous plane (their edge rows of the stage planes)
+                int w = mbar_wait_or_abort(&bars[g % NB], static_cast<uint32_t>((g / NB) & 1), wait_ns,
+                                           abort_flag);
+                if (w > 0 && g > 0)
+                    w = mbar_wait_or_abort(&nbr[2 * warp + ((g - 1) & 1)],
+                                           static_cast<uint32_t>(((g - 1) >> 1) & 1), wait_ns, abort_flag);
+                if (!__all_sync(kFull, w > 0)) {   // one decision for the whole warp
+                    if (lane == 0) {
+                        if (__any_sync(1u, w == 0)) atomicOr(status, 1);
+                        s_abort = 1;
+                    }
+                    break;
+                }
+                plane_body(it);
+                __syncwarp();   // every lane's stage-plane rows are written
+                if (lane == 0) {
+                    mbar_arrive(&done[g % NB]);
+                    if (warp > 0) mbar_arrive(&nbr[2 * (warp - 1) + (g & 1)]);
+                    if (warp < NWC - 1) mbar_arrive(&nbr[2 * (warp + 1) + (g & 1)]);
+                }
+            }
         }
 
         __syncthreads();   // every thread has left the z-march: all read the same s_abort
         if (s_abort) {
-            // wait (bounded) for the loads still in flight, then leave (freeing TMEM below)
-            if (tid == 0) {
-                for (int l = waited; l < issued; ++l) {
+            // wait (bounded) for the loads still in flight, then leave (freeing TMEM below).
+            // With a producer warp, planes before issued - NB had their slots refilled,
+            // which required every warp to have consumed them: only the last NB remain.
+            if (WS ? (producer && lane == 0) : tid == 0) {
+                for (int l = WS ? max(0, issued - NB) : waited; l < issued; ++l) {
                     const long long g = gbase + l;
                     if (!mbar_wait_bounded(&bars[g % NB], static_cast<uint32_t>((g / NB) & 1)))
                         atomicOr(status, 4);   // the CTA leaves with a load still in flight
@@ -536,34 +645,39 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     if (warp == 0) tmem_dealloc(s_tmem, TS::NCOLS);
 }
 
-template <class C>
+template <class C, bool WS>
 cudaError_t launch_tmem_cfg(const StepLaunch &L)
 {
+    typedef TmemSync<C, WS> Y;
     static std::atomic<uint64_t> smem_allowed{0};   // one bit per device
-    cudaError_t e = allow_dynamic_smem(fused_step_tmem_kernel<C>, C::SMEM, smem_allowed);
+    cudaError_t e = allow_dynamic_smem(fused_step_tmem_kernel<C, WS>, Y::SMEM, smem_allowed);
     if (e != cudaSuccess) return e;
-    fused_step_tmem_kernel<C><<<L.grid, C::NT, C::SMEM, L.stream>>>(L.members, L.work, L.counter,
-                                                                    L.status, L.in_buf, L.wait_ns);
+    fused_step_tmem_kernel<C, WS><<<L.grid, Y::THREADS, Y::SMEM, L.stream>>>(
+        L.members, L.work, L.counter, L.status, L.in_buf, L.wait_ns);
     return cudaGetLastError();
 }
 
-template <class C>
+template <class C, bool WS>
 void fill_tmem_config(StepConfig *cfg)
 {
     cfg->tile_x = C::TX;
     cfg->tile_y = C::TY;
     cfg->box_x = C::W;
     cfg->box_y = C::ROWS;
-    cfg->threads = C::NT;
-    cfg->smem = C::SMEM;
+    cfg->threads = TmemSync<C, WS>::THREADS;
+    cfg->smem = TmemSync<C, WS>::SMEM;
     cfg->ctas_per_sm = C::MINB;
 }
 
 }  // namespace
 
 #define TDSE_TMEM_VARIANT(FN, ...)                                                      \
-    cudaError_t launch_##FN(const StepLaunch &L) { return launch_tmem_cfg<Cfg<__VA_ARGS__>>(L); } \
-    void fill_##FN(StepConfig *cfg) { fill_tmem_config<Cfg<__VA_ARGS__>>(cfg); }
+    cudaError_t launch_##FN(const StepLaunch &L) { return launch_tmem_cfg<Cfg<__VA_ARGS__>, false>(L); } \
+    void fill_##FN(StepConfig *cfg) { fill_tmem_config<Cfg<__VA_ARGS__>, false>(cfg); }
+// the same kernel shape with a producer warp and neighbour barriers (TmemSync)
+#define TDSE_TMEM_WS_VARIANT(FN, ...)                                                   \
+    cudaError_t launch_##FN(const StepLaunch &L) { return launch_tmem_cfg<Cfg<__VA_ARGS__>, true>(L); } \
+    void fill_##FN(StepConfig *cfg) { fill_tmem_config<Cfg<__VA_ARGS__>, true>(cfg); }
 
 // Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched, CTAs per SM,
 //     d kept in TMEM>
@@ -578,5 +692,10 @@ TDSE_TMEM_VARIANT(tmem_k32_t2_w32_r28x1_pf2_b2, float, 4, 8, 28, 1, true, 2, 2, 
 TDSE_TMEM_VARIANT(tmem_k32_t2_w32_r32x1_pf2_b2, float, 4, 8, 32, 1, true, 2, 2, true)
 TDSE_TMEM_VARIANT(tmem_f32_t2_w32_r32x1_pf4_b2, float, 4, 8, 32, 1, false, 4, 2, true)
 TDSE_TMEM_VARIANT(tmem_f32_t2_w32_r32x1_pf3_b2, float, 4, 8, 32, 1, false, 3, 2, true)
+// producer warp + neighbour barriers
+TDSE_TMEM_WS_VARIANT(ws_k32_t2_w32_r32x1_pf2_b2, float, 4, 8, 32, 1, true, 2, 2, true)
+TDSE_TMEM_WS_VARIANT(ws_k32_t2_r32x1_pf2, float, 4, 16, 32, 1, true, 2, 1, true)
+TDSE_TMEM_WS_VARIANT(ws_f32_t2_w32_r32x1_pf3_b2, float, 4, 8, 32, 1, false, 3, 2, true)
+TDSE_TMEM_WS_VARIANT(ws_f32_t2_w32_r32x1_pf4_b2, float, 4, 8, 32, 1, false, 4, 2, true)
 
 }  // namespace tdse
