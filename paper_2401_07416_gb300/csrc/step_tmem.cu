@@ -602,9 +602,10 @@ __global__ void __launch_bounds__(TmemSync<C, WS>::THREADS, C::MINB)
                 if (w > 0 && g > 0)
                     w = mbar_wait_or_abort(&nbr[2 * warp + ((g - 1) & 1)],
                                            static_cast<uint32_t>(((g - 1) >> 1) & 1), wait_ns, abort_flag);
+                const bool expired = __any_sync(kFull, w == 0);
                 if (!__all_sync(kFull, w > 0)) {   // one decision for the whole warp
                     if (lane == 0) {
-                        if (__any_sync(1u, w == 0)) atomicOr(status, 1);
+                        if (expired) atomicOr(status, 1);
                         s_abort = 1;
                     }
                     break;
