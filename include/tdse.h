@@ -86,7 +86,9 @@ typedef struct tdse_params {
     int obs_every;           /* norm/energy reduction every obs_every steps (<= 0: 20, Sec. 2.3) */
     int ckpt_every;          /* > 0: keep FP64 checkpoints every ckpt_every steps for tdse_adjoint */
     int precision;           /* TDSE_FP64 / TDSE_FP32 / TDSE_FP32_KAHAN (same for all members) */
-    int tblock;              /* steps fused per kernel launch (temporal blocking); 0: automatic */
+    int tblock;              /* steps fused per kernel launch (temporal blocking), 1..TDSE_MAX_TBLOCK
+                                among the depths with kernel variants (tdse_variant_count: FP64
+                                fuses 1, FP32 and FP32_KAHAN 1 to 4); 0: automatic */
     int mask_kind;           /* TDSE_MASK_COS2 (0) or TDSE_MASK_CAP (1), see below */
     int reserved[5];         /* must be zero */
 } tdse_params;
@@ -184,7 +186,8 @@ TDSE_API tdse_status tdse_set_state(tdse_ctx *ctx, int member, const double *R, 
 /* Advance every member by nsteps leapfrog steps (Eqs. 8-9 + absorbing layer),
  * accumulating the detector flux, reducing Q and E every obs_every steps and
  * recording checkpoints every ckpt_every steps.  Returns EUNSTABLE if a
- * reduction saw non-finite values or Q above (1 + 1e-3) times its first value,
+ * reduction saw non-finite values or, when the first value Q0 is positive, Q
+ * above (1 + 1e-3) Q0,
  * and ETIMEOUT if a step kernel's bounded wait for a tile's data expired (see
  * tdse_set_wait_limit).  Each observation point copies the kernels' status word
  * to the host without stalling the GPU; the host reads these copies as they

@@ -41,6 +41,12 @@ TDSE_TMEM_DECL(tmem_k32_t2_w32_r28x1_pf2_b2)
 TDSE_TMEM_DECL(tmem_k32_t2_w32_r32x1_pf2_b2)
 TDSE_TMEM_DECL(tmem_f32_t2_w32_r32x1_pf4_b2)
 TDSE_TMEM_DECL(tmem_f32_t2_w32_r32x1_pf3_b2)
+TDSE_TMEM_DECL(tmem_k32_t3_w32_r32x1_pf2)
+TDSE_TMEM_DECL(tmem_k32_t4_w32_r32x1_pf2)
+TDSE_TMEM_DECL(tmem_f32_t3_r32x1_pf2)
+TDSE_TMEM_DECL(tmem_f32_t4_w32_r40x1_pf2)
+TDSE_TMEM_DECL(ws_k32_t3_w32_r32x1_pf2)
+TDSE_TMEM_DECL(ws_f32_t3_r32x1_pf2)
 TDSE_TMEM_DECL(ws_k32_t2_w32_r32x1_pf2_b2)
 TDSE_TMEM_DECL(ws_k32_t2_r32x1_pf2)
 TDSE_TMEM_DECL(ws_f32_t2_w32_r32x1_pf3_b2)
@@ -529,6 +535,12 @@ const Variant kVariants[] = {
     Variant{2, 2, "k32_t2_tmem_w32_r28x1_pf2_b2", &fill_tmem_k32_t2_w32_r28x1_pf2_b2, &launch_tmem_k32_t2_w32_r28x1_pf2_b2},
     Variant{2, 2, "k32_t2_tmem_r32x1_pf2", &fill_tmem_k32_t2_r32x1_pf2, &launch_tmem_k32_t2_r32x1_pf2},
     TDSE_VARIANT(2, 2, "k32_t2_w64_r32x2_pf1", float, 4, 16, 32, 2, true, 1),
+    Variant{1, 3, "f32_t3_tmem_r32x1_pf2", &fill_tmem_f32_t3_r32x1_pf2, &launch_tmem_f32_t3_r32x1_pf2},
+    Variant{1, 3, "f32_t3_ws_r32x1_pf2", &fill_ws_f32_t3_r32x1_pf2, &launch_ws_f32_t3_r32x1_pf2},
+    Variant{1, 4, "f32_t4_tmem_w32_r40x1_pf2", &fill_tmem_f32_t4_w32_r40x1_pf2, &launch_tmem_f32_t4_w32_r40x1_pf2},
+    Variant{2, 3, "k32_t3_tmem_w32_r32x1_pf2", &fill_tmem_k32_t3_w32_r32x1_pf2, &launch_tmem_k32_t3_w32_r32x1_pf2},
+    Variant{2, 3, "k32_t3_ws_w32_r32x1_pf2", &fill_ws_k32_t3_w32_r32x1_pf2, &launch_ws_k32_t3_w32_r32x1_pf2},
+    Variant{2, 4, "k32_t4_tmem_w32_r32x1_pf2", &fill_tmem_k32_t4_w32_r32x1_pf2, &launch_tmem_k32_t4_w32_r32x1_pf2},
     TDSE_VARIANT(0, 1, "f64_t1_w64_r16x2_pf1_b2", double, 2, 32, 16, 2, false, 1, 2),
     TDSE_VARIANT(0, 1, "f64_t1_w64_r16x1_pf2", double, 2, 32, 16, 1, false, 2),
 };

@@ -693,6 +693,14 @@ TDSE_TMEM_VARIANT(tmem_k32_t2_w32_r28x1_pf2_b2, float, 4, 8, 28, 1, true, 2, 2, 
 TDSE_TMEM_VARIANT(tmem_k32_t2_w32_r32x1_pf2_b2, float, 4, 8, 32, 1, true, 2, 2, true)
 TDSE_TMEM_VARIANT(tmem_f32_t2_w32_r32x1_pf4_b2, float, 4, 8, 32, 1, false, 4, 2, true)
 TDSE_TMEM_VARIANT(tmem_f32_t2_w32_r32x1_pf3_b2, float, 4, 8, 32, 1, false, 3, 2, true)
+// three and four steps per launch (H = 6, 8): the windows of 5 or 7 intermediate
+// fields fill tensor memory, so one CTA per SM
+TDSE_TMEM_VARIANT(tmem_k32_t3_w32_r32x1_pf2, float, 6, 8, 32, 1, true, 2, 1, true)
+TDSE_TMEM_VARIANT(tmem_k32_t4_w32_r32x1_pf2, float, 8, 8, 32, 1, true, 2, 1, true)
+TDSE_TMEM_VARIANT(tmem_f32_t3_r32x1_pf2, float, 6, 16, 32, 1, false, 2, 1, true)
+TDSE_TMEM_VARIANT(tmem_f32_t4_w32_r40x1_pf2, float, 8, 8, 40, 1, false, 2, 1, true)
+TDSE_TMEM_WS_VARIANT(ws_k32_t3_w32_r32x1_pf2, float, 6, 8, 32, 1, true, 2, 1, true)
+TDSE_TMEM_WS_VARIANT(ws_f32_t3_r32x1_pf2, float, 6, 16, 32, 1, false, 2, 1, true)
 // producer warp + neighbour barriers
 TDSE_TMEM_WS_VARIANT(ws_k32_t2_w32_r32x1_pf2_b2, float, 4, 8, 32, 1, true, 2, 2, true)
 TDSE_TMEM_WS_VARIANT(ws_k32_t2_r32x1_pf2, float, 4, 16, 32, 1, true, 2, 1, true)

@@ -138,10 +138,11 @@ def test_wait_limit_rejects_negative(T):
 
 
 def test_divergence_ends_the_call_at_the_failing_observation(T):
-    """dt |V| = 12, far beyond the leapfrog's bound of 2: Q grows without bound.  A
-    request of a million steps ends at most two observation intervals after the
-    first observation point whose Q is non-finite or above (1 + 1e-3) Q0 (the one
-    the message names), not after all requested steps."""
+    """dt |V| = 12, far beyond the leapfrog's bound of 2: the state grows without
+    bound.  A request of a million steps ends at most two observation intervals
+    after the first observation point that fails the reduction's check (Q or E not
+    finite, or Q above (1 + 1e-3) Q0 when Q0 > 0; here Q0 < 0, so the run is caught
+    when it overflows), the point the message names, not after all requested steps."""
     import re
     from paper_2401_07416_gb300.sim import Sim
     g = W.small_grid(16, 16, 16, h=(0.2, 0.2, 0.2), dt=0.004, bc=(1, 1, 1))
@@ -154,7 +155,8 @@ def test_divergence_ends_the_call_at_the_failing_observation(T):
         named = int(re.search(r"observation of step (\d+)", str(e.value)).group(1))
         hist = s.history(0)                      # rows (step, Q, paper norm, energy)
         q0 = hist[0, 1]
-        bad = [int(r[0]) for r in hist if not np.isfinite(r[1]) or r[1] > (1 + 1e-3) * q0]
+        bad = [int(r[0]) for r in hist
+               if not (np.isfinite(r[1]) and np.isfinite(r[3])) or (q0 > 0 and r[1] > (1 + 1e-3) * q0)]
         assert bad and bad[0] == named, (bad[:3], named)
         end = s.observables(0)["step"]
         assert named <= end <= named + 2 * g.obs_every, (named, end)

@@ -114,7 +114,7 @@ def test_fp64_matches_oracle(T, name):
 
 
 @pytest.mark.parametrize("precision", ["FP32", "FP32_KAHAN"])
-@pytest.mark.parametrize("tblock", [1, 2])
+@pytest.mark.parametrize("tblock", [1, 2, 3, 4])
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp32_matches_oracle(T, name, precision, tblock):
     g, V, p = case(name, seed=1)
@@ -133,10 +133,11 @@ def test_fp32_matches_oracle(T, name, precision, tblock):
 
 
 @pytest.mark.parametrize("precision", ["FP32", "FP32_KAHAN"])
+@pytest.mark.parametrize("tblock", [2, 3, 4])
 @pytest.mark.parametrize("name", ["slab", "mixed"])
-def test_fused_two_steps_bitwise_equal_to_one_step_launches(T, name, precision):
+def test_fused_steps_bitwise_equal_to_one_step_launches(T, name, precision, tblock):
     g, V, p = case(name, seed=2)
-    a = gpu_run(g, V, p, 18, getattr(T, precision), tblock=2)
+    a = gpu_run(g, V, p, 18, getattr(T, precision), tblock=tblock)
     b = gpu_run(g, V, p, 18, getattr(T, precision), tblock=1)
     for x, y in zip(a[1], b[1]):
         assert np.array_equal(x, y)
@@ -258,15 +259,18 @@ def test_unstable_run_reports_status(T):
 
 @pytest.mark.parametrize("precision", ["FP32", "FP32_KAHAN"])
 @pytest.mark.parametrize("name", ["walls", "mixed", "short", "minimal", "thin"])
-def test_every_two_step_variant_bitwise_equal(T, name, precision):
-    """Register-window and tensor-memory-window kernels, every tile shape: the same
-    arithmetic in the same order, so states and flux maps agree bit for bit."""
+def test_every_fused_variant_bitwise_equal(T, name, precision):
+    """Register-window and tensor-memory-window kernels, with a CTA barrier per
+    plane or a producer warp and neighbour barriers, every tile shape and fused
+    depth: the same arithmetic in the same order, so states and flux maps agree bit
+    for bit with one-step launches."""
     g, V, p = case(name, seed=5)
     prec = getattr(T, precision)
     ref = None
-    for v in range(T.tdse_variant_count(prec, 2)):
-        s = make_sim(g, prec, 2)
-        T.tdse_set_variant(s.ctx, 2, v)
+    runs = [(1, 0)] + [(tb, v) for tb in (2, 3, 4) for v in range(T.tdse_variant_count(prec, tb))]
+    for tb, v in runs:
+        s = make_sim(g, prec, tb)
+        T.tdse_set_variant(s.ctx, tb, v)
         s.set_potential(0, V)
         s.set_packet(0, p)
         s.step(14)
@@ -276,7 +280,7 @@ def test_every_two_step_variant_bitwise_equal(T, name, precision):
             ref = got
             continue
         for a, b in zip(got, ref):
-            assert np.array_equal(a, b), (name, precision, v)
+            assert np.array_equal(a, b), (name, precision, tb, v)
 
 
 @pytest.mark.parametrize("precision", ["FP64", "FP32_KAHAN"])
