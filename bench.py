@@ -486,30 +486,73 @@ def dissimilarity_cost(torch, T, K=48, M=100, ny=128, nx=128):
 
 def adjoint_cost(torch, T):
     """96x96x192, 3000 steps: forward with FP64 checkpoints every 100 steps, then the
-    adjoint of the detector-flux loss (dL/dV and the 32 atoms)."""
+    adjoint of the detector-flux loss (dL/dV and the 32 atoms), with the fused
+    backward step (default) and with the three in-place passes; wall time of each
+    call and, from the library's profile, device time of the backward steps."""
     from paper_2401_07416_gb300.sim import Sim
     out = {}
     for prec in (W.FP32_KAHAN, W.FP64):
         wl = W.config4(prec)
         g = wl.grid
-        with Sim(g, precision=prec, ckpt_every=100) as s:
-            s.set_atoms(0, wl.atoms)
-            s.set_packet(0, wl.packet)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s.step(wl.steps)
-            torch.cuda.synchronize()
-            t_fwd = time.perf_counter() - t0
-            gF = 2 * s.flux_map(0)
-            gV = np.zeros((g.nz, g.ny, g.nx))
-            ga = np.zeros_like(wl.atoms)
-            t0 = time.perf_counter()
-            T.tdse_adjoint(s.ctx, 0, gF, gV, ga)
-            t_adj = time.perf_counter() - t0
-        out[PREC_NAME[prec]] = {"forward_s": t_fwd, "adjoint_s": t_adj,
-                                "adjoint_over_forward": t_adj / t_fwd,
-                                "adjoint_cell_steps_per_s": g.cells * wl.steps / t_adj}
+        for fused in (True, False):
+            with Sim(g, precision=prec, ckpt_every=100) as s:
+                s.set_atoms(0, wl.atoms)
+                s.set_packet(0, wl.packet)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.step(wl.steps)
+                torch.cuda.synchronize()
+                t_fwd = time.perf_counter() - t0
+                gF = 2 * s.flux_map(0)
+                gV = np.zeros((g.nz, g.ny, g.nx))
+                ga = np.zeros_like(wl.atoms)
+                T.tdse_set_adjoint_fused(s.ctx, fused)
+                T.tdse_set_profiling(s.ctx, True)
+                t0 = time.perf_counter()
+                T.tdse_adjoint(s.ctx, 0, gF, gV, ga)
+                t_adj = time.perf_counter() - t0
+                prof = T.tdse_get_profile(s.ctx)
+            key = PREC_NAME[prec] + ("" if fused else "_three_pass")
+            out[key] = {"forward_s": t_fwd, "adjoint_s": t_adj, "adjoint_over_forward": t_adj / t_fwd,
+                        "adjoint_cell_steps_per_s": g.cells * wl.steps / t_adj,
+                        "backward_step_us": prof["adjoint_ms"] * 1e3 / max(1, prof["adjoint_steps"]),
+                        "backward_steps": prof["adjoint_steps"]}
+    out["fused_256x256x512"] = adjoint_roofline(torch, T)
     return out
+
+
+def adjoint_roofline(torch, T, steps=200):
+    """The fused backward step on a grid larger than L2 (256x256x512, the 512^3
+    workload's spacing, FP32 + Kahan context, checkpoints every 100 steps): device
+    time per backward step from the library's profile against its algorithmic bytes
+    (R, I, P, Q and d read, R, I, P, Q written, FP32; dL/dV read and written, FP64:
+    52 B per node), and the forward step's time per step on the same grid."""
+    from paper_2401_07416_gb300.sim import Sim
+    g = W.Grid(nx=256, ny=256, nz=512, hx=0.05, hy=0.05, hz=0.05, dt=5e-4, mask_lo=20,
+               mask_hi=20, det_k=180, obs_every=20)
+    atoms = W.square_slab(8, 4, 1.6, 0.4 * 25.6, 12.8, 12.8, W.rng_for(5), 0.05)
+    packet = W.Packet((6.4, 6.4, 12.74), (0.0, 0.0, 2.0), (0.0, 0.0, -1.9))
+    peak = measured_peaks()[0]
+    with Sim(g, precision=W.FP32_KAHAN, tblock=2, ckpt_every=100) as s:
+        s.set_atoms(0, atoms)
+        s.set_packet(0, packet)
+        T.tdse_set_profiling(s.ctx, True)
+        s.step(steps)
+        pf = T.tdse_get_profile(s.ctx)
+        fwd_ms_per_step = pf["step_ms"] / steps
+        gF = 2 * s.flux_map(0)
+        T.tdse_set_profiling(s.ctx, False)
+        T.tdse_set_profiling(s.ctx, True)
+        T.tdse_adjoint(s.ctx, 0, gF, None, None)
+        pa = T.tdse_get_profile(s.ctx)
+    ms = pa["adjoint_ms"] / max(1, pa["adjoint_steps"])
+    bytes_step = 52 * g.cells
+    achieved = bytes_step / (ms * 1e-3) / 1e9
+    return {"nodes": g.cells, "steps": steps, "backward_step_ms": ms,
+            "forward_step_ms": fwd_ms_per_step, "adjoint_over_forward_device": ms / fwd_ms_per_step,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "bytes_per_node": 52,
+                         "kernel": "adj_fused_kernel<float> (one z-march per backward step)"}}
 
 
 def adjoint_case(args):

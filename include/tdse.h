@@ -261,6 +261,13 @@ TDSE_API tdse_status tdse_dissimilarity(const double *frames, int K, int M, long
 TDSE_API tdse_status tdse_adjoint(tdse_ctx *ctx, int member, const double *dL_dF, double *dL_dV,
                          double *dL_datoms, int on_device);
 
+/* Form of tdse_adjoint's backward step: enable != 0 (the default) runs each step as
+ * one z-march over tiles that reads the reconstructed state and its adjoint from
+ * one set of buffers and writes the next into a second set (four more arrays of
+ * the grid's size); 0 runs three passes in place.  Both give the same numbers
+ * (the per-cell arithmetic is shared). */
+TDSE_API tdse_status tdse_set_adjoint_fused(tdse_ctx *ctx, int enable);
+
 /* Save / restore the whole context state to / from a binary file: for every
  * member its parameters, the raw state fields (R, I and, in Kahan mode, their
  * compensation terms, each stored exactly as FP64), V, the flux integral and last flux,
@@ -280,8 +287,9 @@ TDSE_API tdse_status tdse_load_state(tdse_ctx *ctx, const char *path);
  * evenly over its launches; any other sequence is issued as direct launches,
  * each bracketed by its own events.  tdse_get_profile returns, since the last
  * reset, the launches and device milliseconds of the step kernels (in total and
- * per fused depth T) and of the reduction kernels, and the grid nodes per step
- * launch (all members). */
+ * per fused depth T) and of the reduction kernels, the grid nodes per step
+ * launch (all members), and the backward steps of tdse_adjoint with their device
+ * time (each checkpoint segment timed as a whole). */
 typedef struct tdse_profile {
     long long step_launches;        /* fused-step launches, every depth */
     double step_ms;                 /* their device time */
@@ -292,6 +300,8 @@ typedef struct tdse_profile {
     int reserved;
     long long launches_at_depth[TDSE_MAX_TBLOCK + 1];   /* [T]: launches fusing T steps */
     double ms_at_depth[TDSE_MAX_TBLOCK + 1];            /* [T]: their device time */
+    long long adjoint_steps;        /* backward steps of tdse_adjoint */
+    double adjoint_ms;              /* their device time (checkpoint reloads excluded) */
 } tdse_profile;
 TDSE_API tdse_status tdse_set_profiling(tdse_ctx *ctx, int enable);
 TDSE_API tdse_status tdse_get_profile(tdse_ctx *ctx, tdse_profile *out);

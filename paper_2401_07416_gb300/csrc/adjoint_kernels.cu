@@ -18,6 +18,7 @@
 // FP64.  Arrays are unpadded [nz][ny][nx]; neighbours wrap on periodic axes and read
 // zero on walls.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "tdse_internal.cuh"
@@ -113,6 +114,22 @@ __device__ __forceinline__ Real plane_factor(const Real *__restrict__ sc, const 
     return sc[z];
 }
 
+// Rounded products the compiler may not fuse into a following add: the three-pass
+// and the fused step must round every operation identically.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+
+// A f at one cell from its (already scaled) operands: cx (f[x+1] + f[x-1]) + cy (..) +
+// cz (..) + d f as one FMA chain.  Both the three-pass and the fused backward step
+// use this, and the explicit updates below, so they round identically.
+template <typename Real>
+__device__ __forceinline__ Real stencil(const Geo &g, Real xm, Real xp, Real ym, Real yp, Real zm,
+                                        Real zp, Real c, Real d)
+{
+    return fma(static_cast<Real>(g.cx), xp + xm,
+               fma(static_cast<Real>(g.cy), yp + ym, fma(static_cast<Real>(g.cz), zp + zm, rmul(d, c))));
+}
+
 // out = A (s f) at the kCells cells (x0 + k, y, z), cell offset o of x0; s a per-plane
 // factor (NULL: 1).  Per cell: every operand scaled by its plane's factor, then
 // cx (f[x+1] + f[x-1]) + cy (..) + cz (..) + d f as one FMA chain.
@@ -144,16 +161,15 @@ __device__ __forceinline__ void apply_A4(const Real *__restrict__ f, const Real 
         Real xp = k == kCells - 1 ? xr : c[k + 1];
         Real y0 = ym[k], y1 = yp[k], z0 = zm[k], z1 = zp[k], cc = c[k];
         if (sc) {
-            xm *= s0;
-            xp *= s0;
-            y0 *= s0;
-            y1 *= s0;
-            cc *= s0;
-            z0 *= sm;
-            z1 *= sp;
+            xm = rmul(xm, s0);
+            xp = rmul(xp, s0);
+            y0 = rmul(y0, s0);
+            y1 = rmul(y1, s0);
+            cc = rmul(cc, s0);
+            z0 = rmul(z0, sm);
+            z1 = rmul(z1, sp);
         }
-        out[k] = fma(static_cast<Real>(g.cx), xp + xm,
-                     fma(static_cast<Real>(g.cy), y1 + y0, fma(static_cast<Real>(g.cz), z1 + z0, d[k] * cc)));
+        out[k] = stencil(g, xm, xp, y0, y1, z0, z1, cc, d[k]);
     }
 }
 
@@ -188,8 +204,8 @@ __global__ void adj_b_kernel(Geo g, const Real *__restrict__ Mk, const Real *__r
         const Real mi = Mi[z], mk = Mk[z];
 #pragma unroll
         for (int k = 0; k < kCells; ++k) {
-            r[k] = r[k] * mi + ai[k];
-            q[k] = q[k] * mk - ap[k];
+            r[k] = fma(r[k], mi, ai[k]);
+            q[k] = fma(q[k], mk, -ap[k]);
         }
         st4(R + o, r);
         st4(Q + o, q);
@@ -208,11 +224,25 @@ __global__ void adj_flux_q_kernel(Geo g, int kd, const double *__restrict__ w,
     GRID_STRIDE(p, plane)
     {
         const Real wp = static_cast<Real>(w[p]);
-        Ist[p] = I[kd * plane + p] * Mi[kd];
-        Ist[plane + p] = I[(kd + 1) * plane + p] * Mi[kd + 1];
-        Q[(kd + 1) * plane + p] += wp * R[kd * plane + p];
-        Q[kd * plane + p] -= wp * R[(kd + 1) * plane + p];
+        Ist[p] = rmul(I[kd * plane + p], Mi[kd]);
+        Ist[plane + p] = rmul(I[(kd + 1) * plane + p], Mi[kd + 1]);
+        Q[(kd + 1) * plane + p] = fma(wp, R[kd * plane + p], Q[(kd + 1) * plane + p]);
+        Q[kd * plane + p] = fma(-wp, R[(kd + 1) * plane + p], Q[kd * plane + p]);
     }
+}
+
+// Steps d and e at one cell: Pt = M P, It = I' / M, gV -= cv (Qt R - Pt It),
+// P = Pt + A Qt (before the detector terms), I = It - A R.
+template <typename Real>
+__device__ __forceinline__ void de_cell(const Geo &g, Real p, Real i, Real qt, Real r, Real mk,
+                                        Real mi, Real aq, Real ar, double &gv, Real &pn, Real &in)
+{
+    const Real pt = rmul(p, mk);
+    const Real it = rmul(i, mi);
+    const Real ptit = rmul(pt, it);
+    gv = fma(-g.cv, static_cast<double>(fma(qt, r, -ptit)), gv);
+    pn = pt + aq;
+    in = it - ar;
 }
 
 // d and e in one pass, with Pt = M P and It = I' / M at the plane:
@@ -248,17 +278,14 @@ __global__ void adj_de_kernel(Geo g, const Real *__restrict__ Mk, const Real *__
         ld4(gV + o, gv);
 #pragma unroll
         for (int k = 0; k < kCells; ++k) {
-            const Real pt = pp[k] * mk;
-            const Real it = ii[k] * mi;
-            const Real v = q[k] * r[k] - pt * it;
-            gv[k] -= g.cv * static_cast<double>(v);
-            Real pn = pt + aq[k];
+            Real pn, in;
+            de_cell(g, pp[k], ii[k], q[k], r[k], mk, mi, aq[k], ar[k], gv[k], pn, in);
             if (kd >= 0) {
-                if (z == kd) pn += static_cast<Real>(w[xy + k]) * Ist[plane + xy + k];
-                else if (z == kd + 1) pn -= static_cast<Real>(w[xy + k]) * Ist[xy + k];
+                if (z == kd) pn = fma(static_cast<Real>(w[xy + k]), Ist[plane + xy + k], pn);
+                else if (z == kd + 1) pn = fma(-static_cast<Real>(w[xy + k]), Ist[xy + k], pn);
             }
             pp[k] = pn;
-            ii[k] = it - ar[k];
+            ii[k] = in;
         }
         st4(gV + o, gv);
         st4(P + o, pp);
@@ -286,6 +313,214 @@ __global__ void flux_weight_kernel(long long npix, const double *__restrict__ gF
                                    double *w)
 {
     GRID_STRIDE(t, npix) w[t] = gF[t] * scale;
+}
+
+// ---------------------------------------------------------------- fused backward step
+//
+// Steps a-e above in one z-march per backward step.  A block owns a kTX x kTY tile of
+// cells and a chunk [z0, z1) of planes, and keeps rings of planes in shared memory:
+//   old I and P on the tile plus two cells (planes b-3 .. b+1),
+//   old R and Q on the tile plus one cell (plane b), d on the tile plus one (b-2 .. b),
+//   new R and Qt on the tile plus one cell (b-3 .. b).
+// Iteration b: load I, P at plane b+1 and R, Q, d at plane b; step b at plane b on
+// the tile plus one cell; the detector terms of step c once the new R of planes kd and
+// kd+1 exist; steps d and e at plane q = b - 2 on the tile, written out.  Step b runs
+// on planes [z0 - 2, z1 + 2), so the chunk's own rings hold every stencil operand of
+// its planes (the one-cell ring of new R and Qt is recomputed by each tile that
+// reads it), and every step reads one buffer set and writes the other: blocks never
+// read what another block writes within a step.  Per cell and step it moves the
+// fields once: R, I, P, Q, d and gV in, R, I, P, Q and gV out.
+constexpr int kTX = 32, kTY = 8;                         // tile (one cell per thread)
+constexpr int kW1 = kTX + 2, kH1 = kTY + 2, kA1 = kW1 * kH1;   // tile plus one cell
+constexpr int kW2 = kTX + 4, kH2 = kTY + 4, kA2 = kW2 * kH2;   // tile plus two cells
+constexpr int kRingIP = 5, kRingRQ = 4, kRingD = 3;
+
+template <typename Real>
+constexpr size_t fused_smem_bytes()
+{
+    return sizeof(Real) * (2 * kRingIP * kA2 + (2 + kRingD + 2 * kRingRQ) * kA1);
+}
+
+struct FusedArgs {
+    Geo g;
+    int kd;
+    int tiles_x, tiles_y, chunk;
+    const double *w;          // dL/dF dt cj per pixel
+    const void *Mk, *Mi;      // absorbing factor per plane and its reciprocal
+    const void *D;            // d of the forward step (padded)
+    const void *R, *I, *P, *Q;     // state and adjoints read by this step
+    void *Ro, *Io, *Po, *Qo;       // ... written by this step
+    double *gV;
+};
+
+// A coordinate one of the grid's axes: the periodic image, or -1 beyond a wall.
+__device__ __forceinline__ int wrap_axis(int v, int n, int per)
+{
+    if (v >= 0 && v < n) return v;
+    if (!per) return -1;
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real plane_factor_any(const Real *__restrict__ sc, const Geo &g, int z)
+{
+    const int zz = wrap_axis(z, g.nz, g.per[2]);
+    return zz < 0 ? Real(1) : sc[zz];
+}
+
+// Region of w x h cells at global (ox, oy) of plane z of an unpadded field into dst.
+template <typename Real>
+__device__ __forceinline__ void load_region(Real *__restrict__ dst, const Real *__restrict__ f,
+                                            const Geo &g, int ox, int oy, int z, int w, int h)
+{
+    const int zz = wrap_axis(z, g.nz, g.per[2]);
+    for (int t = threadIdx.x; t < w * h; t += blockDim.x) {
+        const int i = t % w, j = t / w;
+        const int x = wrap_axis(ox + i, g.nx, g.per[0]), y = wrap_axis(oy + j, g.ny, g.per[1]);
+        dst[t] = (zz < 0 || x < 0 || y < 0) ? Real(0) : f[cell(g, x, y, zz)];
+    }
+}
+
+// The same for d, read from the forward step's padded array.
+template <typename Real>
+__device__ __forceinline__ void load_region_d(Real *__restrict__ dst, const Real *__restrict__ D,
+                                              const Geo &g, int ox, int oy, int z, int w, int h)
+{
+    const int zz = wrap_axis(z, g.nz, g.per[2]);
+    for (int t = threadIdx.x; t < w * h; t += blockDim.x) {
+        const int i = t % w, j = t / w;
+        const int x = wrap_axis(ox + i, g.nx, g.per[0]), y = wrap_axis(oy + j, g.ny, g.per[1]);
+        dst[t] = (zz < 0 || x < 0 || y < 0)
+                     ? Real(0)
+                     : D[static_cast<long long>(zz) * g.pplane + static_cast<long long>(y + g.G) * g.pitch +
+                         (x + g.G)];
+    }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kTX * kTY) adj_fused_kernel(FusedArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    Real *sI = reinterpret_cast<Real *>(smem_raw);     // [kRingIP][kA2]
+    Real *sP = sI + kRingIP * kA2;                     // [kRingIP][kA2]
+    Real *sR = sP + kRingIP * kA2;                     // [kA1]
+    Real *sQ = sR + kA1;                               // [kA1]
+    Real *sD = sQ + kA1;                               // [kRingD][kA1]
+    Real *sRn = sD + kRingD * kA1;                     // [kRingRQ][kA1]
+    Real *sQt = sRn + kRingRQ * kA1;                   // [kRingRQ][kA1]
+
+    const Geo &g = a.g;
+    const int tiles = a.tiles_x * a.tiles_y;
+    const int tile = blockIdx.x % tiles, chunk = blockIdx.x / tiles;
+    const int x0 = (tile % a.tiles_x) * kTX, y0 = (tile / a.tiles_x) * kTY;
+    const int z0 = chunk * a.chunk, z1 = min(z0 + a.chunk, g.nz);
+    const Real *Mk = static_cast<const Real *>(a.Mk), *Mi = static_cast<const Real *>(a.Mi);
+    const Real *D = static_cast<const Real *>(a.D);
+    const Real *Rg = static_cast<const Real *>(a.R), *Ig = static_cast<const Real *>(a.I);
+    const Real *Pg = static_cast<const Real *>(a.P), *Qg = static_cast<const Real *>(a.Q);
+    const int kd = a.kd;
+    auto ring = [](int z, int n) { return ((z % n) + n) % n; };
+
+    // this thread's cell for steps d and e
+    const int ti = threadIdx.x % kTX, tj = threadIdx.x / kTX;
+    const int cx = x0 + ti, cy = y0 + tj;
+    const bool own = cx < g.nx && cy < g.ny;
+    const int c1 = (tj + 1) * kW1 + (ti + 1);     // its index in the one-cell regions
+    const int c2 = (tj + 2) * kW2 + (ti + 2);     // ... and in the two-cell regions
+
+    for (int z = z0 - 3; z <= z0 - 2; ++z) {      // the first planes of I and P
+        load_region(sI + ring(z, kRingIP) * kA2, Ig, g, x0 - 2, y0 - 2, z, kW2, kH2);
+        load_region(sP + ring(z, kRingIP) * kA2, Pg, g, x0 - 2, y0 - 2, z, kW2, kH2);
+    }
+    for (int b = z0 - 2; b <= z1 + 1; ++b) {
+        __syncthreads();   // the previous iteration's reads of the slots reloaded now are done
+        load_region(sI + ring(b + 1, kRingIP) * kA2, Ig, g, x0 - 2, y0 - 2, b + 1, kW2, kH2);
+        load_region(sP + ring(b + 1, kRingIP) * kA2, Pg, g, x0 - 2, y0 - 2, b + 1, kW2, kH2);
+        load_region(sR, Rg, g, x0 - 1, y0 - 1, b, kW1, kH1);
+        load_region(sQ, Qg, g, x0 - 1, y0 - 1, b, kW1, kH1);
+        load_region_d(sD + ring(b, kRingD) * kA1, D, g, x0 - 1, y0 - 1, b, kW1, kH1);
+        __syncthreads();
+        // b. undo Eq. 8 and its adjoint at plane b on the tile plus one cell
+        {
+            const Real mi0 = plane_factor_any(Mi, g, b), mim = plane_factor_any(Mi, g, b - 1),
+                       mip = plane_factor_any(Mi, g, b + 1);
+            const Real mk0 = plane_factor_any(Mk, g, b), mkm = plane_factor_any(Mk, g, b - 1),
+                       mkp = plane_factor_any(Mk, g, b + 1);
+            const Real *I0 = sI + ring(b, kRingIP) * kA2, *Im = sI + ring(b - 1, kRingIP) * kA2,
+                       *Ip = sI + ring(b + 1, kRingIP) * kA2;
+            const Real *P0 = sP + ring(b, kRingIP) * kA2, *Pm = sP + ring(b - 1, kRingIP) * kA2,
+                       *Pp = sP + ring(b + 1, kRingIP) * kA2;
+            const Real *d0 = sD + ring(b, kRingD) * kA1;
+            Real *Rn = sRn + ring(b, kRingRQ) * kA1, *Qt = sQt + ring(b, kRingRQ) * kA1;
+            const bool zin = wrap_axis(b, g.nz, g.per[2]) >= 0;
+            for (int t = threadIdx.x; t < kA1; t += blockDim.x) {
+                const int i = t % kW1, j = t / kW1;
+                const int k = (j + 1) * kW2 + (i + 1);     // same cell in the two-cell regions
+                // beyond a wall the new R and Qt are zero, like every field there
+                if (!zin || wrap_axis(x0 - 1 + i, g.nx, g.per[0]) < 0 || wrap_axis(y0 - 1 + j, g.ny, g.per[1]) < 0) {
+                    Rn[t] = Real(0);
+                    Qt[t] = Real(0);
+                    continue;
+                }
+                const Real ai = stencil(g, rmul(I0[k - 1], mi0), rmul(I0[k + 1], mi0), rmul(I0[k - kW2], mi0),
+                                        rmul(I0[k + kW2], mi0), rmul(Im[k], mim), rmul(Ip[k], mip),
+                                        rmul(I0[k], mi0), d0[t]);
+                const Real ap = stencil(g, rmul(P0[k - 1], mk0), rmul(P0[k + 1], mk0), rmul(P0[k - kW2], mk0),
+                                        rmul(P0[k + kW2], mk0), rmul(Pm[k], mkm), rmul(Pp[k], mkp),
+                                        rmul(P0[k], mk0), d0[t]);
+                Rn[t] = fma(sR[t], mi0, ai);
+                Qt[t] = fma(sQ[t], mk0, -ap);
+            }
+        }
+        // c. the detector terms, once the new R of planes kd and kd + 1 exist (the
+        // stencils of d and e below read only planes written before this iteration,
+        // so only then is a barrier needed between the two)
+        if (kd >= 0 && b == kd + 1 && b - 1 >= z0 - 2) {
+            __syncthreads();
+            Real *Qlo = sQt + ring(kd, kRingRQ) * kA1, *Qhi = sQt + ring(kd + 1, kRingRQ) * kA1;
+            const Real *Rlo = sRn + ring(kd, kRingRQ) * kA1, *Rhi = sRn + ring(kd + 1, kRingRQ) * kA1;
+            for (int t = threadIdx.x; t < kA1; t += blockDim.x) {
+                const int x = wrap_axis(x0 - 1 + t % kW1, g.nx, g.per[0]);
+                const int y = wrap_axis(y0 - 1 + t / kW1, g.ny, g.per[1]);
+                if (x < 0 || y < 0) continue;
+                const Real wp = static_cast<Real>(a.w[y * g.nx + x]);
+                Qhi[t] = fma(wp, Rlo[t], Qhi[t]);
+                Qlo[t] = fma(-wp, Rhi[t], Qlo[t]);
+            }
+            __syncthreads();
+        }
+        // d and e at plane q = b - 2 on the tile
+        const int q = b - 2;
+        if (q >= z0 && q < z1 && own) {
+            const Real *Qq = sQt + ring(q, kRingRQ) * kA1, *Qm = sQt + ring(q - 1, kRingRQ) * kA1,
+                       *Qp = sQt + ring(q + 1, kRingRQ) * kA1;
+            const Real *Rq = sRn + ring(q, kRingRQ) * kA1, *Rm = sRn + ring(q - 1, kRingRQ) * kA1,
+                       *Rp = sRn + ring(q + 1, kRingRQ) * kA1;
+            const Real dq = sD[ring(q, kRingD) * kA1 + c1];
+            const Real aq = stencil(g, Qq[c1 - 1], Qq[c1 + 1], Qq[c1 - kW1], Qq[c1 + kW1], Qm[c1], Qp[c1],
+                                    Qq[c1], dq);
+            const Real ar = stencil(g, Rq[c1 - 1], Rq[c1 + 1], Rq[c1 - kW1], Rq[c1 + kW1], Rm[c1], Rp[c1],
+                                    Rq[c1], dq);
+            const long long o = cell(g, cx, cy, q);
+            double gv = a.gV[o];
+            Real pn, in;
+            de_cell(g, sP[ring(q, kRingIP) * kA2 + c2], sI[ring(q, kRingIP) * kA2 + c2], Qq[c1], Rq[c1],
+                    Mk[q], Mi[q], aq, ar, gv, pn, in);
+            if (kd >= 0 && (q == kd || q == kd + 1)) {
+                const Real wp = static_cast<Real>(a.w[cy * g.nx + cx]);
+                if (q == kd)   // It of plane kd + 1
+                    pn = fma(wp, rmul(sI[ring(kd + 1, kRingIP) * kA2 + c2], Mi[kd + 1]), pn);
+                else           // It of plane kd
+                    pn = fma(-wp, rmul(sI[ring(kd, kRingIP) * kA2 + c2], Mi[kd]), pn);
+            }
+            a.gV[o] = gv;
+            static_cast<Real *>(a.Ro)[o] = Rq[c1];
+            static_cast<Real *>(a.Qo)[o] = Qq[c1];
+            static_cast<Real *>(a.Po)[o] = pn;
+            static_cast<Real *>(a.Io)[o] = in;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- atom chain rule
@@ -403,8 +638,47 @@ Geo make_geo(const MemberDev &m)
 }
 
 template <typename Real>
+cudaError_t fused_step_t(const MemberDev &m, const AdjointBuffers &b, cudaStream_t s)
+{
+    FusedArgs a;
+    a.g = make_geo(m);
+    a.kd = m.det_k;
+    a.tiles_x = (m.nx + kTX - 1) / kTX;
+    a.tiles_y = (m.ny + kTY - 1) / kTY;
+    // z-chunks: about four blocks per SM, at least 16 planes (each chunk recomputes
+    // step b on four extra planes)
+    const long long tiles = static_cast<long long>(a.tiles_x) * a.tiles_y;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long want = (4LL * sms + tiles - 1) / tiles;
+    a.chunk = static_cast<int>(std::max<long long>(16, (m.nz + want - 1) / want));
+    a.chunk = std::min(a.chunk, m.nz);
+    const long long chunks = (m.nz + a.chunk - 1) / a.chunk;
+    a.w = b.w;
+    a.Mk = m.mask;
+    a.Mi = b.Minv;
+    a.D = m.d;
+    a.R = b.R; a.I = b.I; a.P = b.P; a.Q = b.Q;
+    a.Ro = b.R2; a.Io = b.I2; a.Po = b.P2; a.Qo = b.Q2;
+    a.gV = b.gV;
+    static std::atomic<uint64_t> smem_allowed{0};   // one bit per device
+    const uint64_t bit = dev < 64 ? (uint64_t{1} << dev) : 0;
+    if (!(bit && (smem_allowed.load() & bit))) {
+        e = cudaFuncSetAttribute(adj_fused_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(fused_smem_bytes<Real>()));
+        if (e != cudaSuccess) return e;
+        if (bit) smem_allowed.fetch_or(bit);
+    }
+    adj_fused_kernel<Real><<<static_cast<unsigned>(tiles * chunks), kTX * kTY, fused_smem_bytes<Real>(), s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename Real>
 cudaError_t backward_step_t(const MemberDev &m, const AdjointBuffers &b, cudaStream_t s)
 {
+    if (b.R2) return fused_step_t<Real>(m, b, s);
     const Geo g = make_geo(m);
     const long long plane = static_cast<long long>(m.nx) * m.ny;
     // planes: one block row per plane up to 65535, then a plane-stride loop

@@ -84,12 +84,13 @@ struct tdse_ctx {
     std::vector<cudaEvent_t> event_pool;           // reused timing events
     struct Interval {
         int start, stop;                           // indices into event_pool
-        int kind;                                  // 0: step launches, 1: reductions
+        int kind;                                  // 0: step launches, 1: reductions, 2: backward steps
         int launches, depth;                       // step launches timed together, their depth
     };
     std::vector<Interval> pending;
     size_t events_used = 0;
     bool graphs = true;                            // replay step segments as CUDA graphs
+    bool adjoint_fused = true;                     // one z-march per backward step
     cudaStream_t gstream = nullptr;                // capture/replay stream
     cudaEvent_t gev[2] = {nullptr, nullptr};
     struct GraphEntry {
@@ -560,9 +561,12 @@ tdse_status resolve_timers(tdse_ctx *c)
                 c->prof.launches_at_depth[iv.depth] += iv.launches;
                 c->prof.ms_at_depth[iv.depth] += ms;
             }
-        } else {
+        } else if (iv.kind == 1) {
             c->prof.reduce_launches += 2 * static_cast<long long>(c->m.size());
             c->prof.reduce_ms += ms;
+        } else {
+            c->prof.adjoint_steps += iv.launches;
+            c->prof.adjoint_ms += ms;
         }
     }
     c->pending.clear();
@@ -1062,8 +1066,10 @@ tdse_status tdse_step(tdse_ctx *c, long long nsteps)
         if (c->step % c->obs_every == 0) {
             TRY(observe_all(c, nrec));
             for (size_t i = 0; i < c->m.size(); ++i) TRY(capture_frame(c, static_cast<int>(i)));
-            TRY(post_status(c));
-            if (++nrec == kRecCap) {
+            ++nrec;
+            // posting may wait for (and report) an earlier point's status
+            if ((st = post_status(c)) != TDSE_OK) break;
+            if (nrec == kRecCap) {
                 TRY(drain_records(c, nrec));
                 nrec = 0;
             }
@@ -1235,59 +1241,93 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
         for (void *p : tmp) dfree(c, p);
     };
     void *R, *I, *P, *Q, *gV, *w, *gF, *cur, *Ist;
+    void *R2 = nullptr, *I2 = nullptr, *P2 = nullptr, *Q2 = nullptr;
     tdse_status st = TDSE_OK;
     if ((st = alloc(cells * elem, &R)) || (st = alloc(cells * elem, &I)) ||
         (st = alloc(cells * elem, &P)) || (st = alloc(cells * elem, &Q)) ||
         (st = alloc(cells * 8, &gV)) || (st = alloc(npix * 8, &w)) || (st = alloc(npix * 8, &gF)) ||
-        (st = alloc(2 * cells * 8, &cur)) || (st = alloc(2 * npix * elem, &Ist))) {
+        (st = alloc(2 * cells * 8, &cur)) || (st = alloc(2 * npix * elem, &Ist)) ||
+        (c->adjoint_fused && ((st = alloc(cells * elem, &R2)) || (st = alloc(cells * elem, &I2)) ||
+                              (st = alloc(cells * elem, &P2)) || (st = alloc(cells * elem, &Q2))))) {
         cleanup();
         return st;
     }
-    AdjointBuffers b{R, I, P, Q, static_cast<double *>(gV), static_cast<double *>(w), mb.mask_inv,
-                     Ist, mb.V64};
-    // backward steps of one checkpoint segment, replayed from a CUDA graph per
-    // segment length (the buffers are this call's, so the graphs are too)
-    std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
-    auto back_steps = [&](long long nsteps) -> tdse_status {
+    const AdjointBuffers base{R, I, P, Q, R2, I2, P2, Q2, static_cast<double *>(gV),
+                              static_cast<double *>(w), mb.mask_inv, Ist, mb.V64};
+    // The fused step reads one buffer set and writes the other: `par` says which set
+    // holds the current state (the three-pass step works in place, par stays 0).
+    int par = 0;
+    auto view = [&]() {
+        AdjointBuffers v = base;
+        if (par) {
+            std::swap(v.R, v.R2);
+            std::swap(v.I, v.I2);
+            std::swap(v.P, v.P2);
+            std::swap(v.Q, v.Q2);
+        }
+        return v;
+    };
+    auto issue_step = [&](cudaStream_t s) -> cudaError_t {
+        const cudaError_t e = adjoint_backward_step(d, elem, view(), s);
+        if (base.R2) par ^= 1;
+        return e;
+    };
+    // backward steps of one checkpoint segment, replayed from a CUDA graph per segment
+    // length and starting buffer set (the buffers are this call's, so the graphs are too)
+    struct AdjGraph {
+        long long nsteps;
+        int par;
+        cudaGraphExec_t exec;
+    };
+    std::vector<AdjGraph> graphs;
+    auto back_steps_untimed = [&](long long nsteps) -> tdse_status {
         if (nsteps <= 0) return TDSE_OK;
         if (!c->graphs) {
-            for (long long k = 0; k < nsteps; ++k)
-                CUDA_TRY(c, adjoint_backward_step(d, elem, b, c->stream));
+            for (long long k = 0; k < nsteps; ++k) CUDA_TRY(c, issue_step(c->stream));
             return TDSE_OK;
         }
         TRY(ensure_gstream(c));
         cudaGraphExec_t exec = nullptr;
         for (auto &g : graphs)
-            if (g.first == nsteps) exec = g.second;
+            if (g.nsteps == nsteps && g.par == par) exec = g.exec;
+        const int par0 = par;
         if (!exec) {
             cudaGraph_t graph = nullptr;
             CUDA_TRY(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaSuccess;
-            for (long long k = 0; k < nsteps && e == cudaSuccess; ++k)
-                e = adjoint_backward_step(d, elem, b, c->gstream);
+            for (long long k = 0; k < nsteps && e == cudaSuccess; ++k) e = issue_step(c->gstream);
+            par = par0;
             const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &graph);
             if (e == cudaSuccess) e = e2;
             if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
             if (graph) cudaGraphDestroy(graph);
             if (e != cudaSuccess)
                 return fail(c, TDSE_ECUDA, "adjoint graph capture failed: %s", cudaGetErrorString(e));
-            graphs.push_back({nsteps, exec});
+            graphs.push_back({nsteps, par0, exec});
         }
-        return replay_graph(c, exec);
+        TRY(replay_graph(c, exec));
+        if (base.R2 && (nsteps & 1)) par ^= 1;
+        return TDSE_OK;
+    };
+    auto back_steps = [&](long long nsteps) -> tdse_status {
+        int t0 = -1;
+        TRY(timer_start(c, &t0));
+        TRY(back_steps_untimed(nsteps));
+        return timer_stop(c, t0, 2, static_cast<int>(nsteps), 0);
     };
     auto drop_graphs = [&]() {
-        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
         graphs.clear();
     };
     auto run = [&]() -> tdse_status {
         CUDA_TRY(c, cudaMemcpyAsync(gF, dL_dF, npix * 8,
                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     c->stream));
-        CUDA_TRY(c, adjoint_flux_weights(d, static_cast<double *>(gF), b.w, c->stream));
+        CUDA_TRY(c, adjoint_flux_weights(d, static_cast<double *>(gF), base.w, c->stream));
         // start from the latest state, then walk the checkpoints backwards
         double *cur64 = static_cast<double *>(cur);
         CUDA_TRY(c, launch_get_state(d, cur64, cur64 + cells, c->precision, c->cur, c->stream));
-        CUDA_TRY(c, adjoint_load_state(d, elem, b, cur64, cur64 + cells, c->stream));
+        CUDA_TRY(c, adjoint_load_state(d, elem, view(), cur64, cur64 + cells, c->stream));
         long long n = c->step;
         for (int k = static_cast<int>(mb.ckpts.size()) - 1; k >= 0; --k) {
             const long long n0 = mb.ckpts[k].first;
@@ -1295,10 +1335,10 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
             n = n0;
             // re-anchor the reconstructed forward state on the FP64 checkpoint
             const double *ck = mb.ckpts[k].second;
-            CUDA_TRY(c, adjoint_load_state(d, elem, b, ck, ck + cells, c->stream));
+            CUDA_TRY(c, adjoint_load_state(d, elem, view(), ck, ck + cells, c->stream));
         }
         if (mb.from_packet)
-            CUDA_TRY(c, adjoint_start_term(d, elem, b, mb.ckpts[0].second, c->stream));
+            CUDA_TRY(c, adjoint_start_term(d, elem, view(), mb.ckpts[0].second, c->stream));
         if (dL_dV)
             CUDA_TRY(c, cudaMemcpyAsync(dL_dV, gV, cells * 8,
                                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -1324,6 +1364,7 @@ tdse_status tdse_adjoint(tdse_ctx *c, int member, const double *dL_dF, double *d
     st = run();
     cleanup();
     drop_graphs();
+    if (st == TDSE_OK) st = resolve_timers(c);   // the stream is synchronised
     return st;
 }
 
@@ -1472,6 +1513,13 @@ tdse_status tdse_set_wait_limit(tdse_ctx *c, long long ns)
     if (ns < 0) return fail(c, TDSE_EINVAL, "negative wait limit");
     c->wait_ns = static_cast<unsigned long long>(ns);
     drop_graphs(c);   // captured launches carry the limit as an argument
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_adjoint_fused(tdse_ctx *c, int enable)
+{
+    if (!c) return TDSE_EINVAL;
+    c->adjoint_fused = enable != 0;
     return TDSE_OK;
 }
 

@@ -133,6 +133,8 @@ constexpr int kObsPartialsPerBlock = 5;   // Q, paper norm, energy, flux (last s
 struct AdjointBuffers {
     void *R, *I;          // forward state being reconstructed: R^n, I^{n-1/2}
     void *P, *Q;          // their adjoints
+    void *R2, *I2, *P2, *Q2;   // second set for the fused step, which reads one set and
+                               // writes the other (NULL: three passes in place)
     double *gV;           // dL/dV accumulator
     double *w;            // dL/dF * dt * cj per detector pixel
     const void *Minv;     // reciprocal of the absorbing factor per plane (the context's
@@ -140,6 +142,9 @@ struct AdjointBuffers {
     void *Ist;            // It of the two detector planes (2 nx ny values, that format)
     const double *V;      // potential (FP64)
 };
+// One backward step.  With a second buffer set, one fused z-march that reads (R, I, P,
+// Q) and writes (R2, I2, P2, Q2), after which the caller swaps the two sets; without,
+// three passes in place.
 cudaError_t adjoint_backward_step(const MemberDev &m, int elem, const AdjointBuffers &b,
                                   cudaStream_t s);
 cudaError_t adjoint_start_term(const MemberDev &m, int elem, const AdjointBuffers &b,

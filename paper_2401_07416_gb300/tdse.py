@@ -62,7 +62,8 @@ class Profile(ctypes.Structure):
                 ("cells_per_launch", ctypes.c_longlong), ("steps_per_launch", ctypes.c_int),
                 ("reserved", ctypes.c_int),
                 ("launches_at_depth", ctypes.c_longlong * (MAX_TBLOCK + 1)),
-                ("ms_at_depth", ctypes.c_double * (MAX_TBLOCK + 1))]
+                ("ms_at_depth", ctypes.c_double * (MAX_TBLOCK + 1)),
+                ("adjoint_steps", ctypes.c_longlong), ("adjoint_ms", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -104,6 +105,7 @@ SIGNATURES = {
     "tdse_get_tuning": (_I, [_VP, ctypes.POINTER(Tuning)]),
     "tdse_set_graphs": (_I, [_VP, _I]),
     "tdse_set_wait_limit": (_I, [_VP, _LL]),
+    "tdse_set_adjoint_fused": (_I, [_VP, _I]),
     "tdse_set_profiling": (_I, [_VP, _I]),
     "tdse_get_profile": (_I, [_VP, ctypes.POINTER(Profile)]),
     "tdse_observables_static": (_I, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP]),
@@ -355,6 +357,10 @@ def tdse_get_tuning(ctx) -> dict:
 
 def tdse_set_graphs(ctx, enable: bool):
     _check(ctx, lib().tdse_set_graphs(ctx, int(bool(enable))))
+
+
+def tdse_set_adjoint_fused(ctx, enable: bool):
+    _check(ctx, lib().tdse_set_adjoint_fused(ctx, int(bool(enable))))
 
 
 def tdse_set_wait_limit(ctx, ns: int):

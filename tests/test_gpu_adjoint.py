@@ -68,6 +68,54 @@ def test_fp64_adjoint_matches_oracle(T):
     assert np.abs(ga - ga_o).max() <= 1e-9 * np.abs(ga_o).max()
 
 
+ADJ_CASES = {
+    # (nx, ny, nz, bc, mask, det_k, atoms): ragged 32 x 8 tiles, several z-chunks, the
+    # detector faces at a chunk boundary and at the top plane, a periodic z axis
+    "walls": (8, 8, 24, (0, 0, 1), 4, 6),
+    "chunks": (36, 20, 48, (0, 0, 1), 5, 15),
+    "zper": (12, 10, 40, (1, 0, 0), 0, 38),
+    "wallxy": (20, 12, 36, (1, 1, 1), 3, 16),
+}
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32", "FP32_KAHAN"])
+@pytest.mark.parametrize("name", list(ADJ_CASES))
+def test_fused_adjoint_step_equals_three_passes(T, name, precision):
+    """The fused backward step (one z-march over tiles, two buffer sets) and the
+    three in-place passes share their per-cell arithmetic: dL/dV and the atom
+    gradient agree bit for bit, and the FP64 form matches the oracle."""
+    from paper_2401_07416_gb300.sim import Sim
+    nx, ny, nz, bc, mask, kd = ADJ_CASES[name]
+    g = W.small_grid(nx, ny, nz, h=(0.25, 0.22, 0.24), dt=0.004, bc=bc, det_k=kd, mask=mask, eta=0.5)
+    L = g.lengths
+    atoms = np.array([[0.3 * L[0], 0.4 * L[1], 0.5 * L[2], 6.0], [0.7 * L[0], 0.2 * L[1], 0.45 * L[2], 8.0]])
+    p = W.Packet((0.5 * L[0], 0.5 * L[1], 0.6 * L[2]), (0.0, 0.0, 0.7), (0.0, 0.0, -2.5))
+    prec = getattr(T, precision)
+    n = 37
+    rng = np.random.default_rng(7)
+    out = {}
+    for fused in (True, False):
+        with Sim(g, precision=prec, ckpt_every=10) as s:
+            s.set_atoms(0, atoms)
+            s.set_packet(0, p)
+            s.step(n)
+            gF = rng.normal(size=(ny, nx)) if not out else out["gF"]
+            gV = np.zeros((nz, ny, nx))
+            ga = np.zeros_like(atoms)
+            T.tdse_set_adjoint_fused(s.ctx, fused)
+            T.tdse_adjoint(s.ctx, 0, gF, gV, ga)
+        out.setdefault("gF", gF)
+        out[fused] = (gV, ga)
+    assert np.array_equal(out[True][0], out[False][0]), name
+    assert np.array_equal(out[True][1], out[False][1]), name
+    assert np.abs(out[True][0]).max() > 0
+    if prec == T.FP64:
+        V = oracle.potential_atoms(g, atoms)
+        R0, I0 = oracle.wavepacket(g, p.r0, p.sigma, p.k0)
+        gV_o = oracle.adjoint(g, V, R0, I0, n, out["gF"])
+        assert np.abs(out[True][0] - gV_o).max() <= 1e-9 * np.abs(gV_o).max()
+
+
 @pytest.mark.parametrize("precision", ["FP32", "FP32_KAHAN"])
 def test_fp32_adjoint_close_to_fp64(T, precision):
     g, atoms, p = small_case()
