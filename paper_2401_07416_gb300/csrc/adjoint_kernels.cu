@@ -476,10 +476,12 @@ __global__ void __launch_bounds__(kTX * kTY) adj_fused_kernel(FusedArgs a)
         // c. the detector terms, once the new R of planes kd and kd + 1 exist (the
         // stencils of d and e below read only planes written before this iteration,
         // so only then is a barrier needed between the two)
-        if (kd >= 0 && b == kd + 1 && b - 1 >= z0 - 2) {
+        // (on a periodic z axis the chunk's planes may be images: compare the plane
+        // itself, act on the ring slots of b - 1 and b)
+        if (kd >= 0 && wrap_axis(b, g.nz, g.per[2]) == kd + 1 && b - 1 >= z0 - 2) {
             __syncthreads();
-            Real *Qlo = sQt + ring(kd, kRingRQ) * kA1, *Qhi = sQt + ring(kd + 1, kRingRQ) * kA1;
-            const Real *Rlo = sRn + ring(kd, kRingRQ) * kA1, *Rhi = sRn + ring(kd + 1, kRingRQ) * kA1;
+            Real *Qlo = sQt + ring(b - 1, kRingRQ) * kA1, *Qhi = sQt + ring(b, kRingRQ) * kA1;
+            const Real *Rlo = sRn + ring(b - 1, kRingRQ) * kA1, *Rhi = sRn + ring(b, kRingRQ) * kA1;
             for (int t = threadIdx.x; t < kA1; t += blockDim.x) {
                 const int x = wrap_axis(x0 - 1 + t % kW1, g.nx, g.per[0]);
                 const int y = wrap_axis(y0 - 1 + t / kW1, g.ny, g.per[1]);
