@@ -315,7 +315,12 @@ __global__ void __launch_bounds__(TmemSync<C, WS>::THREADS, C::MINB)
                           const Real *I1, const Real *sb_prev, Real *sb_cur, auto FASTc) {
             constexpr bool FAST = decltype(FASTc)::value;
             const bool p_out = !FAST && !zper && (p < 0 || p >= nz);
-            Real zmR[RPT][VEC];    // R at plane p-2: stage 1's z- neighbour, stage 2's accumulator
+            // The z- neighbour of stage s is F_{s-1} at plane p-s-1, which is also the
+            // accumulator of stage s+1 (F_{s-1} at plane p-(s+1)): it stays in registers
+            // from one stage to the next (for stage 1, R at plane p-2 from shared memory).
+            // Stage s runs only when stage s-1 ran in the same iteration (the pipeline
+            // fill and the cone both shrink with s), so zmh always holds that value.
+            Real zmh[RPT][VEC];
             Real prev[RPT][VEC];   // the previous stage's output: this stage's z+ neighbour
 #pragma unroll
             for (int s = 1; s <= H; ++s) {
@@ -343,16 +348,14 @@ __global__ void __launch_bounds__(TmemSync<C, WS>::THREADS, C::MINB)
                 if (s == 1) {
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
-                        ld_vec<Real>(A2 + own + r * W, zmR[r]);
+                        ld_vec<Real>(A2 + own + r * W, zm[r]);
                         ld_vec<Real>(A1 + own + r * W, c[r]);
                         ld_vec<Real>(A0 + own + r * W, zp[r]);
                         ld_vec<Real>(I1 + own + r * W, acc[r]);
                         if constexpr (C::KAHAN) ld_vec<Real>(I1 + OFF_C + own + r * W, cacc[r]);
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            zm[r][v] = zmR[r][v];
+                        for (int v = 0; v < VEC; ++v)
                             if (p_out) zp[r][v] = 0.f;
-                        }
                     }
                     ld_vec<Real>(A1 + off_ym, ym);
                     ld_vec<Real>(A1 + off_yp, yp);
@@ -364,10 +367,7 @@ __global__ void __launch_bounds__(TmemSync<C, WS>::THREADS, C::MINB)
                     for (int r = 0; r < RPT; ++r) {
                         tmem_ld4(K0 + fcol(s - 2, 0) + r * VEC, zm[r]);
                         tmem_ld4(K1 + fcol(s - 2, 0) + r * VEC, c[r]);
-                        if (s >= 3) {
-                            tmem_ld4(K0 + fcol(s - 3, 0) + r * VEC, acc[r]);
-                            if constexpr (C::KAHAN) tmem_ld4(K0 + fcol(s - 3, 1) + r * VEC, cacc[r]);
-                        }
+                        if (s >= 3 && C::KAHAN) tmem_ld4(K0 + fcol(s - 3, 1) + r * VEC, cacc[r]);
                     }
                     const Real *Sp = sb_prev + (s - 2) * 2 * PLANE;
                     ld_vec<Real>(Sp + off_ym, ym);
@@ -375,12 +375,11 @@ __global__ void __launch_bounds__(TmemSync<C, WS>::THREADS, C::MINB)
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) zp[r][v] = prev[r][v];
-                        if (s == 2) {
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) acc[r][v] = zmR[r][v];
-                            if constexpr (C::KAHAN) ld_vec<Real>(A2 + OFF_C + own + r * W, cacc[r]);
+                        for (int v = 0; v < VEC; ++v) {
+                            zp[r][v] = prev[r][v];
+                            acc[r][v] = zmh[r][v];
                         }
+                        if (s == 2 && C::KAHAN) ld_vec<Real>(A2 + OFF_C + own + r * W, cacc[r]);
                     }
                     tmem_wait_ld();
 #pragma unroll
@@ -388,10 +387,7 @@ __global__ void __launch_bounds__(TmemSync<C, WS>::THREADS, C::MINB)
                         after_wait(dd[r]);
                         after_wait(zm[r]);
                         after_wait(c[r]);
-                        if (s >= 3) {
-                            after_wait(acc[r]);
-                            if constexpr (C::KAHAN) after_wait(cacc[r]);
-                        }
+                        if (s >= 3 && C::KAHAN) after_wait(cacc[r]);
                     }
                 }
                 if (s >= 3 && odd && absorb) {   // I of the previous step carries its absorbing factor
@@ -467,7 +463,10 @@ __global__ void __launch_bounds__(TmemSync<C, WS>::THREADS, C::MINB)
                         tmem_st4(K2 + fcol(s - 1, 0) + r * VEC, out[r]);
                         if constexpr (C::KAHAN) tmem_st4(K2 + fcol(s - 1, 1) + r * VEC, cout[r]);
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) prev[r][v] = out[r][v];
+                        for (int v = 0; v < VEC; ++v) {
+                            prev[r][v] = out[r][v];
+                            zmh[r][v] = zm[r][v];
+                        }
                         if (r == 0 || r == RPT - 1) st_vec<Real>(So + own + r * W, out[r]);
                     }
                 } else {

@@ -78,7 +78,7 @@ def test_static_scratch_rejects_too_many_planes(T):
     import torch
     g = W.small_grid(4, 1, 8193, h=(0.2, 0.2, 0.2), dt=0.003)
     p = T.params_from_grid(g, T.FP64)
-    x = torch.zeros(4, device="cuda", dtype=torch.float64)
+    x = torch.zeros(4 * 1 * 8193, device="cuda", dtype=torch.float64)   # a full grid's worth
     with pytest.raises(T.TdseError) as e:
         T.tdse_observables_static(p, x, x, None)
     assert e.value.status == T.EINVAL
