@@ -1,0 +1,457 @@
+// Fused leapfrog step, tensor-memory windows, with every ring slot a compile-time
+// offset (arXiv 2401.07416, Sec. 2.1, Eqs. 8-9), FP32 and FP32 + Kahan, two time
+// steps per launch.
+//
+// Same schedule, windows and arithmetic as fused_step_tmem_kernel (step_tmem.cu):
+// a CTA marches an xy tile along z, stage s of the 2T half-step stages works on
+// plane p - s while plane p arrives by TMA, the stage windows and d live in tensor
+// memory.  What differs is the bookkeeping, which dominated the instruction count
+// there (ring heads, window phases, d slots and their addresses were computed at
+// run time, about a third of all instructions):
+//   - Fields read only by the thread that owns a cell are loaded late: the loads
+//     that complete on the barrier of plane p bring R and d at p, I and cI at p-1
+//     and cR at p-2, so their rings only cover the planes in flight (3 slots);
+//     R, read as a stencil at p-1 and by its owner at p and p-2, keeps 6 slots.
+//   - Every period is a divisor of 6: the R ring (6), the other rings and
+//     barriers (3), the three-plane windows (3), the double-buffered stage planes
+//     (2) and the d slots in tensor memory (6).  The z-march is unrolled by 6, so
+//     each iteration's slots are constants, and the barriers are re-initialised for
+//     each work item so that their phases restart with it.
+#include <type_traits>
+
+#include "step_common.cuh"
+#include "tmem_common.cuh"
+
+namespace tdse {
+namespace {
+
+constexpr int kSlimU = 6;   // unroll of the z-march: every slot period divides it
+
+template <class C>
+struct SlimShape {
+    typedef typename C::Real Real;
+    static constexpr int H = C::H, PF = C::PF;
+    static constexpr int NRS = 6;                      // R ring
+    static constexpr int NBS = PF + 1;                 // I, cI, cR, d rings and barriers
+    static constexpr int NSB = 2 * (H - 1);            // stage planes, double-buffered
+    static constexpr int NPL = NRS + NBS * (C::KAHAN ? 4 : 2) + NSB;
+    static constexpr size_t SMEM = static_cast<size_t>(NPL) * C::PLANE_BYTES + 8 * NBS + 128;
+    static constexpr uint32_t TX_BYTES = C::PLANE_BYTES * (C::KAHAN ? 5 : 3);
+    // tensor memory: the three-plane windows of F_1 .. F_{H-1} and 6 d slots
+    static constexpr int NF = H - 1, NCMP = C::KAHAN ? 2 : 1, SLOT = C::VEC;
+    static constexpr int NDT = 6;
+    static constexpr int PHASE_COLS = NF * NCMP * SLOT;
+    static constexpr int WIN_COLS = 3 * PHASE_COLS;
+    static constexpr int THREAD_COLS = WIN_COLS + NDT * SLOT;
+    static constexpr int NW = C::NT / 32;
+    static constexpr int QUAD_COLS = ((NW + 3) / 4) * THREAD_COLS;
+    static constexpr uint32_t NCOLS = tmem_cols_for(QUAD_COLS);
+    static constexpr int MAX_RESIDENT_SMEM = 233472 / static_cast<int>(SMEM + 1024);
+    static constexpr int MAX_RESIDENT_THREADS = 2048 / C::NT;
+    static constexpr int MAX_RESIDENT = MAX_RESIDENT_SMEM < MAX_RESIDENT_THREADS ? MAX_RESIDENT_SMEM
+                                                                                 : MAX_RESIDENT_THREADS;
+    static_assert(sizeof(Real) == 4 && C::RPT == 1 && C::DSTASH, "FP32 fields, one row per thread");
+    static_assert(H + 1 <= NDT, "d is read H planes back");
+    static_assert(NRS >= PF + 3 && kSlimU % NRS == 0 && kSlimU % NBS == 0 && kSlimU % 3 == 0 &&
+                      kSlimU % 2 == 0 && kSlimU % NDT == 0,
+                  "every slot period must divide the unroll");
+    static_assert(QUAD_COLS <= 512, "windows exceed tensor memory");
+    static_assert(MAX_RESIDENT * NCOLS <= 512, "co-resident CTAs exceed tensor memory");
+    static_assert(C::MINB * (SMEM + 1024) <= 233472, "CTAs per SM exceed the shared memory");
+};
+
+template <class C>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    fused_step_slim_kernel(const MemberDev *__restrict__ members, const WorkDev *__restrict__ work,
+                           int *counter, int *status, int in_buf, unsigned long long wait_ns)
+{
+    typedef float Real;
+    typedef SlimShape<C> SS;
+    constexpr int H = C::H, VEC = C::VEC, W = C::W, ROWS = C::ROWS, PLANE = C::PLANE;
+    constexpr int PF = C::PF, NRS = SS::NRS, NBS = SS::NBS;
+    constexpr bool KAHAN = C::KAHAN;
+
+    extern __shared__ unsigned char smem_raw[];
+    Real *ringR = reinterpret_cast<Real *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    Real *ringI = ringR + NRS * PLANE;
+    Real *ringD = ringI + NBS * PLANE;
+    Real *ringCI = ringD + NBS * PLANE;                 // Kahan only
+    Real *ringCR = ringCI + (KAHAN ? NBS : 0) * PLANE;   // Kahan only
+    Real *sbuf = ringCR + (KAHAN ? NBS : 0) * PLANE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sbuf + SS::NSB * PLANE);
+    __shared__ int s_item;
+    __shared__ int s_abort;
+    __shared__ uint32_t s_tmem;
+    __shared__ ItemScalars S;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int qx = tid % C::TPX;
+    const int r0 = tid / C::TPX;                         // this thread's region row
+    const int warp_row0 = warp * C::RW;
+    // stages this warp runs: its rows leave the cone of stage s for s > smax_w
+    const int smax_w = min(warp_row0 + C::RW - 1, ROWS - 1 - warp_row0);
+    const int own = r0 * W + qx * VEC;
+    const int off_ym = (r0 > 0 ? r0 - 1 : r0) * W + qx * VEC;
+    const int off_yp = (r0 + 1 < ROWS ? r0 + 1 : r0) * W + qx * VEC;
+
+    if (warp == 0) tmem_alloc(&s_tmem, SS::NCOLS);
+    if (tid == 0) {
+        s_abort = 0;
+        for (int b = 0; b < NBS; ++b) mbar_init(&bars[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    const uint32_t tbase = s_tmem + ((static_cast<uint32_t>(warp & 3) * 32u) << 16) +
+                           static_cast<uint32_t>(warp >> 2) * SS::THREAD_COLS;
+    // window plane k (0..2) of field f (F_{f+1}), value (0) or compensation (1)
+    auto wcol = [&](int k, int f, int cmp) {
+        return tbase + static_cast<uint32_t>(k * SS::PHASE_COLS + (f * SS::NCMP + cmp) * SS::SLOT);
+    };
+    auto dcol = [&](int j) { return tbase + static_cast<uint32_t>(SS::WIN_COLS + j * SS::SLOT); };
+
+    bool first_item = true;
+    for (;;) {
+        if (tid == 0) fetch_item(members, work, counter, in_buf, &s_item, S);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= work->total) break;
+        const MemberDev &M = members[S.m];   // tensor maps only (thread 0)
+        const int tile_x = S.tile_x, tile_y = S.tile_y, kz0 = S.kz0, kz1 = S.kz1;
+        const int L0 = kz0 - H;
+        const int nit = (kz1 - kz0) + 2 * H;
+        const int G = S.G, nx = S.nx, ny = S.ny, nz = S.nz;
+        const int bx = G + tile_x * C::TX - C::HX;
+        const int by = G + tile_y * C::TY - H;
+        const int xs = tile_x * C::TX - C::HX + qx * VEC;
+        const int ys0 = tile_y * C::TY - H + r0;
+        const bool zper = S.per_z != 0;
+        const int mlo = S.mask_lo, mhi = nz - S.mask_hi;
+        const float cxs = static_cast<float>(S.cx), cys = static_cast<float>(S.cy),
+                    czs = static_cast<float>(S.cz);
+        const float2 cx2 = make_float2(cxs, cxs), cy2 = make_float2(cys, cys),
+                     cz2 = make_float2(czs, czs);
+        const Real *maskz = reinterpret_cast<const Real *>(S.mask);
+        const int kd = S.det_k;
+        const bool flux_owner = kd >= kz0 && kd < kz1;
+
+        auto inside = [&](int v) {
+            return (S.per_x || (xs + v >= 0 && xs + v < nx)) && (S.per_y || (ys0 >= 0 && ys0 < ny));
+        };
+        bool walls = false;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) walls |= !inside(v);
+        const bool store_row = qx * VEC >= C::HX && qx * VEC < C::HX + C::TX && xs < nx &&
+                               r0 >= H && r0 < H + C::TY && ys0 < ny;
+        const long long pitch = S.pitch;
+        const bool seam = (S.per_x && (xs < G || xs >= nx - G)) || (S.per_y && (ys0 < G || ys0 >= ny - G));
+        Real *outR = reinterpret_cast<Real *>(S.outR);
+        Real *outI = reinterpret_cast<Real *>(S.outI);
+        Real *outCR = reinterpret_cast<Real *>(S.outCR);
+        Real *outCI = reinterpret_cast<Real *>(S.outCI);
+        const long long out0 = static_cast<long long>(ys0 + G) * pitch + (xs + G);
+
+        // windows start at zero (planes before the first computed one)
+        {
+            float zero[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < 3; ++k)
+                for (int f = 0; f < SS::NF; ++f)
+                    for (int cmp = 0; cmp < SS::NCMP; ++cmp) tmem_st4(wcol(k, f, cmp), zero);
+            tmem_wait_st();
+        }
+        // barriers restart their phases with each item (every load of the previous
+        // item has been waited for)
+        if (tid == 0) {
+            if (!first_item)
+                for (int b = 0; b < NBS; ++b) {
+                    mbar_inval(&bars[b]);
+                    mbar_init(&bars[b], 1);
+                }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        first_item = false;
+        const bool tile_walls = __syncthreads_or(walls) != 0;
+        const int fast_lo = mlo + H;
+        const int fast_hi = zper ? mhi + 1 : min(mhi + 1, nz);
+        auto zwrap = [&](int L) { return zper ? ((L % nz) + nz) % nz : L; };
+
+        // loads completing on barrier j % NBS: R and d at plane L0 + j, I and cI at
+        // L0 + j - 1, cR at L0 + j - 2 (beyond a wall TMA fills zeros)
+        auto issue = [&](int j) {
+            const int L = L0 + j;
+            uint64_t *bar = &bars[j % NBS];
+            mbar_arrive_expect_tx(bar, SS::TX_BYTES);
+            tma_load_3d(ringR + (j % NRS) * PLANE, &M.tm_R[in_buf], bx, by, zwrap(L), bar);
+            tma_load_3d(ringD + (j % NBS) * PLANE, &M.tm_d, bx, by, zwrap(L), bar);
+            tma_load_3d(ringI + (j % NBS) * PLANE, &M.tm_I[in_buf], bx, by, zwrap(L - 1), bar);
+            if constexpr (KAHAN) {
+                tma_load_3d(ringCI + (j % NBS) * PLANE, &M.tm_cI[in_buf], bx, by, zwrap(L - 1), bar);
+                tma_load_3d(ringCR + (j % NBS) * PLANE, &M.tm_cR[in_buf], bx, by, zwrap(L - 2), bar);
+            }
+        };
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int j = 0; j < PF && j < nit; ++j) issue(j);
+        }
+        int issued = min(PF, nit);
+        int waited = 0;
+
+        // The stages of iteration it = it0 + K (it0 a multiple of kSlimU), plane p.
+        auto stages = [&](const int it, const int p, auto Kc, auto FASTc) {
+            constexpr int K = decltype(Kc)::value;
+            constexpr bool FAST = decltype(FASTc)::value;
+            constexpr int ph = K % 3;                              // window slot of the old plane
+            constexpr int k0 = ph, k1 = (ph + 1) % 3, k2 = (ph + 2) % 3;   // old, center, new
+            const Real *R0 = ringR + (K % NRS) * PLANE;               // R at p
+            const Real *R1 = ringR + ((K + NRS - 1) % NRS) * PLANE;   // R at p-1
+            const Real *R2 = ringR + ((K + NRS - 2) % NRS) * PLANE;   // R at p-2
+            const Real *Ib = ringI + (K % NBS) * PLANE;               // I at p-1
+            [[maybe_unused]] const Real *CIb = ringCI + (K % NBS) * PLANE;   // cI at p-1
+            [[maybe_unused]] const Real *CRb = ringCR + (K % NBS) * PLANE;   // cR at p-2
+            const Real *sb_prev = sbuf + ((K + 1) & 1) * PLANE;
+            Real *sb_cur = sbuf + (K & 1) * PLANE;
+            const bool p_out = !FAST && !zper && (p < 0 || p >= nz);
+            Real zmh[VEC];    // z- neighbour of the previous stage = accumulator of this one
+            Real prev[VEC];   // the previous stage's output: this stage's z+ neighbour
+#pragma unroll
+            for (int s = 1; s <= H; ++s) {
+                if (!FAST && it < 2 * s) continue;   // pipeline filling
+                if (s > smax_w) continue;            // rows outside the cone
+                const int q = p - s;
+                const bool odd = (s & 1) != 0;
+                bool q_out = false, absorb = false;
+                Real mq = 1.f;
+                if constexpr (!FAST) {
+                    q_out = !zper && (q < 0 || q >= nz);
+                    int qm = q;
+                    if (zper) {
+                        qm = q % nz;
+                        if (qm < 0) qm += nz;
+                    }
+                    absorb = !q_out && (qm < mlo || qm >= mhi);
+                    if (absorb) mq = maskz[qm];
+                }
+                const int jd = (K - s + 2 * SS::NDT) % SS::NDT;   // d slot of plane q
+                Real zm[VEC], c[VEC], zp[VEC], ym[VEC], yp[VEC], dd[VEC], acc[VEC], cacc[VEC];
+                tmem_ld4(dcol(jd), dd);
+                if (s == 1) {
+                    ld_vec<Real>(R2 + own, zm);
+                    ld_vec<Real>(R1 + own, c);
+                    ld_vec<Real>(R0 + own, zp);
+                    ld_vec<Real>(Ib + own, acc);
+                    if constexpr (KAHAN) ld_vec<Real>(CIb + own, cacc);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v)
+                        if (p_out) zp[v] = 0.f;
+                    ld_vec<Real>(R1 + off_ym, ym);
+                    ld_vec<Real>(R1 + off_yp, yp);
+                    tmem_wait_ld();
+                    after_wait(dd);
+                } else {
+                    tmem_ld4(wcol(k0, s - 2, 0), zm);
+                    tmem_ld4(wcol(k1, s - 2, 0), c);
+                    if (s >= 3 && KAHAN) tmem_ld4(wcol(k0, s - 3, 1), cacc);
+                    const Real *Sp = sb_prev + (s - 2) * 2 * PLANE;
+                    ld_vec<Real>(Sp + off_ym, ym);
+                    ld_vec<Real>(Sp + off_yp, yp);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        zp[v] = prev[v];
+                        acc[v] = zmh[v];
+                    }
+                    if (s == 2 && KAHAN) ld_vec<Real>(CRb + own, cacc);
+                    tmem_wait_ld();
+                    after_wait(dd);
+                    after_wait(zm);
+                    after_wait(c);
+                    if (s >= 3 && KAHAN) after_wait(cacc);
+                }
+                if (s >= 3 && odd && absorb) {   // I of the previous step carries its absorbing factor
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        acc[v] = mul_rn(acc[v], mq);
+                        if constexpr (KAHAN) cacc[v] = mul_rn(cacc[v], mq);
+                    }
+                }
+
+                Real out[VEC], cout[VEC];
+                {
+                    const Real xl = __shfl_up_sync(kFull, c[VEC - 1], 1);
+                    const Real xr = __shfl_down_sync(kFull, c[0], 1);
+                    update_row_f32<KAHAN, VEC>(odd, c, xl, xr, ym, yp, zm, zp, dd, acc, cacc, cx2, cy2,
+                                               cz2, out, cout);
+                }
+                if (!odd && absorb) {   // Eq. 8 step complete: absorbing factor on R
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        out[v] = mul_rn(out[v], mq);
+                        if constexpr (KAHAN) cout[v] = mul_rn(cout[v], mq);
+                    }
+                }
+                if constexpr (!FAST) {
+                    if (walls || q_out) {
+                        const Real zq = q_out ? 0.f : 1.f;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            const Real keep = inside(v) ? 1.f : 0.f;
+                            out[v] *= keep * zq;
+                            if constexpr (KAHAN) cout[v] *= keep * zq;
+                        }
+                    }
+                    // detector flux of step (s+1)/2: R^n at planes kd, kd+1 and the new I
+                    if (odd && s < H && flux_owner && q == kd + 1) {
+                        Real ilo[VEC];   // I at plane kd: the center of stage s's window
+                        tmem_ld4(wcol(k1, s - 1, 0), ilo);
+                        tmem_wait_ld();
+                        after_wait(ilo);
+                        if (store_row) {
+                            const int pix = ys0 * nx + xs;
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) {
+                                const double j = S.cj * (static_cast<double>(zm[v]) * out[v] -
+                                                         static_cast<double>(c[v]) * ilo[v]);
+                                S.flux[pix + v] += j * S.dt;
+                                if (s == H - 1) S.jlast[pix + v] = j;
+                            }
+                        }
+                    }
+                }
+
+                if (s < H) {
+                    tmem_st4(wcol(k2, s - 1, 0), out);
+                    if constexpr (KAHAN) tmem_st4(wcol(k2, s - 1, 1), cout);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        prev[v] = out[v];
+                        zmh[v] = zm[v];
+                    }
+                    st_vec<Real>(sb_cur + (s - 1) * 2 * PLANE + own, out);
+                } else {
+                    // I of the last step: the center of F_{H-1}'s window
+                    Real vi[VEC], vci[VEC];
+                    tmem_ld4(wcol(k1, H - 2, 0), vi);
+                    if constexpr (KAHAN) tmem_ld4(wcol(k1, H - 2, 1), vci);
+                    tmem_wait_ld();
+                    after_wait(vi);
+                    if constexpr (KAHAN) after_wait(vci);
+                    if (store_row && (FAST || (q >= kz0 && q < kz1))) {
+                        if (absorb) {
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) {
+                                vi[v] = mul_rn(vi[v], mq);
+                                if constexpr (KAHAN) vci[v] = mul_rn(vci[v], mq);
+                            }
+                        }
+                        const long long zoff = static_cast<long long>(q) * S.plane;
+                        store_output_row<Real, KAHAN, VEC>(S, outR, outI, outCR, outCI, zoff + out0, pitch,
+                                                           seam, xs, ys0, out, vi, cout, vci);
+                    }
+                }
+            }
+        };
+
+        // One iteration: wait for plane L0 + it, refill, d to tensor memory, stages.
+        auto plane_step = [&](const int it, auto Kc) -> bool {
+            constexpr int K = decltype(Kc)::value;
+            const int p = L0 + it;
+            if (tid == 0) {
+                if (mbar_wait_bounded(&bars[K % NBS], static_cast<uint32_t>((K / NBS) & 1), wait_ns)) {
+                    waited = it + 1;
+                } else {
+                    atomicOr(status, 1);
+                    s_abort = 1;
+                }
+            }
+            __syncthreads();   // plane p has landed; the previous iteration's reads are done
+            if (s_abort) return false;
+            if (it + PF < nit) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(it + PF);
+                }
+                issued = it + PF + 1;
+            }
+            tmem_wait_st();   // the previous iteration's window planes are in TMEM
+            {
+                Real dp[VEC];
+                ld_vec<Real>(ringD + (K % NBS) * PLANE + own, dp);
+                tmem_st4(dcol(K % SS::NDT), dp);
+            }
+            const bool fast = !tile_walls && it >= 2 * H && p >= fast_lo && p < fast_hi &&
+                              !(flux_owner && p >= kd + 2 && p <= kd + H);
+            if (fast)
+                stages(it, p, Kc, std::true_type{});
+            else
+                stages(it, p, Kc, std::false_type{});
+            return true;
+        };
+
+        for (int it0 = 0; it0 < nit; it0 += kSlimU) {
+            if (!plane_step(it0, std::integral_constant<int, 0>{})) break;
+            if (it0 + 1 >= nit || !plane_step(it0 + 1, std::integral_constant<int, 1>{})) break;
+            if (it0 + 2 >= nit || !plane_step(it0 + 2, std::integral_constant<int, 2>{})) break;
+            if (it0 + 3 >= nit || !plane_step(it0 + 3, std::integral_constant<int, 3>{})) break;
+            if (it0 + 4 >= nit || !plane_step(it0 + 4, std::integral_constant<int, 4>{})) break;
+            if (it0 + 5 >= nit || !plane_step(it0 + 5, std::integral_constant<int, 5>{})) break;
+        }
+
+        __syncthreads();   // every thread has left the z-march: all read the same s_abort
+        if (s_abort) {
+            // wait (bounded) for the loads still in flight, then leave (freeing TMEM below)
+            if (tid == 0) {
+                for (int l = waited; l < issued; ++l)
+                    if (!mbar_wait_bounded(&bars[l % NBS], static_cast<uint32_t>((l / NBS) & 1)))
+                        atomicOr(status, 4);   // the CTA leaves with a load still in flight
+            }
+            __syncthreads();
+            break;
+        }
+        tmem_wait_st();
+        __syncthreads();
+    }
+
+    tmem_wait_st();
+    tmem_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(s_tmem, SS::NCOLS);
+}
+
+template <class C>
+cudaError_t launch_slim_cfg(const StepLaunch &L)
+{
+    typedef SlimShape<C> SS;
+    static std::atomic<uint64_t> smem_allowed{0};   // one bit per device
+    cudaError_t e = allow_dynamic_smem(fused_step_slim_kernel<C>, SS::SMEM, smem_allowed);
+    if (e != cudaSuccess) return e;
+    fused_step_slim_kernel<C><<<L.grid, C::NT, SS::SMEM, L.stream>>>(L.members, L.work, L.counter,
+                                                                     L.status, L.in_buf, L.wait_ns);
+    return cudaGetLastError();
+}
+
+template <class C>
+void fill_slim_config(StepConfig *cfg)
+{
+    cfg->tile_x = C::TX;
+    cfg->tile_y = C::TY;
+    cfg->box_x = C::W;
+    cfg->box_y = C::ROWS;
+    cfg->threads = C::NT;
+    cfg->smem = SlimShape<C>::SMEM;
+    cfg->ctas_per_sm = C::MINB;
+}
+
+}  // namespace
+
+#define TDSE_SLIM_VARIANT(FN, ...)                                                      \
+    cudaError_t launch_##FN(const StepLaunch &L) { return launch_slim_cfg<Cfg<__VA_ARGS__>>(L); } \
+    void fill_##FN(StepConfig *cfg) { fill_slim_config<Cfg<__VA_ARGS__>>(cfg); }
+
+// Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched, CTAs per SM,
+//     d kept in TMEM>
+TDSE_SLIM_VARIANT(slim_k32_t2_w32_r32x1_pf2_b2, float, 4, 8, 32, 1, true, 2, 2, true)
+TDSE_SLIM_VARIANT(slim_k32_t2_w32_r28x1_pf2_b2, float, 4, 8, 28, 1, true, 2, 2, true)
+TDSE_SLIM_VARIANT(slim_f32_t2_w32_r32x1_pf2_b2, float, 4, 8, 32, 1, false, 2, 2, true)
+
+}  // namespace tdse

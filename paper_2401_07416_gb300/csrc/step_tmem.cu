@@ -22,64 +22,10 @@
 #include <type_traits>
 
 #include "step_common.cuh"
+#include "tmem_common.cuh"
 
 namespace tdse {
 namespace {
-
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
-{
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(dst)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_fence_before_sync()
-{
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_fence_after_sync()
-{
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Four consecutive columns of this thread's lane.
-__device__ __forceinline__ void tmem_st4(uint32_t addr, const float (&v)[4])
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr),
-                 "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld4(uint32_t addr, float (&v)[4])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
-                 : "r"(addr)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st()
-{
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Values loaded by tcgen05.ld may only be read after tcgen05.wait::ld; passing
-// them through an empty volatile asm after the wait orders every later use.
-__device__ __forceinline__ void after_wait(float (&v)[4])
-{
-    asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]));
-}
 
 // TMEM footprint of a configuration.
 template <class C>
@@ -93,8 +39,7 @@ struct TmemShape {
     static constexpr int WIN_COLS = 3 * PHASE_COLS;          // one thread's windows
     static constexpr int THREAD_COLS = WIN_COLS + NDT * SLOT;
     static constexpr int QUAD_COLS = ((NW + 3) / 4) * THREAD_COLS;   // warps w, w+4, ... share a quadrant
-    static constexpr uint32_t NCOLS = QUAD_COLS <= 32 ? 32 : QUAD_COLS <= 64 ? 64
-                                    : QUAD_COLS <= 128 ? 128 : QUAD_COLS <= 256 ? 256 : 512;
+    static constexpr uint32_t NCOLS = tmem_cols_for(QUAD_COLS);
     static_assert(QUAD_COLS <= 512, "windows exceed tensor memory");
     // CTAs that shared memory and the thread limit let share an SM must fit in TMEM
     // together (an allocation that cannot be met would wait for another CTA to exit)
