@@ -433,13 +433,78 @@ __global__ void __launch_bounds__(kTX * kTY) adj_fused_kernel(FusedArgs a)
         load_region(sI + ring(z, kRingIP) * kA2, Ig, g, x0 - 2, y0 - 2, z, kW2, kH2);
         load_region(sP + ring(z, kRingIP) * kA2, Pg, g, x0 - 2, y0 - 2, z, kW2, kH2);
     }
+    // The cells this thread loads in every plane (at most two of each region) as
+    // offsets within a plane, -1 beyond a wall; the next plane's values are fetched
+    // into registers while the current one is computed.
+    constexpr int kN2 = (kA2 + kTX * kTY - 1) / (kTX * kTY), kN1 = (kA1 + kTX * kTY - 1) / (kTX * kTY);
+    const long long plane = static_cast<long long>(g.nx) * g.ny;
+    int xy2[kN2], xy1[kN1];
+    long long dxy1[kN1];
+#pragma unroll
+    for (int k = 0; k < kN2; ++k) {
+        const int t = threadIdx.x + k * kTX * kTY;
+        const int x = wrap_axis(x0 - 2 + t % kW2, g.nx, g.per[0]), y = wrap_axis(y0 - 2 + t / kW2, g.ny, g.per[1]);
+        xy2[k] = (t < kA2 && x >= 0 && y >= 0) ? y * g.nx + x : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kN1; ++k) {
+        const int t = threadIdx.x + k * kTX * kTY;
+        const int x = wrap_axis(x0 - 1 + t % kW1, g.nx, g.per[0]), y = wrap_axis(y0 - 1 + t / kW1, g.ny, g.per[1]);
+        const bool ok = t < kA1 && x >= 0 && y >= 0;
+        xy1[k] = ok ? y * g.nx + x : -1;
+        dxy1[k] = ok ? static_cast<long long>(y + g.G) * g.pitch + (x + g.G) : -1;
+    }
+    Real fI[kN2], fP[kN2], fR[kN1], fQ[kN1], fD[kN1];
+    // I and P at plane zi, R, Q and d at plane zr into the fetch registers
+    auto fetch = [&](int zi, int zr) {
+        const int wi = wrap_axis(zi, g.nz, g.per[2]), wr = wrap_axis(zr, g.nz, g.per[2]);
+#pragma unroll
+        for (int k = 0; k < kN2; ++k) {
+            const bool ok = wi >= 0 && xy2[k] >= 0;
+            const long long o = wi * plane + xy2[k];
+            fI[k] = ok ? Ig[o] : Real(0);
+            fP[k] = ok ? Pg[o] : Real(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kN1; ++k) {
+            const bool ok = wr >= 0 && xy1[k] >= 0;
+            const long long o = wr * plane + xy1[k];
+            fR[k] = ok ? Rg[o] : Real(0);
+            fQ[k] = ok ? Qg[o] : Real(0);
+            fD[k] = ok ? D[wr * g.pplane + dxy1[k]] : Real(0);
+        }
+    };
+    auto deposit = [&](int zi, int zr) {
+        Real *dI = sI + ring(zi, kRingIP) * kA2, *dP = sP + ring(zi, kRingIP) * kA2;
+        Real *dD = sD + ring(zr, kRingD) * kA1;
+#pragma unroll
+        for (int k = 0; k < kN2; ++k) {
+            const int t = threadIdx.x + k * kTX * kTY;
+            if (t < kA2) {
+                dI[t] = fI[k];
+                dP[t] = fP[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kN1; ++k) {
+            const int t = threadIdx.x + k * kTX * kTY;
+            if (t < kA1) {
+                sR[t] = fR[k];
+                sQ[t] = fQ[k];
+                dD[t] = fD[k];
+            }
+        }
+    };
+    fetch(z0 - 1, z0 - 2);
     for (int b = z0 - 2; b <= z1 + 1; ++b) {
-        __syncthreads();   // the previous iteration's reads of the slots reloaded now are done
-        load_region(sI + ring(b + 1, kRingIP) * kA2, Ig, g, x0 - 2, y0 - 2, b + 1, kW2, kH2);
-        load_region(sP + ring(b + 1, kRingIP) * kA2, Pg, g, x0 - 2, y0 - 2, b + 1, kW2, kH2);
-        load_region(sR, Rg, g, x0 - 1, y0 - 1, b, kW1, kH1);
-        load_region(sQ, Qg, g, x0 - 1, y0 - 1, b, kW1, kH1);
-        load_region_d(sD + ring(b, kRingD) * kA1, D, g, x0 - 1, y0 - 1, b, kW1, kH1);
+        __syncthreads();   // the previous iteration's reads of the slots refilled now are done
+        deposit(b + 1, b);
+        if (b + 1 <= z1 + 1) fetch(b + 2, b + 1);
+        // dL/dV of the cell updated below (plane b - 2), fetched ahead of its use
+        double gv = 0.0;
+        const int qd = b - 2;
+        const long long od = cell(g, min(cx, g.nx - 1), min(cy, g.ny - 1), max(qd, 0));
+        if (qd >= z0 && qd < z1 && own) gv = a.gV[od];
         __syncthreads();
         // b. undo Eq. 8 and its adjoint at plane b on the tile plus one cell
         {
@@ -504,8 +569,7 @@ __global__ void __launch_bounds__(kTX * kTY) adj_fused_kernel(FusedArgs a)
                                     Qq[c1], dq);
             const Real ar = stencil(g, Rq[c1 - 1], Rq[c1 + 1], Rq[c1 - kW1], Rq[c1 + kW1], Rm[c1], Rp[c1],
                                     Rq[c1], dq);
-            const long long o = cell(g, cx, cy, q);
-            double gv = a.gV[o];
+            const long long o = od;
             Real pn, in;
             de_cell(g, sP[ring(q, kRingIP) * kA2 + c2], sI[ring(q, kRingIP) * kA2 + c2], Qq[c1], Rq[c1],
                     Mk[q], Mi[q], aq, ar, gv, pn, in);
