@@ -386,6 +386,7 @@ def batch_throughput(torch, T, steps, warmup):
     return {"value": cells * steps / (ms * 1e-3), "unit": "cell-updates/s", "members": 48,
             "cells": cells, "steps": steps, "precision": "f32+kahan", "tuning": tun,
             "graphs": True, "steps_per_launch": tb, "launches": nl, "avg_launch_ms": lms,
+            "timed_ms": ms, "reduce_ms": prof["reduce_ms"], "reduce_launches": prof["reduce_launches"],
             "hbm_frac_of_algorithmic_bytes": BYTES_PER_NODE[W.FP32_KAHAN] * cells / (lms * 1e-3) / 1e9
                                              / measured_peaks()[0],
             "solo_sum_value": cells * steps / (solo_ms * 1e-3),

@@ -60,13 +60,73 @@ struct SlimShape {
     static_assert(C::MINB * (SMEM + 1024) <= 233472, "CTAs per SM exceed the shared memory");
 };
 
+// Slot offsets of one iteration (it = it0 + k, it0 a multiple of kSlimU): ring
+// offsets in elements, tensor-memory columns relative to the thread's base.
 template <class C>
+struct SlimSlots {
+    typedef SlimShape<C> SS;
+    static constexpr int PLANE = C::PLANE, NRS = SS::NRS, NBS = SS::NBS, NDT = SS::NDT, H = C::H;
+    int r0, r1, r2;          // R at p, p-1, p-2
+    int bb;                  // I, cI (p-1), cR (p-2), d (p)
+    int sbp, sbc;            // stage planes read (previous iteration) and written
+    uint32_t w0, w1, w2;     // window planes: old, center, new
+    uint32_t d[H + 1];       // d at planes p, p-1, ..., p-H
+    int bar;                 // barrier slot
+    uint32_t par;            // its phase parity
+    __device__ __forceinline__ static SlimSlots at(int k)
+    {
+        SlimSlots x;
+        x.r0 = (k % NRS) * PLANE;
+        x.r1 = ((k + NRS - 1) % NRS) * PLANE;
+        x.r2 = ((k + NRS - 2) % NRS) * PLANE;
+        x.bb = (k % NBS) * PLANE;
+        x.sbp = ((k + 1) & 1) * PLANE;
+        x.sbc = (k & 1) * PLANE;
+        x.w0 = static_cast<uint32_t>((k % 3) * SS::PHASE_COLS);
+        x.w1 = static_cast<uint32_t>(((k + 1) % 3) * SS::PHASE_COLS);
+        x.w2 = static_cast<uint32_t>(((k + 2) % 3) * SS::PHASE_COLS);
+#pragma unroll
+        for (int j = 0; j <= H; ++j)
+            x.d[j] = static_cast<uint32_t>(SS::WIN_COLS + ((k - j + 2 * NDT) % NDT) * SS::SLOT);
+        x.bar = k % NBS;
+        x.par = static_cast<uint32_t>((k / NBS) & 1);
+        return x;
+    }
+    // the next iteration's slots
+    __device__ __forceinline__ void advance()
+    {
+        r2 = r1;
+        r1 = r0;
+        r0 = r0 + PLANE == NRS * PLANE ? 0 : r0 + PLANE;
+        bb = bb + PLANE == NBS * PLANE ? 0 : bb + PLANE;
+        const int t = sbp;
+        sbp = sbc;
+        sbc = t;
+        const uint32_t w = w0;
+        w0 = w1;
+        w1 = w2;
+        w2 = w;
+#pragma unroll
+        for (int j = H; j > 0; --j) d[j] = d[j - 1];
+        d[0] = d[0] + SS::SLOT == SS::WIN_COLS + NDT * SS::SLOT ? SS::WIN_COLS : d[0] + SS::SLOT;
+        if (++bar == NBS) {
+            bar = 0;
+            par ^= 1u;
+        }
+    }
+};
+
+// ROLL: the z-march as a plain loop whose slot offsets rotate in registers
+// (compact code), instead of unrolled by 6 with constant offsets (fewer
+// instructions, but six copies of the stages for the instruction cache).
+template <class C, bool ROLL>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fused_step_slim_kernel(const MemberDev *__restrict__ members, const WorkDev *__restrict__ work,
                            int *counter, int *status, int in_buf, unsigned long long wait_ns)
 {
     typedef float Real;
     typedef SlimShape<C> SS;
+    typedef SlimSlots<C> Slots;
     constexpr int H = C::H, VEC = C::VEC, W = C::W, ROWS = C::ROWS, PLANE = C::PLANE;
     constexpr int PF = C::PF, NRS = SS::NRS, NBS = SS::NBS;
     constexpr bool KAHAN = C::KAHAN;
@@ -106,11 +166,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     tmem_fence_after_sync();
     const uint32_t tbase = s_tmem + ((static_cast<uint32_t>(warp & 3) * 32u) << 16) +
                            static_cast<uint32_t>(warp >> 2) * SS::THREAD_COLS;
-    // window plane k (0..2) of field f (F_{f+1}), value (0) or compensation (1)
-    auto wcol = [&](int k, int f, int cmp) {
-        return tbase + static_cast<uint32_t>(k * SS::PHASE_COLS + (f * SS::NCMP + cmp) * SS::SLOT);
-    };
-    auto dcol = [&](int j) { return tbase + static_cast<uint32_t>(SS::WIN_COLS + j * SS::SLOT); };
+    // column of field f (F_{f+1}), value (0) or compensation (1), within a window plane
+    auto fcol = [](int f, int cmp) { return static_cast<uint32_t>((f * SS::NCMP + cmp) * SS::SLOT); };
 
     bool first_item = true;
     for (;;) {
@@ -158,7 +215,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             float zero[4] = {0.f, 0.f, 0.f, 0.f};
             for (int k = 0; k < 3; ++k)
                 for (int f = 0; f < SS::NF; ++f)
-                    for (int cmp = 0; cmp < SS::NCMP; ++cmp) tmem_st4(wcol(k, f, cmp), zero);
+                    for (int cmp = 0; cmp < SS::NCMP; ++cmp)
+                        tmem_st4(tbase + static_cast<uint32_t>(k * SS::PHASE_COLS) + fcol(f, cmp), zero);
             tmem_wait_st();
         }
         // barriers restart their phases with each item (every load of the previous
@@ -198,20 +256,17 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         int issued = min(PF, nit);
         int waited = 0;
 
-        // The stages of iteration it = it0 + K (it0 a multiple of kSlimU), plane p.
-        auto stages = [&](const int it, const int p, auto Kc, auto FASTc) {
-            constexpr int K = decltype(Kc)::value;
+        // The stages of iteration it (plane p) with its slots.
+        auto stages = [&](const int it, const int p, const Slots &sl, auto FASTc) {
             constexpr bool FAST = decltype(FASTc)::value;
-            constexpr int ph = K % 3;                              // window slot of the old plane
-            constexpr int k0 = ph, k1 = (ph + 1) % 3, k2 = (ph + 2) % 3;   // old, center, new
-            const Real *R0 = ringR + (K % NRS) * PLANE;               // R at p
-            const Real *R1 = ringR + ((K + NRS - 1) % NRS) * PLANE;   // R at p-1
-            const Real *R2 = ringR + ((K + NRS - 2) % NRS) * PLANE;   // R at p-2
-            const Real *Ib = ringI + (K % NBS) * PLANE;               // I at p-1
-            [[maybe_unused]] const Real *CIb = ringCI + (K % NBS) * PLANE;   // cI at p-1
-            [[maybe_unused]] const Real *CRb = ringCR + (K % NBS) * PLANE;   // cR at p-2
-            const Real *sb_prev = sbuf + ((K + 1) & 1) * PLANE;
-            Real *sb_cur = sbuf + (K & 1) * PLANE;
+            const Real *R0 = ringR + sl.r0;                  // R at p
+            const Real *R1 = ringR + sl.r1;                  // R at p-1
+            const Real *R2 = ringR + sl.r2;                  // R at p-2
+            const Real *Ib = ringI + sl.bb;                  // I at p-1
+            [[maybe_unused]] const Real *CIb = ringCI + sl.bb;   // cI at p-1
+            [[maybe_unused]] const Real *CRb = ringCR + sl.bb;   // cR at p-2
+            const Real *sb_prev = sbuf + sl.sbp;
+            Real *sb_cur = sbuf + sl.sbc;
             const bool p_out = !FAST && !zper && (p < 0 || p >= nz);
             Real zmh[VEC];    // z- neighbour of the previous stage = accumulator of this one
             Real prev[VEC];   // the previous stage's output: this stage's z+ neighbour
@@ -233,9 +288,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     absorb = !q_out && (qm < mlo || qm >= mhi);
                     if (absorb) mq = maskz[qm];
                 }
-                const int jd = (K - s + 2 * SS::NDT) % SS::NDT;   // d slot of plane q
                 Real zm[VEC], c[VEC], zp[VEC], ym[VEC], yp[VEC], dd[VEC], acc[VEC], cacc[VEC];
-                tmem_ld4(dcol(jd), dd);
+                tmem_ld4(tbase + sl.d[s], dd);   // d at plane q
                 if (s == 1) {
                     ld_vec<Real>(R2 + own, zm);
                     ld_vec<Real>(R1 + own, c);
@@ -250,9 +304,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     tmem_wait_ld();
                     after_wait(dd);
                 } else {
-                    tmem_ld4(wcol(k0, s - 2, 0), zm);
-                    tmem_ld4(wcol(k1, s - 2, 0), c);
-                    if (s >= 3 && KAHAN) tmem_ld4(wcol(k0, s - 3, 1), cacc);
+                    tmem_ld4(tbase + sl.w0 + fcol(s - 2, 0), zm);
+                    tmem_ld4(tbase + sl.w1 + fcol(s - 2, 0), c);
+                    if (s >= 3 && KAHAN) tmem_ld4(tbase + sl.w0 + fcol(s - 3, 1), cacc);
                     const Real *Sp = sb_prev + (s - 2) * 2 * PLANE;
                     ld_vec<Real>(Sp + off_ym, ym);
                     ld_vec<Real>(Sp + off_yp, yp);
@@ -303,7 +357,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     // detector flux of step (s+1)/2: R^n at planes kd, kd+1 and the new I
                     if (odd && s < H && flux_owner && q == kd + 1) {
                         Real ilo[VEC];   // I at plane kd: the center of stage s's window
-                        tmem_ld4(wcol(k1, s - 1, 0), ilo);
+                        tmem_ld4(tbase + sl.w1 + fcol(s - 1, 0), ilo);
                         tmem_wait_ld();
                         after_wait(ilo);
                         if (store_row) {
@@ -320,8 +374,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 }
 
                 if (s < H) {
-                    tmem_st4(wcol(k2, s - 1, 0), out);
-                    if constexpr (KAHAN) tmem_st4(wcol(k2, s - 1, 1), cout);
+                    tmem_st4(tbase + sl.w2 + fcol(s - 1, 0), out);
+                    if constexpr (KAHAN) tmem_st4(tbase + sl.w2 + fcol(s - 1, 1), cout);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
                         prev[v] = out[v];
@@ -331,8 +385,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 } else {
                     // I of the last step: the center of F_{H-1}'s window
                     Real vi[VEC], vci[VEC];
-                    tmem_ld4(wcol(k1, H - 2, 0), vi);
-                    if constexpr (KAHAN) tmem_ld4(wcol(k1, H - 2, 1), vci);
+                    tmem_ld4(tbase + sl.w1 + fcol(H - 2, 0), vi);
+                    if constexpr (KAHAN) tmem_ld4(tbase + sl.w1 + fcol(H - 2, 1), vci);
                     tmem_wait_ld();
                     after_wait(vi);
                     if constexpr (KAHAN) after_wait(vci);
@@ -353,11 +407,10 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         };
 
         // One iteration: wait for plane L0 + it, refill, d to tensor memory, stages.
-        auto plane_step = [&](const int it, auto Kc) -> bool {
-            constexpr int K = decltype(Kc)::value;
+        auto plane_step = [&](const int it, const Slots &sl) -> bool {
             const int p = L0 + it;
             if (tid == 0) {
-                if (mbar_wait_bounded(&bars[K % NBS], static_cast<uint32_t>((K / NBS) & 1), wait_ns)) {
+                if (mbar_wait_bounded(&bars[sl.bar], sl.par, wait_ns)) {
                     waited = it + 1;
                 } else {
                     atomicOr(status, 1);
@@ -376,25 +429,33 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             tmem_wait_st();   // the previous iteration's window planes are in TMEM
             {
                 Real dp[VEC];
-                ld_vec<Real>(ringD + (K % NBS) * PLANE + own, dp);
-                tmem_st4(dcol(K % SS::NDT), dp);
+                ld_vec<Real>(ringD + sl.bb + own, dp);
+                tmem_st4(tbase + sl.d[0], dp);
             }
             const bool fast = !tile_walls && it >= 2 * H && p >= fast_lo && p < fast_hi &&
                               !(flux_owner && p >= kd + 2 && p <= kd + H);
             if (fast)
-                stages(it, p, Kc, std::true_type{});
+                stages(it, p, sl, std::true_type{});
             else
-                stages(it, p, Kc, std::false_type{});
+                stages(it, p, sl, std::false_type{});
             return true;
         };
 
-        for (int it0 = 0; it0 < nit; it0 += kSlimU) {
-            if (!plane_step(it0, std::integral_constant<int, 0>{})) break;
-            if (it0 + 1 >= nit || !plane_step(it0 + 1, std::integral_constant<int, 1>{})) break;
-            if (it0 + 2 >= nit || !plane_step(it0 + 2, std::integral_constant<int, 2>{})) break;
-            if (it0 + 3 >= nit || !plane_step(it0 + 3, std::integral_constant<int, 3>{})) break;
-            if (it0 + 4 >= nit || !plane_step(it0 + 4, std::integral_constant<int, 4>{})) break;
-            if (it0 + 5 >= nit || !plane_step(it0 + 5, std::integral_constant<int, 5>{})) break;
+        if constexpr (ROLL) {
+            Slots sl = Slots::at(0);
+            for (int it = 0; it < nit; ++it) {
+                if (!plane_step(it, sl)) break;
+                sl.advance();
+            }
+        } else {
+            for (int it0 = 0; it0 < nit; it0 += kSlimU) {
+                if (!plane_step(it0, Slots::at(0))) break;
+                if (it0 + 1 >= nit || !plane_step(it0 + 1, Slots::at(1))) break;
+                if (it0 + 2 >= nit || !plane_step(it0 + 2, Slots::at(2))) break;
+                if (it0 + 3 >= nit || !plane_step(it0 + 3, Slots::at(3))) break;
+                if (it0 + 4 >= nit || !plane_step(it0 + 4, Slots::at(4))) break;
+                if (it0 + 5 >= nit || !plane_step(it0 + 5, Slots::at(5))) break;
+            }
         }
 
         __syncthreads();   // every thread has left the z-march: all read the same s_abort
@@ -418,15 +479,15 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     if (warp == 0) tmem_dealloc(s_tmem, SS::NCOLS);
 }
 
-template <class C>
+template <class C, bool ROLL>
 cudaError_t launch_slim_cfg(const StepLaunch &L)
 {
     typedef SlimShape<C> SS;
     static std::atomic<uint64_t> smem_allowed{0};   // one bit per device
-    cudaError_t e = allow_dynamic_smem(fused_step_slim_kernel<C>, SS::SMEM, smem_allowed);
+    cudaError_t e = allow_dynamic_smem(fused_step_slim_kernel<C, ROLL>, SS::SMEM, smem_allowed);
     if (e != cudaSuccess) return e;
-    fused_step_slim_kernel<C><<<L.grid, C::NT, SS::SMEM, L.stream>>>(L.members, L.work, L.counter,
-                                                                     L.status, L.in_buf, L.wait_ns);
+    fused_step_slim_kernel<C, ROLL><<<L.grid, C::NT, SS::SMEM, L.stream>>>(
+        L.members, L.work, L.counter, L.status, L.in_buf, L.wait_ns);
     return cudaGetLastError();
 }
 
@@ -444,14 +505,15 @@ void fill_slim_config(StepConfig *cfg)
 
 }  // namespace
 
-#define TDSE_SLIM_VARIANT(FN, ...)                                                      \
-    cudaError_t launch_##FN(const StepLaunch &L) { return launch_slim_cfg<Cfg<__VA_ARGS__>>(L); } \
+#define TDSE_SLIM_VARIANT(FN, ROLL, ...)                                                \
+    cudaError_t launch_##FN(const StepLaunch &L) { return launch_slim_cfg<Cfg<__VA_ARGS__>, ROLL>(L); } \
     void fill_##FN(StepConfig *cfg) { fill_slim_config<Cfg<__VA_ARGS__>>(cfg); }
 
 // Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched, CTAs per SM,
-//     d kept in TMEM>
-TDSE_SLIM_VARIANT(slim_k32_t2_w32_r32x1_pf2_b2, float, 4, 8, 32, 1, true, 2, 2, true)
-TDSE_SLIM_VARIANT(slim_k32_t2_w32_r28x1_pf2_b2, float, 4, 8, 28, 1, true, 2, 2, true)
-TDSE_SLIM_VARIANT(slim_f32_t2_w32_r32x1_pf2_b2, float, 4, 8, 32, 1, false, 2, 2, true)
+//     d kept in TMEM>; "roll": slot offsets rotating in registers
+TDSE_SLIM_VARIANT(slim_k32_t2_w32_r32x1_pf2_b2, false, float, 4, 8, 32, 1, true, 2, 2, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf2_b2, true, float, 4, 8, 32, 1, true, 2, 2, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_w32_r28x1_pf2_b2, true, float, 4, 8, 28, 1, true, 2, 2, true)
+TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf2_b2, true, float, 4, 8, 32, 1, false, 2, 2, true)
 
 }  // namespace tdse

@@ -240,8 +240,9 @@ tdse_status encode_map(tdse_ctx *c, CUtensorMap *map, const Member &mb, void *pt
     return TDSE_OK;
 }
 
-// z-chunk length minimising the estimated makespan ceil(items / P) * (L + 2T)
-// of the dynamically scheduled work list.
+// z-chunk length minimising the estimated makespan ceil(items / P) * (L + 4T) of
+// the dynamically scheduled work list (an item of L planes takes L + 2H = L + 4T
+// iterations: its pipeline fills over the 2T half-step stages at each end).
 int choose_chunk(const std::vector<int> &tiles, const std::vector<int> &nz, int tsteps, int P)
 {
     int nzmax = *std::max_element(nz.begin(), nz.end());
@@ -250,7 +251,7 @@ int choose_chunk(const std::vector<int> &tiles, const std::vector<int> &nz, int 
     for (int L = 8; L <= nzmax; ++L) {
         long long items = 0;
         for (size_t i = 0; i < tiles.size(); ++i) items += static_cast<long long>(tiles[i]) * ((nz[i] + L - 1) / L);
-        const double span = static_cast<double>((items + P - 1) / P) * (L + 2.0 * tsteps);
+        const double span = static_cast<double>((items + P - 1) / P) * (L + 4.0 * tsteps);
         if (span < best - 1e-9 || (std::fabs(span - best) < 1e-9 && L > bestL)) {
             best = span;
             bestL = L;
