@@ -519,10 +519,11 @@ def adjoint_cost(torch, T):
                         "backward_step_us": prof["adjoint_ms"] * 1e3 / max(1, prof["adjoint_steps"]),
                         "backward_steps": prof["adjoint_steps"]}
     out["fused_256x256x512"] = adjoint_roofline(torch, T)
+    out["three_pass_256x256x512"] = adjoint_roofline(torch, T, fused=False)
     return out
 
 
-def adjoint_roofline(torch, T, steps=200):
+def adjoint_roofline(torch, T, steps=200, fused=True):
     """The fused backward step on a grid larger than L2 (256x256x512, the 512^3
     workload's spacing, FP32 + Kahan context, checkpoints every 100 steps): device
     time per backward step from the library's profile against its algorithmic bytes
@@ -544,16 +545,20 @@ def adjoint_roofline(torch, T, steps=200):
         gF = 2 * s.flux_map(0)
         T.tdse_set_profiling(s.ctx, False)
         T.tdse_set_profiling(s.ctx, True)
+        T.tdse_set_adjoint_fused(s.ctx, fused)
         T.tdse_adjoint(s.ctx, 0, gF, None, None)
         pa = T.tdse_get_profile(s.ctx)
     ms = pa["adjoint_ms"] / max(1, pa["adjoint_steps"])
-    bytes_step = 52 * g.cells
+    # the fused step moves each field once (52 B per node); the three passes read
+    # d, R, I, P, Q, then d, P, I, Q, R, gV and write R, Q, then gV, P, I (72 B)
+    bytes_step = (52 if fused else 72) * g.cells
     achieved = bytes_step / (ms * 1e-3) / 1e9
     return {"nodes": g.cells, "steps": steps, "backward_step_ms": ms,
             "forward_step_ms": fwd_ms_per_step, "adjoint_over_forward_device": ms / fwd_ms_per_step,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "bytes_per_node": 52,
-                         "kernel": "adj_fused_kernel<float> (one z-march per backward step)"}}
+                         "frac": achieved / peak, "bytes_per_node": 52 if fused else 72,
+                         "kernel": "adj_fused_kernel<float> (one z-march per backward step)" if fused
+                                   else "adj_b_kernel, adj_flux_q_kernel, adj_de_kernel <float> (three passes)"}}
 
 
 def adjoint_case(args):

@@ -322,12 +322,21 @@ typedef struct tdse_tuning {
     int variant[TDSE_MAX_TBLOCK + 1];           /* [T]: variant index for T fused steps ([0] unused) */
     double ms_per_step[TDSE_MAX_TBLOCK + 1];    /* [T]: measured by tdse_autotune, 0 if not measured */
     char name[TDSE_MAX_TBLOCK + 1][48];         /* [T]: variant names ("" without variants) */
+    int chunk[TDSE_MAX_TBLOCK + 1];             /* [T]: z-planes per work item of the longest member */
 } tdse_tuning;
 TDSE_API int tdse_variant_count(int precision, int tsteps);
 TDSE_API tdse_status tdse_set_variant(tdse_ctx *ctx, int tsteps, int variant);
 TDSE_API tdse_status tdse_autotune(tdse_ctx *ctx, int launches);
 TDSE_API tdse_status tdse_get_tuning(tdse_ctx *ctx, tdse_tuning *out);
 TDSE_API tdse_status tdse_set_graphs(tdse_ctx *ctx, int enable);
+
+/* z-planes per work item of the fused step with `tsteps` steps per launch (planes
+ * <= 0: the makespan model's choice, the default; members shorter than that take
+ * one item per tile).  A work item also loads and computes the 2 tsteps planes on
+ * each side that its pipeline needs, so shorter items cost more arithmetic; they
+ * finish sooner, and neighbouring tiles then read their shared halos while they are
+ * still in L2.  EINVAL: no variants for that depth, planes < 0. */
+TDSE_API tdse_status tdse_set_chunk(tdse_ctx *ctx, int tsteps, int planes);
 
 /* Limit, in nanoseconds, of each wait of a step kernel for a tile's data to land
  * in shared memory (default 2e9 = 2 s; no correct launch comes near it).  When a

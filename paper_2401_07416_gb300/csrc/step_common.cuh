@@ -186,8 +186,10 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 //   PF    planes loaded ahead of use
 //   DSTASH  d is copied out of shared memory as each plane lands (tensor-memory
 //           kernel), so its ring only covers the planes in flight
+//   OWNRINGS  the kernel lays out its own rings (and checks their size itself); SMEM
+//           below is then only the layout of the other kernels
 template <typename Real_, int H_, int TPX_, int ROWS_, int RPT_, bool KAHAN_, int PF_, int MINB_ = 1,
-          bool DSTASH_ = false>
+          bool DSTASH_ = false, bool OWNRINGS_ = false>
 struct Cfg {
     typedef Real_ Real;
     static constexpr int H = H_, TPX = TPX_, ROWS = ROWS_, RPT = RPT_, PF = PF_;
@@ -218,8 +220,8 @@ struct Cfg {
     static_assert(TX > 0 && TY > 0, "halo larger than region");
     static_assert(W <= 256 && ROWS <= 256, "TMA box dimension limit");
     static_assert(H % 2 == 0, "whole time steps only");
-    static_assert(SMEM <= 232448, "more than 227 KB of shared memory per CTA");
-    static_assert(MINB * (SMEM + 1024) <= 233472, "CTAs per SM exceed the shared memory");
+    static_assert(OWNRINGS_ || SMEM <= 232448, "more than 227 KB of shared memory per CTA");
+    static_assert(OWNRINGS_ || MINB * (SMEM + 1024) <= 233472, "CTAs per SM exceed the shared memory");
 };
 
 // One row of an FP32 stage update in paired instructions: the increment

@@ -52,9 +52,9 @@ struct SlimShape {
                                                                                  : MAX_RESIDENT_THREADS;
     static_assert(sizeof(Real) == 4 && C::RPT == 1 && C::DSTASH, "FP32 fields, one row per thread");
     static_assert(H + 1 <= NDT, "d is read H planes back");
-    static_assert(NRS >= PF + 3 && kSlimU % NRS == 0 && kSlimU % NBS == 0 && kSlimU % 3 == 0 &&
-                      kSlimU % 2 == 0 && kSlimU % NDT == 0,
-                  "every slot period must divide the unroll");
+    static_assert(NRS >= PF + 3, "R is read two planes back");
+    static constexpr bool UNROLLABLE = kSlimU % NRS == 0 && kSlimU % NBS == 0 && kSlimU % 3 == 0 &&
+                                       kSlimU % 2 == 0 && kSlimU % NDT == 0;
     static_assert(QUAD_COLS <= 512, "windows exceed tensor memory");
     static_assert(MAX_RESIDENT * NCOLS <= 512, "co-resident CTAs exceed tensor memory");
     static_assert(C::MINB * (SMEM + 1024) <= 233472, "CTAs per SM exceed the shared memory");
@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     typedef float Real;
     typedef SlimShape<C> SS;
     typedef SlimSlots<C> Slots;
+    static_assert(ROLL || SS::UNROLLABLE, "every slot period must divide the unroll");
     constexpr int H = C::H, VEC = C::VEC, W = C::W, ROWS = C::ROWS, PLANE = C::PLANE;
     constexpr int PF = C::PF, NRS = SS::NRS, NBS = SS::NBS;
     constexpr bool KAHAN = C::KAHAN;
@@ -510,10 +511,15 @@ void fill_slim_config(StepConfig *cfg)
     void fill_##FN(StepConfig *cfg) { fill_slim_config<Cfg<__VA_ARGS__>>(cfg); }
 
 // Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched, CTAs per SM,
-//     d kept in TMEM>; "roll": slot offsets rotating in registers
-TDSE_SLIM_VARIANT(slim_k32_t2_w32_r32x1_pf2_b2, false, float, 4, 8, 32, 1, true, 2, 2, true)
-TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf2_b2, true, float, 4, 8, 32, 1, true, 2, 2, true)
-TDSE_SLIM_VARIANT(roll_k32_t2_w32_r28x1_pf2_b2, true, float, 4, 8, 28, 1, true, 2, 2, true)
-TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf2_b2, true, float, 4, 8, 32, 1, false, 2, 2, true)
+//     d kept in TMEM, own rings>; "roll": slot offsets rotating in registers
+TDSE_SLIM_VARIANT(slim_k32_t2_w32_r32x1_pf2_b2, false, float, 4, 8, 32, 1, true, 2, 2, true, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf2_b2, true, float, 4, 8, 32, 1, true, 2, 2, true, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_w32_r28x1_pf2_b2, true, float, 4, 8, 28, 1, true, 2, 2, true, true)
+TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf2_b2, true, float, 4, 8, 32, 1, false, 2, 2, true, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf3_b2, true, float, 4, 8, 32, 1, true, 3, 2, true, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_r32x1_pf2, true, float, 4, 16, 32, 1, true, 2, 1, true, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_r32x1_pf3, true, float, 4, 16, 32, 1, true, 3, 1, true, true)
+TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf3_b2, true, float, 4, 8, 32, 1, false, 3, 2, true, true)
+TDSE_SLIM_VARIANT(roll_f32_t2_r32x1_pf3, true, float, 4, 16, 32, 1, false, 3, 1, true, true)
 
 }  // namespace tdse

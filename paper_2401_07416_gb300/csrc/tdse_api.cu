@@ -45,6 +45,8 @@ struct Member {
 struct StepPlan {
     int tsteps = 0;
     int variant = 0;
+    int chunk_request = 0;          // z-planes per work item requested (0: the makespan model's)
+    int chunk = 0;                  // ... in use (the longest member's)
     StepConfig cfg{};
     MemberDev *d_members = nullptr; // members with tensor maps for this config's box
     WorkDev *d_work = nullptr;
@@ -302,7 +304,7 @@ tdse_status build_plan(tdse_ctx *c, int T, int variant)
     CUDA_TRY(c, cudaGetDevice(&dev));
     CUDA_TRY(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
     const int P = c->sms * std::max(1, cfg.ctas_per_sm);
-    const int L = choose_chunk(tiles, nzs, T, P);
+    const int L = pl.chunk_request > 0 ? pl.chunk_request : choose_chunk(tiles, nzs, T, P);
     int total = 0;
     for (int i = 0; i < B; ++i) {
         w.item_begin[i] = total;
@@ -324,6 +326,7 @@ tdse_status build_plan(tdse_ctx *c, int T, int variant)
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     pl.tsteps = T;
     pl.variant = variant;
+    pl.chunk = L;
     pl.cfg = cfg;
     pl.grid = std::min(total, P);
     drop_graphs(c);
@@ -1524,6 +1527,17 @@ tdse_status tdse_set_adjoint_fused(tdse_ctx *c, int enable)
     return TDSE_OK;
 }
 
+tdse_status tdse_set_chunk(tdse_ctx *c, int tsteps, int planes)
+{
+    if (!c) return TDSE_EINVAL;
+    if (tsteps < 1 || tsteps > kMaxTblock || step_variant_count(c->precision, tsteps) == 0)
+        return fail(c, TDSE_EINVAL, "no kernel variants for %d fused steps", tsteps);
+    if (planes < 0) return fail(c, TDSE_EINVAL, "negative chunk length");
+    TRY(ensure_device(c));
+    c->plans[tsteps].chunk_request = planes;
+    return build_plan(c, tsteps, c->plans[tsteps].variant);
+}
+
 tdse_status tdse_set_graphs(tdse_ctx *c, int enable)
 {
     if (!c) return TDSE_EINVAL;
@@ -1539,6 +1553,7 @@ tdse_status tdse_get_tuning(tdse_ctx *c, tdse_tuning *out)
     for (int T = 1; T <= kMaxTblock; ++T) {
         if (step_variant_count(c->precision, T) == 0) continue;
         out->variant[T] = c->plans[T].variant;
+        out->chunk[T] = c->plans[T].chunk;
         out->ms_per_step[T] = c->tuned_ms_per_step[T];
         const char *n = step_variant_name(c->precision, T, c->plans[T].variant);
         if (n) snprintf(out->name[T], sizeof out->name[T], "%s", n);

@@ -69,7 +69,8 @@ class Profile(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("tblock", ctypes.c_int), ("variant", ctypes.c_int * (MAX_TBLOCK + 1)),
                 ("ms_per_step", ctypes.c_double * (MAX_TBLOCK + 1)),
-                ("name", (ctypes.c_char * 48) * (MAX_TBLOCK + 1))]
+                ("name", (ctypes.c_char * 48) * (MAX_TBLOCK + 1)),
+                ("chunk", ctypes.c_int * (MAX_TBLOCK + 1))]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -106,6 +107,7 @@ SIGNATURES = {
     "tdse_set_graphs": (_I, [_VP, _I]),
     "tdse_set_wait_limit": (_I, [_VP, _LL]),
     "tdse_set_adjoint_fused": (_I, [_VP, _I]),
+    "tdse_set_chunk": (_I, [_VP, _I, _I]),
     "tdse_set_profiling": (_I, [_VP, _I]),
     "tdse_get_profile": (_I, [_VP, ctypes.POINTER(Profile)]),
     "tdse_observables_static": (_I, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP]),
@@ -352,11 +354,16 @@ def tdse_get_tuning(ctx) -> dict:
     return {"tblock": t.tblock,
             "variant": {T: t.variant[T] for T in depths},
             "ms_per_step": {T: t.ms_per_step[T] for T in depths},
-            "name": {T: t.name[T].value.decode() for T in depths}}
+            "name": {T: t.name[T].value.decode() for T in depths},
+            "chunk": {T: t.chunk[T] for T in depths}}
 
 
 def tdse_set_graphs(ctx, enable: bool):
     _check(ctx, lib().tdse_set_graphs(ctx, int(bool(enable))))
+
+
+def tdse_set_chunk(ctx, tsteps: int, planes: int):
+    _check(ctx, lib().tdse_set_chunk(ctx, tsteps, planes))
 
 
 def tdse_set_adjoint_fused(ctx, enable: bool):

@@ -53,7 +53,7 @@ int main(void) {
          sizeof(tdse_profile), offsetof(tdse_profile, launches_at_depth),
          offsetof(tdse_profile, ms_at_depth), sizeof(tdse_tuning), offsetof(tdse_tuning, ms_per_step),
          offsetof(tdse_tuning, name), TDSE_MAX_TBLOCK);
-  printf("%zu\n", offsetof(tdse_profile, adjoint_ms));
+  printf("%zu %zu\n", offsetof(tdse_profile, adjoint_ms), offsetof(tdse_tuning, chunk));
   return 0;
 }
 """)
@@ -65,7 +65,8 @@ int main(void) {
     assert vals == [ctypes.sizeof(P), P.hx.offset, P.bc.offset, P.mask_eta.offset,
                     P.det_k.offset, P.tblock.offset, ctypes.sizeof(T.Obs), ctypes.sizeof(Pr),
                     Pr.launches_at_depth.offset, Pr.ms_at_depth.offset, ctypes.sizeof(Tu),
-                    Tu.ms_per_step.offset, Tu.name.offset, T.MAX_TBLOCK, Pr.adjoint_ms.offset]
+                    Tu.ms_per_step.offset, Tu.name.offset, T.MAX_TBLOCK, Pr.adjoint_ms.offset,
+                    Tu.chunk.offset]
 
 
 def _params(**kw):
