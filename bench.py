@@ -142,7 +142,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-KERNEL_SOURCES = ("step_common.cuh", "step_kernels.cu", "step_tmem.cu")
+KERNEL_SOURCES = ("step_common.cuh", "tmem_common.cuh", "step_kernels.cu", "step_tmem.cu", "step_slim.cu")
 
 
 def kernel_source_hash() -> str:

@@ -261,11 +261,12 @@ TDSE_API tdse_status tdse_dissimilarity(const double *frames, int K, int M, long
 TDSE_API tdse_status tdse_adjoint(tdse_ctx *ctx, int member, const double *dL_dF, double *dL_dV,
                          double *dL_datoms, int on_device);
 
-/* Form of tdse_adjoint's backward step: enable != 0 (the default) runs each step as
- * one z-march over tiles that reads the reconstructed state and its adjoint from
- * one set of buffers and writes the next into a second set (four more arrays of
- * the grid's size); 0 runs three passes in place.  Both give the same numbers
- * (the per-cell arithmetic is shared). */
+/* Form of tdse_adjoint's backward step: 0 (the default) runs three passes in
+ * place; enable != 0 runs each step as one z-march over tiles that reads the
+ * reconstructed state and its adjoint from one set of buffers and writes the next
+ * into a second set (four more arrays of the grid's size; it moves each field once
+ * per step, but measured slower than the three passes on GB300).  Both give the
+ * same numbers, bit for bit (the per-cell arithmetic is shared). */
 TDSE_API tdse_status tdse_set_adjoint_fused(tdse_ctx *ctx, int enable);
 
 /* Save / restore the whole context state to / from a binary file: for every

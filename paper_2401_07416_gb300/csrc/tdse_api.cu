@@ -92,7 +92,7 @@ struct tdse_ctx {
     std::vector<Interval> pending;
     size_t events_used = 0;
     bool graphs = true;                            // replay step segments as CUDA graphs
-    bool adjoint_fused = true;                     // one z-march per backward step
+    bool adjoint_fused = false;                    // one z-march per backward step (else three passes)
     cudaStream_t gstream = nullptr;                // capture/replay stream
     cudaEvent_t gev[2] = {nullptr, nullptr};
     struct GraphEntry {
