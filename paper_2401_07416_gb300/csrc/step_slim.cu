@@ -116,10 +116,14 @@ struct SlimSlots {
     }
 };
 
-// ROLL: the z-march as a plain loop whose slot offsets rotate in registers
-// (compact code), instead of unrolled by 6 with constant offsets (fewer
-// instructions, but six copies of the stages for the instruction cache).
-template <class C, bool ROLL>
+// MODE: how the z-march is laid out.
+//   kSlimUnrolled  unrolled by 6 with constant offsets: fewest instructions, but twelve
+//                  copies of the stages (fast and general path) for the instruction cache;
+//   kSlimRolled    a plain loop whose slot offsets rotate in registers: compact code;
+//   kSlimHybrid    blocks of 6 planes that all take the fast path run unrolled (six
+//                  copies of the fast stages), every other block the rolled loop.
+constexpr int kSlimUnrolled = 0, kSlimRolled = 1, kSlimHybrid = 2;
+template <class C, int MODE>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fused_step_slim_kernel(const MemberDev *__restrict__ members, const WorkDev *__restrict__ work,
                            int *counter, int *status, int in_buf, unsigned long long wait_ns)
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     typedef float Real;
     typedef SlimShape<C> SS;
     typedef SlimSlots<C> Slots;
-    static_assert(ROLL || SS::UNROLLABLE, "every slot period must divide the unroll");
+    static_assert(MODE == kSlimRolled || SS::UNROLLABLE, "every slot period must divide the unroll");
     constexpr int H = C::H, VEC = C::VEC, W = C::W, ROWS = C::ROWS, PLANE = C::PLANE;
     constexpr int PF = C::PF, NRS = SS::NRS, NBS = SS::NBS;
     constexpr bool KAHAN = C::KAHAN;
@@ -407,8 +411,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             }
         };
 
-        // One iteration: wait for plane L0 + it, refill, d to tensor memory, stages.
-        auto plane_step = [&](const int it, const Slots &sl) -> bool {
+        // One iteration: wait for plane L0 + it, refill, d to tensor memory, stages
+        // (ONLY_FAST: the caller knows the plane takes the fast path).
+        auto plane_step = [&](const int it, const Slots &sl, auto ONLY_FASTc) -> bool {
             const int p = L0 + it;
             if (tid == 0) {
                 if (mbar_wait_bounded(&bars[sl.bar], sl.par, wait_ns)) {
@@ -433,29 +438,55 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 ld_vec<Real>(ringD + sl.bb + own, dp);
                 tmem_st4(tbase + sl.d[0], dp);
             }
-            const bool fast = !tile_walls && it >= 2 * H && p >= fast_lo && p < fast_hi &&
-                              !(flux_owner && p >= kd + 2 && p <= kd + H);
-            if (fast)
+            if constexpr (decltype(ONLY_FASTc)::value) {
                 stages(it, p, sl, std::true_type{});
-            else
-                stages(it, p, sl, std::false_type{});
+            } else {
+                const bool fast = !tile_walls && it >= 2 * H && p >= fast_lo && p < fast_hi &&
+                                  !(flux_owner && p >= kd + 2 && p <= kd + H);
+                if (fast)
+                    stages(it, p, sl, std::true_type{});
+                else
+                    stages(it, p, sl, std::false_type{});
+            }
             return true;
         };
+        const std::false_type any{};
+        const std::true_type only_fast{};
 
-        if constexpr (ROLL) {
+        if constexpr (MODE == kSlimRolled) {
             Slots sl = Slots::at(0);
             for (int it = 0; it < nit; ++it) {
-                if (!plane_step(it, sl)) break;
+                if (!plane_step(it, sl, any)) break;
                 sl.advance();
             }
-        } else {
+        } else if constexpr (MODE == kSlimUnrolled) {
             for (int it0 = 0; it0 < nit; it0 += kSlimU) {
-                if (!plane_step(it0, Slots::at(0))) break;
-                if (it0 + 1 >= nit || !plane_step(it0 + 1, Slots::at(1))) break;
-                if (it0 + 2 >= nit || !plane_step(it0 + 2, Slots::at(2))) break;
-                if (it0 + 3 >= nit || !plane_step(it0 + 3, Slots::at(3))) break;
-                if (it0 + 4 >= nit || !plane_step(it0 + 4, Slots::at(4))) break;
-                if (it0 + 5 >= nit || !plane_step(it0 + 5, Slots::at(5))) break;
+                if (!plane_step(it0, Slots::at(0), any)) break;
+                if (it0 + 1 >= nit || !plane_step(it0 + 1, Slots::at(1), any)) break;
+                if (it0 + 2 >= nit || !plane_step(it0 + 2, Slots::at(2), any)) break;
+                if (it0 + 3 >= nit || !plane_step(it0 + 3, Slots::at(3), any)) break;
+                if (it0 + 4 >= nit || !plane_step(it0 + 4, Slots::at(4), any)) break;
+                if (it0 + 5 >= nit || !plane_step(it0 + 5, Slots::at(5), any)) break;
+            }
+        } else {
+            bool ok = true;
+            for (int it0 = 0; it0 < nit && ok; it0 += kSlimU) {
+                const int p0 = L0 + it0;
+                const bool block_fast = !tile_walls && it0 >= 2 * H && it0 + kSlimU <= nit && p0 >= fast_lo &&
+                                        p0 + kSlimU - 1 < fast_hi &&
+                                        !(flux_owner && p0 <= kd + H && p0 + kSlimU - 1 >= kd + 2);
+                if (block_fast) {
+                    ok = plane_step(it0, Slots::at(0), only_fast) && plane_step(it0 + 1, Slots::at(1), only_fast) &&
+                         plane_step(it0 + 2, Slots::at(2), only_fast) &&
+                         plane_step(it0 + 3, Slots::at(3), only_fast) &&
+                         plane_step(it0 + 4, Slots::at(4), only_fast) && plane_step(it0 + 5, Slots::at(5), only_fast);
+                } else {
+                    Slots sl = Slots::at(0);
+                    for (int k = 0; k < kSlimU && it0 + k < nit && ok; ++k) {
+                        ok = plane_step(it0 + k, sl, any);
+                        sl.advance();
+                    }
+                }
             }
         }
 
@@ -480,14 +511,14 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     if (warp == 0) tmem_dealloc(s_tmem, SS::NCOLS);
 }
 
-template <class C, bool ROLL>
+template <class C, int MODE>
 cudaError_t launch_slim_cfg(const StepLaunch &L)
 {
     typedef SlimShape<C> SS;
     static std::atomic<uint64_t> smem_allowed{0};   // one bit per device
-    cudaError_t e = allow_dynamic_smem(fused_step_slim_kernel<C, ROLL>, SS::SMEM, smem_allowed);
+    cudaError_t e = allow_dynamic_smem(fused_step_slim_kernel<C, MODE>, SS::SMEM, smem_allowed);
     if (e != cudaSuccess) return e;
-    fused_step_slim_kernel<C, ROLL><<<L.grid, C::NT, SS::SMEM, L.stream>>>(
+    fused_step_slim_kernel<C, MODE><<<L.grid, C::NT, SS::SMEM, L.stream>>>(
         L.members, L.work, L.counter, L.status, L.in_buf, L.wait_ns);
     return cudaGetLastError();
 }
@@ -506,20 +537,22 @@ void fill_slim_config(StepConfig *cfg)
 
 }  // namespace
 
-#define TDSE_SLIM_VARIANT(FN, ROLL, ...)                                                \
-    cudaError_t launch_##FN(const StepLaunch &L) { return launch_slim_cfg<Cfg<__VA_ARGS__>, ROLL>(L); } \
+#define TDSE_SLIM_VARIANT(FN, MODE, ...)                                                \
+    cudaError_t launch_##FN(const StepLaunch &L) { return launch_slim_cfg<Cfg<__VA_ARGS__>, MODE>(L); } \
     void fill_##FN(StepConfig *cfg) { fill_slim_config<Cfg<__VA_ARGS__>>(cfg); }
 
 // Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched, CTAs per SM,
-//     d kept in TMEM, own rings>; "roll": slot offsets rotating in registers
-TDSE_SLIM_VARIANT(slim_k32_t2_w32_r32x1_pf2_b2, false, float, 4, 8, 32, 1, true, 2, 2, true, true)
-TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf2_b2, true, float, 4, 8, 32, 1, true, 2, 2, true, true)
-TDSE_SLIM_VARIANT(roll_k32_t2_w32_r28x1_pf2_b2, true, float, 4, 8, 28, 1, true, 2, 2, true, true)
-TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf2_b2, true, float, 4, 8, 32, 1, false, 2, 2, true, true)
-TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf3_b2, true, float, 4, 8, 32, 1, true, 3, 2, true, true)
-TDSE_SLIM_VARIANT(roll_k32_t2_r32x1_pf2, true, float, 4, 16, 32, 1, true, 2, 1, true, true)
-TDSE_SLIM_VARIANT(roll_k32_t2_r32x1_pf3, true, float, 4, 16, 32, 1, true, 3, 1, true, true)
-TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf3_b2, true, float, 4, 8, 32, 1, false, 3, 2, true, true)
-TDSE_SLIM_VARIANT(roll_f32_t2_r32x1_pf3, true, float, 4, 16, 32, 1, false, 3, 1, true, true)
+//     d kept in TMEM, own rings>; "slim": unrolled, "roll": rolled, "hyb": hybrid (MODE)
+TDSE_SLIM_VARIANT(slim_k32_t2_w32_r32x1_pf2_b2, kSlimUnrolled, float, 4, 8, 32, 1, true, 2, 2, true, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf2_b2, kSlimRolled, float, 4, 8, 32, 1, true, 2, 2, true, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_w32_r28x1_pf2_b2, kSlimRolled, float, 4, 8, 28, 1, true, 2, 2, true, true)
+TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf2_b2, kSlimRolled, float, 4, 8, 32, 1, false, 2, 2, true, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf3_b2, kSlimRolled, float, 4, 8, 32, 1, true, 3, 2, true, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_r32x1_pf2, kSlimRolled, float, 4, 16, 32, 1, true, 2, 1, true, true)
+TDSE_SLIM_VARIANT(roll_k32_t2_r32x1_pf3, kSlimRolled, float, 4, 16, 32, 1, true, 3, 1, true, true)
+TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf3_b2, kSlimRolled, float, 4, 8, 32, 1, false, 3, 2, true, true)
+TDSE_SLIM_VARIANT(roll_f32_t2_r32x1_pf3, kSlimRolled, float, 4, 16, 32, 1, false, 3, 1, true, true)
+TDSE_SLIM_VARIANT(hyb_k32_t2_w32_r32x1_pf2_b2, kSlimHybrid, float, 4, 8, 32, 1, true, 2, 2, true, true)
+TDSE_SLIM_VARIANT(hyb_f32_t2_w32_r32x1_pf2_b2, kSlimHybrid, float, 4, 8, 32, 1, false, 2, 2, true, true)
 
 }  // namespace tdse
