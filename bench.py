@@ -282,7 +282,7 @@ def make_ctx(T, wl, precision, tblock, V_dev=None, autotune=True):
     else:
         s.set_potential(0, V_dev)
     if autotune:
-        s.autotune(2)
+        s.autotune(4)
     s.set_packet(0, wl.packet)
     return s
 
@@ -725,7 +725,7 @@ def main():
                "statistic": f"median of {len(runs)} complete runs"}
         del V_host
         # FP64 unfused step and the FP32 variants on the same grid (same potential)
-        variants = [(W.FP64, 1)] + [(p, t) for p in (W.FP32, W.FP32_KAHAN) for t in (1, 2)]
+        variants = [(W.FP64, 1)] + [(p, t) for p in (W.FP32, W.FP32_KAHAN) for t in (1, 2, 3, 4)]
         for vp, vt in variants:
             steps_v = max(10, args.steps // (8 if vp == W.FP64 else 2))
             sv = make_ctx(T, W.config5(vp), vp, vt, V_dev)
@@ -736,6 +736,7 @@ def main():
             extras[f"{PREC_NAME[vp]}_t{vt}"] = {
                 "value": cells * steps_v / (vms * 1e-3), "unit": "cell-updates/s",
                 "steps": steps_v, "variant": vname, "avg_launch_ms": vlaunch,
+                "ms_per_step_of_launches": vlaunch / vt,
                 "hbm_frac_of_algorithmic_bytes": BYTES_PER_NODE[vp] * cells / (vlaunch * 1e-3) / 1e9 / hbm_peak}
         extras["speedup_vs_fp64_plain"] = value / world / extras["f64_t1"]["value"]
         extras["batched_48_films"] = batch_throughput(torch, T, max(20, args.steps // 2),

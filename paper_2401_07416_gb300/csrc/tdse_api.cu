@@ -1603,25 +1603,49 @@ tdse_status tdse_autotune(tdse_ctx *c, int launches)
         c->tblock = T;
         double best = 1e300;
         int bestv = 0;
-        for (int v = 0; v < step_variant_count(c->precision, T) && st == TDSE_OK; ++v) {
-            if ((st = build_plan(c, T, v)) != TDSE_OK) break;
-            if ((st = launch_fused(c, T)) != TDSE_OK) break;
+        // ms per step of the plan as built (one warm-up launch, then `launches`)
+        auto trial = [&](double *per_step) -> tdse_status {
+            TRY(launch_fused(c, T));
             cudaEventRecord(e0, c->stream);
-            for (int l = 0; l < launches && st == TDSE_OK; ++l) st = launch_fused(c, T);
+            for (int l = 0; l < launches; ++l) TRY(launch_fused(c, T));
             cudaEventRecord(e1, c->stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                st = fail(c, TDSE_ECUDA, "autotune launch failed");
-                break;
-            }
+            if (cudaEventSynchronize(e1) != cudaSuccess) return fail(c, TDSE_ECUDA, "autotune launch failed");
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            const double per_step = ms / (launches * T);
+            *per_step = ms / (launches * T);
+            return TDSE_OK;
+        };
+        StepPlan &pl = c->plans[T];
+        const int request = pl.chunk_request;   // a chunk fixed by tdse_set_chunk stays
+        for (int v = 0; v < step_variant_count(c->precision, T) && st == TDSE_OK; ++v) {
+            double per_step = 0.0;
+            if ((st = build_plan(c, T, v)) != TDSE_OK || (st = trial(&per_step)) != TDSE_OK) break;
             if (per_step < best) {
                 best = per_step;
                 bestv = v;
             }
         }
         if (st == TDSE_OK) st = build_plan(c, T, bestv);
+        // shorter z-chunks for the chosen variant: more pipeline fill per plane, but
+        // neighbouring tiles start and finish closer together and share their halo
+        // rows through L2 (the makespan model counts the first only)
+        if (st == TDSE_OK && request == 0) {
+            const int model = pl.chunk;
+            int best_chunk = 0;
+            for (int frac4 : {3, 2}) {
+                const int L = model * frac4 / 4;
+                if (L < 16) continue;
+                double per_step = 0.0;
+                pl.chunk_request = L;
+                if ((st = build_plan(c, T, bestv)) != TDSE_OK || (st = trial(&per_step)) != TDSE_OK) break;
+                if (per_step < best) {
+                    best = per_step;
+                    best_chunk = L;
+                }
+            }
+            pl.chunk_request = best_chunk;
+            if (st == TDSE_OK) st = build_plan(c, T, bestv);
+        }
         c->tuned_ms_per_step[T] = best;
     }
     cudaEventDestroy(e0);
