@@ -433,27 +433,27 @@ struct ColumnSum<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
-// Sums of the detector flux map (last step and time-integrated) over this
-// block's share of the pixels.
-__device__ __forceinline__ void flux_partials(const MemberDev &m, double &fl, double &fi)
+// Sums of the detector flux map (last step and time-integrated) over block lb's
+// share (of nb) of the pixels.
+__device__ __forceinline__ void flux_partials(const MemberDev &m, double &fl, double &fi, int lb, int nb)
 {
     if (m.det_k < 0) return;
     const long long npix = static_cast<long long>(m.nx) * m.ny;
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < npix;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    for (long long i = lb * static_cast<long long>(blockDim.x) + threadIdx.x; i < npix;
+         i += static_cast<long long>(nb) * blockDim.x) {
         fl += m.jlast[i];
         fi += m.flux[i];
     }
 }
 
 __device__ __forceinline__ void write_partials(double *partials, double *sh, double q, double pn,
-                                               double e, double fl, double fi)
+                                               double e, double fl, double fi, int lb)
 {
     const double v[5] = {q, pn, e, fl, fi};
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const double t = block_sum(v[k], sh);
-        if (threadIdx.x == 0) partials[kObsPartialsPerBlock * blockIdx.x + k] = t;
+        if (threadIdx.x == 0) partials[kObsPartialsPerBlock * lb + k] = t;
     }
 }
 
@@ -463,12 +463,13 @@ __device__ __forceinline__ void write_partials(double *partials, double *sh, dou
 // in ColumnSum.  Items go to threads in a fixed order and the block count is fixed
 // by the grid shape, so the sums are reproducible.  V = 1 is the scalar form for
 // rows whose length is not a multiple of the vector width.
+// Block lb of the nb blocks that reduce member m (the work of one block of
+// observables_kernel, wherever it is launched).
 template <typename Real, int V, int ZC>
-__global__ void __launch_bounds__(kObsThreads)
-    observables_kernel(MemberDev m, int buf, double *__restrict__ partials, int zch_arg)
+__device__ __forceinline__ void observables_block(const MemberDev &m, int buf, double *__restrict__ partials,
+                                                  int zch_arg, int lb, int nb, double *sh)
 {
     const int zch = ZC > 0 ? ZC : zch_arg;   // ZC > 0: the chunk is a compile-time constant
-    __shared__ double sh[32];
     const Real *__restrict__ R = reinterpret_cast<const Real *>(m.R[buf]);
     const Real *__restrict__ I = reinterpret_cast<const Real *>(m.I[buf]);
     const Real *__restrict__ D = reinterpret_cast<const Real *>(m.d);
@@ -494,8 +495,8 @@ __global__ void __launch_bounds__(kObsThreads)
         }
     };
     double q = 0.0, pn = 0.0, e = 0.0;
-    for (long long item = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-         item < nitems; item += static_cast<long long>(gridDim.x) * blockDim.x) {
+    for (long long item = lb * static_cast<long long>(blockDim.x) + threadIdx.x;
+         item < nitems; item += static_cast<long long>(nb) * blockDim.x) {
         const long long grp = item % ngrp;
         const int z0 = static_cast<int>(item / ngrp) * zch;
         const int z1 = min(z0 + zch, m.nz);
@@ -570,17 +571,41 @@ __global__ void __launch_bounds__(kObsThreads)
         e += se.value();
     }
     double fl = 0.0, fi = 0.0;
-    flux_partials(m, fl, fi);
-    write_partials(partials, sh, q, pn, e, fl, fi);
+    flux_partials(m, fl, fi, lb, nb);
+    write_partials(partials, sh, q, pn, e, fl, fi, lb);
+}
+
+template <typename Real, int V, int ZC>
+__global__ void __launch_bounds__(kObsThreads)
+    observables_kernel(MemberDev m, int buf, double *__restrict__ partials, int zch_arg)
+{
+    __shared__ double sh[32];
+    observables_block<Real, V, ZC>(m, buf, partials, zch_arg, blockIdx.x, gridDim.x, sh);
+}
+
+// Every member of a batch in one launch: block b belongs to the member whose slice
+// of blocks contains it and does exactly the work of that member's block b - begin
+// in a launch of its own (same items, same order), so the sums are the same bits.
+template <typename Real, int V>
+__global__ void __launch_bounds__(kObsThreads)
+    observables_batch_kernel(const MemberDev *__restrict__ members, const ObsSlice *__restrict__ slices,
+                             int nmembers, int buf, double *__restrict__ partials)
+{
+    __shared__ double sh[32];
+    int mm = 0;
+    while (mm + 1 < nmembers && static_cast<int>(blockIdx.x) >= slices[mm + 1].block_begin) ++mm;
+    const ObsSlice sl = slices[mm];
+    observables_block<Real, V, 0>(members[mm], buf, partials + kObsPartialsPerBlock * sl.block_begin, sl.zch,
+                                  static_cast<int>(blockIdx.x) - sl.block_begin, sl.nparts, sh);
 }
 
 // record = {step, Q, norm_paper, energy, flux_last, flux_integrated}; sets
 // status bit 1 on non-finite Q or Q > (1 + 1e-3) q_ref (q_ref <= 0: no check).
-__global__ void observables_finalize_kernel(MemberDev m, const double *__restrict__ partials,
-                                            int nparts, double *__restrict__ record,
-                                            int *status, double q_ref, long long step)
+__device__ __forceinline__ void observables_finalize_block(const MemberDev &m, const double *__restrict__ partials,
+                                                           int nparts, double *__restrict__ record,
+                                                           int *status, double q_ref, long long step,
+                                                           double *sh)
 {
-    __shared__ double sh[32];
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int i = threadIdx.x; i < nparts; i += blockDim.x)
 #pragma unroll
@@ -600,6 +625,27 @@ __global__ void observables_finalize_kernel(MemberDev m, const double *__restric
         if (!isfinite(q * h3) || !isfinite(e) || (q_ref > 0.0 && q * h3 > q_ref * (1.0 + 1e-3)))
             atomicOr(status, 2);
     }
+}
+
+__global__ void observables_finalize_kernel(MemberDev m, const double *__restrict__ partials,
+                                            int nparts, double *__restrict__ record,
+                                            int *status, double q_ref, long long step)
+{
+    __shared__ double sh[32];
+    observables_finalize_block(m, partials, nparts, record, status, q_ref, step, sh);
+}
+
+// One block per member of a batch: its record goes to records + member * rec_stride.
+__global__ void observables_batch_finalize_kernel(const MemberDev *__restrict__ members,
+                                                  const ObsSlice *__restrict__ slices,
+                                                  const double *__restrict__ partials,
+                                                  double *__restrict__ records, long long rec_stride,
+                                                  int *status, long long step)
+{
+    __shared__ double sh[32];
+    const ObsSlice sl = slices[blockIdx.x];
+    observables_finalize_block(members[blockIdx.x], partials + kObsPartialsPerBlock * sl.block_begin,
+                               sl.nparts, records + blockIdx.x * rec_stride, status, sl.q_ref, step, sh);
 }
 
 int grid_for(long long n)
@@ -814,9 +860,7 @@ cudaError_t launch_interp(const MemberDev &m, double hx, double hy, double hz, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_observables(const MemberDev &m, int precision, int buf, double *partials,
-                               double *record, int *status, double q_ref, long long step,
-                               cudaStream_t s)
+void observables_shape(const MemberDev &m, int precision, int *nparts_out, int *zch_out)
 {
     const int vec = precision == 0 ? 2 : 4;          // one 16-byte vector per field and plane
     const bool vector = m.nx % vec == 0;
@@ -828,8 +872,36 @@ cudaError_t launch_observables(const MemberDev &m, int precision, int buf, doubl
     const int zch = static_cast<int>(
         std::min<long long>(kObsZ, std::max<long long>(4, (m.nz + want - 1) / want)));
     const long long nitems = groups * ((m.nz + zch - 1) / zch);
-    const int nparts = static_cast<int>(
+    *zch_out = zch;
+    *nparts_out = static_cast<int>(
         std::max<long long>(1, std::min<long long>((nitems + kObsThreads - 1) / kObsThreads, kObsParts)));
+}
+
+cudaError_t launch_observables_batch(const MemberDev *members, const ObsSlice *slices, int nmembers,
+                                     int total_blocks, int precision, int buf, double *partials,
+                                     double *records, long long rec_stride, int *status, long long step,
+                                     cudaStream_t s)
+{
+    // every member's nx is a multiple of 4, so the vector form applies to all
+    if (precision == 0)
+        observables_batch_kernel<double, 2><<<total_blocks, kObsThreads, 0, s>>>(members, slices, nmembers,
+                                                                                 buf, partials);
+    else
+        observables_batch_kernel<float, 4><<<total_blocks, kObsThreads, 0, s>>>(members, slices, nmembers,
+                                                                                buf, partials);
+    observables_batch_finalize_kernel<<<nmembers, kThreads, 0, s>>>(members, slices, partials, records,
+                                                                    rec_stride, status, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observables(const MemberDev &m, int precision, int buf, double *partials,
+                               double *record, int *status, double q_ref, long long step,
+                               cudaStream_t s)
+{
+    const int vec = precision == 0 ? 2 : 4;
+    const bool vector = m.nx % vec == 0;
+    int nparts = 0, zch = 0;
+    observables_shape(m, precision, &nparts, &zch);
     auto run = [&](auto kernel_full, auto kernel_short) {
         if (zch == kObsZ) kernel_full<<<nparts, kObsThreads, 0, s>>>(m, buf, partials, zch);
         else kernel_short<<<nparts, kObsThreads, 0, s>>>(m, buf, partials, zch);

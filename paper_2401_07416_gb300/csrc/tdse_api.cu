@@ -77,6 +77,10 @@ struct tdse_ctx {
     bool failed = false;                           // a step kernel timed out or the run diverged
     unsigned long long wait_ns = kDefaultWaitNs;   // limit of each wait for a tile's data
     double *d_partials = nullptr;
+    // batched reductions (more than one member): each member's block slice
+    std::vector<ObsSlice> obs_slices;
+    ObsSlice *d_obs_slices = nullptr;
+    int obs_blocks = 0;
     double *d_records = nullptr;    // [B][kRecCap][kRecLen]
     int cur = 0;                    // ping-pong buffer holding the state
     long long step = 0;
@@ -408,8 +412,21 @@ tdse_status ensure_device(tdse_ctx *c)
                               cudaHostAllocDefault));
     for (int k = 0; k < kStatusLag; ++k)
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->status_ev[k], cudaEventDisableTiming));
-    TRY(dalloc(c, kObsParts * kObsPartialsPerBlock * sizeof(double), &p));
+    // each member's reduction blocks, one slice after the other (batched launches)
+    c->obs_slices.resize(c->m.size());
+    c->obs_blocks = 0;
+    for (size_t i = 0; i < c->m.size(); ++i) {
+        ObsSlice &sl = c->obs_slices[i];
+        observables_shape(c->m[i].dev, c->precision, &sl.nparts, &sl.zch);
+        sl.block_begin = c->obs_blocks;
+        sl.q_ref = 0.0;
+        c->obs_blocks += sl.nparts;
+    }
+    TRY(dalloc(c, static_cast<size_t>(std::max(kObsParts, c->obs_blocks)) * kObsPartialsPerBlock * sizeof(double),
+               &p));
     c->d_partials = static_cast<double *>(p);
+    TRY(dalloc(c, c->obs_slices.size() * sizeof(ObsSlice), &p));
+    c->d_obs_slices = static_cast<ObsSlice *>(p);
     TRY(dalloc(c, c->m.size() * kRecCap * kRecLen * sizeof(double), &p));
     c->d_records = static_cast<double *>(p);
     TRY(build_plans(c));
@@ -566,7 +583,7 @@ tdse_status resolve_timers(tdse_ctx *c)
                 c->prof.ms_at_depth[iv.depth] += ms;
             }
         } else if (iv.kind == 1) {
-            c->prof.reduce_launches += 2 * static_cast<long long>(c->m.size());
+            c->prof.reduce_launches += 2;   // the reduction and its finalize (all members at once)
             c->prof.reduce_ms += ms;
         } else {
             c->prof.adjoint_steps += iv.launches;
@@ -707,7 +724,15 @@ tdse_status observe_all(tdse_ctx *c, int slot)
 {
     int t0;
     TRY(timer_start(c, &t0));
-    for (size_t i = 0; i < c->m.size(); ++i) TRY(observe(c, static_cast<int>(i), slot, c->m[i].q0));
+    if (c->m.size() == 1) {
+        TRY(observe(c, 0, slot, c->m[0].q0));
+    } else {   // every member in one reduction launch and one finalize launch
+        CUDA_TRY(c, launch_observables_batch(c->plans[1].d_members, c->d_obs_slices,
+                                             static_cast<int>(c->m.size()), c->obs_blocks, c->precision,
+                                             c->cur, c->d_partials, c->d_records + slot * kRecLen,
+                                             static_cast<long long>(kRecCap) * kRecLen, c->d_status, c->step,
+                                             c->stream));
+    }
     TRY(timer_stop(c, t0, 1));
     return TDSE_OK;
 }
@@ -766,6 +791,8 @@ tdse_status reset_run(tdse_ctx *c, int i)
     double rec[kRecLen];
     TRY(current_obs(c, i, rec));
     mb.q0 = rec[1];
+    c->obs_slices[i].q_ref = mb.q0;
+    CUDA_TRY(c, cudaMemcpy(c->d_obs_slices + i, &c->obs_slices[i], sizeof(ObsSlice), cudaMemcpyHostToDevice));
     mb.hist.insert(mb.hist.end(), {static_cast<double>(c->step), rec[1], rec[2], rec[3]});
     mb.frame_steps.clear();
     TRY(capture_frame(c, i));
@@ -1496,6 +1523,9 @@ tdse_status tdse_load_state(tdse_ctx *c, const char *path)
     }
     fclose(f);
     c->step = step;
+    for (size_t i = 0; i < c->m.size(); ++i) c->obs_slices[i].q_ref = c->m[i].q0;
+    CUDA_TRY(c, cudaMemcpy(c->d_obs_slices, c->obs_slices.data(), c->obs_slices.size() * sizeof(ObsSlice),
+                           cudaMemcpyHostToDevice));
     return TDSE_OK;
 }
 

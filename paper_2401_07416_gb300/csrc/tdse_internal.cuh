@@ -123,6 +123,21 @@ cudaError_t launch_field_io(const MemberDev &m, void *field, int elem, double *a
 cudaError_t launch_observables(const MemberDev &m, int precision, int buf, double *partials,
                                double *record, int *status, double q_ref, long long step,
                                cudaStream_t s);
+// One member's share of a batched reduction launch (observables_batch_kernel).
+struct ObsSlice {
+    int block_begin;       // its first block in the launch
+    int nparts;            // its blocks (as in a launch of its own)
+    int zch;               // z planes per work item
+    double q_ref;          // Q of its first observation (<= 0: no growth check)
+};
+// Blocks and z-chunk of one member's reduction (the same in both launch forms).
+void observables_shape(const MemberDev &m, int precision, int *nparts, int *zch);
+// Every member's reduction in two launches; member i's record goes to
+// records + i * rec_stride.  Bitwise the same records as launch_observables per member.
+cudaError_t launch_observables_batch(const MemberDev *members, const ObsSlice *slices, int nmembers,
+                                     int total_blocks, int precision, int buf, double *partials,
+                                     double *records, long long rec_stride, int *status, long long step,
+                                     cudaStream_t s);
 constexpr int kObsParts = 1216;     // fixed block count: the reduction order never changes
 constexpr int kObsZ = 64;           // largest z-chunk of an observables work item
 constexpr int kObsThreads = 256;    // observables block size (8 blocks per SM fill an SM)

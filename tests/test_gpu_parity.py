@@ -208,6 +208,31 @@ def test_batched_members_equal_solo_runs(T):
             assert np.array_equal(batch[i][1], F)
 
 
+@pytest.mark.parametrize("precision", ["FP32_KAHAN", "FP64"])
+def test_batched_reductions_equal_solo_reductions(T, precision):
+    """A context with several members reduces all of them in one launch: every
+    member's recorded Q, paper norm and energy equal, bit for bit, those of the
+    same member run alone (same blocks, same items, same order)."""
+    prec = getattr(T, precision)
+    cs = [case(n, seed=4) for n in ["walls", "slab", "mixed", "periodic"]]
+    s = make_sim([c[0] for c in cs], prec)
+    for i, (g, V, p) in enumerate(cs):
+        s.set_potential(i, V)
+        s.set_packet(i, p)
+    s.step(45)
+    hist = [s.history(i) for i in range(len(cs))]
+    s.close()
+    for i, (g, V, p) in enumerate(cs):
+        solo = make_sim(g, prec)
+        solo.set_potential(0, V)
+        solo.set_packet(0, p)
+        solo.step(45)
+        h = solo.history(0)
+        solo.close()
+        assert h.shape == hist[i].shape == (3, 4)
+        assert np.array_equal(h, hist[i]), i
+
+
 def test_config1_free_packet_full_size(T):
     """64^3 FP64, 500 steps: GPU = oracle to 1e-11, and the oracle-pinned closed-form
     drift of the centroid holds for the GPU result too."""
