@@ -60,34 +60,42 @@ struct SlimShape {
     static_assert(C::MINB * (SMEM + 1024) <= 233472, "CTAs per SM exceed the shared memory");
 };
 
-// Slot offsets of one iteration (it = it0 + k, it0 a multiple of kSlimU): ring
-// offsets in elements, tensor-memory columns relative to the thread's base.
+// Slots of one iteration (it = it0 + k, it0 a multiple of kSlimU), as this thread
+// uses them: element offsets of its own cell in the shared-memory rings and
+// absolute tensor-memory addresses of its columns, so that each access adds at
+// most a constant.
 template <class C>
 struct SlimSlots {
     typedef SlimShape<C> SS;
     static constexpr int PLANE = C::PLANE, NRS = SS::NRS, NBS = SS::NBS, NDT = SS::NDT, H = C::H;
-    int r0, r1, r2;          // R at p, p-1, p-2
-    int bb;                  // I, cI (p-1), cR (p-2), d (p)
-    int sbp, sbc;            // stage planes read (previous iteration) and written
+    int r0, r1, r2;          // R at p, p-1, p-2 (offset of the thread's cell in the R ring)
+    int bb;                  // I, cI (p-1), cR (p-2), d (p): the thread's cell in the batch rings
+    int sbp, sbc;            // its cell in the stage planes read (previous iteration) and written
     uint32_t w0, w1, w2;     // window planes: old, center, new
     uint32_t d[H + 1];       // d at planes p, p-1, ..., p-H
+    int rend, bend;          // ends of the rings (offsets of the thread's cell)
+    uint32_t dbeg, dend;     // first and one past the last d slot
     int bar;                 // barrier slot
     uint32_t par;            // its phase parity
-    __device__ __forceinline__ static SlimSlots at(int k)
+    __device__ __forceinline__ static SlimSlots at(int k, uint32_t tbase, int own)
     {
         SlimSlots x;
-        x.r0 = (k % NRS) * PLANE;
-        x.r1 = ((k + NRS - 1) % NRS) * PLANE;
-        x.r2 = ((k + NRS - 2) % NRS) * PLANE;
-        x.bb = (k % NBS) * PLANE;
-        x.sbp = ((k + 1) & 1) * PLANE;
-        x.sbc = (k & 1) * PLANE;
-        x.w0 = static_cast<uint32_t>((k % 3) * SS::PHASE_COLS);
-        x.w1 = static_cast<uint32_t>(((k + 1) % 3) * SS::PHASE_COLS);
-        x.w2 = static_cast<uint32_t>(((k + 2) % 3) * SS::PHASE_COLS);
+        x.r0 = own + (k % NRS) * PLANE;
+        x.r1 = own + ((k + NRS - 1) % NRS) * PLANE;
+        x.r2 = own + ((k + NRS - 2) % NRS) * PLANE;
+        x.bb = own + (k % NBS) * PLANE;
+        x.sbp = own + ((k + 1) & 1) * PLANE;
+        x.sbc = own + (k & 1) * PLANE;
+        x.w0 = tbase + static_cast<uint32_t>((k % 3) * SS::PHASE_COLS);
+        x.w1 = tbase + static_cast<uint32_t>(((k + 1) % 3) * SS::PHASE_COLS);
+        x.w2 = tbase + static_cast<uint32_t>(((k + 2) % 3) * SS::PHASE_COLS);
 #pragma unroll
         for (int j = 0; j <= H; ++j)
-            x.d[j] = static_cast<uint32_t>(SS::WIN_COLS + ((k - j + 2 * NDT) % NDT) * SS::SLOT);
+            x.d[j] = tbase + static_cast<uint32_t>(SS::WIN_COLS + ((k - j + 2 * NDT) % NDT) * SS::SLOT);
+        x.rend = own + NRS * PLANE;
+        x.bend = own + NBS * PLANE;
+        x.dbeg = tbase + SS::WIN_COLS;
+        x.dend = tbase + SS::WIN_COLS + NDT * SS::SLOT;
         x.bar = k % NBS;
         x.par = static_cast<uint32_t>((k / NBS) & 1);
         return x;
@@ -97,8 +105,10 @@ struct SlimSlots {
     {
         r2 = r1;
         r1 = r0;
-        r0 = r0 + PLANE == NRS * PLANE ? 0 : r0 + PLANE;
-        bb = bb + PLANE == NBS * PLANE ? 0 : bb + PLANE;
+        r0 += PLANE;
+        if (r0 == rend) r0 -= NRS * PLANE;
+        bb += PLANE;
+        if (bb == bend) bb -= NBS * PLANE;
         const int t = sbp;
         sbp = sbc;
         sbc = t;
@@ -108,7 +118,8 @@ struct SlimSlots {
         w2 = w;
 #pragma unroll
         for (int j = H; j > 0; --j) d[j] = d[j - 1];
-        d[0] = d[0] + SS::SLOT == SS::WIN_COLS + NDT * SS::SLOT ? SS::WIN_COLS : d[0] + SS::SLOT;
+        d[0] += SS::SLOT;
+        if (d[0] == dend) d[0] = dbeg;
         if (++bar == NBS) {
             bar = 0;
             par ^= 1u;
@@ -159,6 +170,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int own = r0 * W + qx * VEC;
     const int off_ym = (r0 > 0 ? r0 - 1 : r0) * W + qx * VEC;
     const int off_yp = (r0 + 1 < ROWS ? r0 + 1 : r0) * W + qx * VEC;
+    const int dym = off_ym - own, dyp = off_yp - own;   // the neighbouring rows' cells, from own
 
     if (warp == 0) tmem_alloc(&s_tmem, SS::NCOLS);
     if (tid == 0) {
@@ -264,6 +276,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         // The stages of iteration it (plane p) with its slots.
         auto stages = [&](const int it, const int p, const Slots &sl, auto FASTc) {
             constexpr bool FAST = decltype(FASTc)::value;
+            // this thread's cell in each ring slot of the iteration
             const Real *R0 = ringR + sl.r0;                  // R at p
             const Real *R1 = ringR + sl.r1;                  // R at p-1
             const Real *R2 = ringR + sl.r2;                  // R at p-2
@@ -294,33 +307,33 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     if (absorb) mq = maskz[qm];
                 }
                 Real zm[VEC], c[VEC], zp[VEC], ym[VEC], yp[VEC], dd[VEC], acc[VEC], cacc[VEC];
-                tmem_ld4(tbase + sl.d[s], dd);   // d at plane q
+                tmem_ld4(sl.d[s], dd);   // d at plane q
                 if (s == 1) {
-                    ld_vec<Real>(R2 + own, zm);
-                    ld_vec<Real>(R1 + own, c);
-                    ld_vec<Real>(R0 + own, zp);
-                    ld_vec<Real>(Ib + own, acc);
-                    if constexpr (KAHAN) ld_vec<Real>(CIb + own, cacc);
+                    ld_vec<Real>(R2, zm);
+                    ld_vec<Real>(R1, c);
+                    ld_vec<Real>(R0, zp);
+                    ld_vec<Real>(Ib, acc);
+                    if constexpr (KAHAN) ld_vec<Real>(CIb, cacc);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v)
                         if (p_out) zp[v] = 0.f;
-                    ld_vec<Real>(R1 + off_ym, ym);
-                    ld_vec<Real>(R1 + off_yp, yp);
+                    ld_vec<Real>(R1 + dym, ym);
+                    ld_vec<Real>(R1 + dyp, yp);
                     tmem_wait_ld();
                     after_wait(dd);
                 } else {
-                    tmem_ld4(tbase + sl.w0 + fcol(s - 2, 0), zm);
-                    tmem_ld4(tbase + sl.w1 + fcol(s - 2, 0), c);
-                    if (s >= 3 && KAHAN) tmem_ld4(tbase + sl.w0 + fcol(s - 3, 1), cacc);
+                    tmem_ld4(sl.w0 + fcol(s - 2, 0), zm);
+                    tmem_ld4(sl.w1 + fcol(s - 2, 0), c);
+                    if (s >= 3 && KAHAN) tmem_ld4(sl.w0 + fcol(s - 3, 1), cacc);
                     const Real *Sp = sb_prev + (s - 2) * 2 * PLANE;
-                    ld_vec<Real>(Sp + off_ym, ym);
-                    ld_vec<Real>(Sp + off_yp, yp);
+                    ld_vec<Real>(Sp + dym, ym);
+                    ld_vec<Real>(Sp + dyp, yp);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
                         zp[v] = prev[v];
                         acc[v] = zmh[v];
                     }
-                    if (s == 2 && KAHAN) ld_vec<Real>(CRb + own, cacc);
+                    if (s == 2 && KAHAN) ld_vec<Real>(CRb, cacc);
                     tmem_wait_ld();
                     after_wait(dd);
                     after_wait(zm);
@@ -362,7 +375,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                     // detector flux of step (s+1)/2: R^n at planes kd, kd+1 and the new I
                     if (odd && s < H && flux_owner && q == kd + 1) {
                         Real ilo[VEC];   // I at plane kd: the center of stage s's window
-                        tmem_ld4(tbase + sl.w1 + fcol(s - 1, 0), ilo);
+                        tmem_ld4(sl.w1 + fcol(s - 1, 0), ilo);
                         tmem_wait_ld();
                         after_wait(ilo);
                         if (store_row) {
@@ -379,19 +392,19 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 }
 
                 if (s < H) {
-                    tmem_st4(tbase + sl.w2 + fcol(s - 1, 0), out);
-                    if constexpr (KAHAN) tmem_st4(tbase + sl.w2 + fcol(s - 1, 1), cout);
+                    tmem_st4(sl.w2 + fcol(s - 1, 0), out);
+                    if constexpr (KAHAN) tmem_st4(sl.w2 + fcol(s - 1, 1), cout);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
                         prev[v] = out[v];
                         zmh[v] = zm[v];
                     }
-                    st_vec<Real>(sb_cur + (s - 1) * 2 * PLANE + own, out);
+                    st_vec<Real>(sb_cur + (s - 1) * 2 * PLANE, out);
                 } else {
                     // I of the last step: the center of F_{H-1}'s window
                     Real vi[VEC], vci[VEC];
-                    tmem_ld4(tbase + sl.w1 + fcol(H - 2, 0), vi);
-                    if constexpr (KAHAN) tmem_ld4(tbase + sl.w1 + fcol(H - 2, 1), vci);
+                    tmem_ld4(sl.w1 + fcol(H - 2, 0), vi);
+                    if constexpr (KAHAN) tmem_ld4(sl.w1 + fcol(H - 2, 1), vci);
                     tmem_wait_ld();
                     after_wait(vi);
                     if constexpr (KAHAN) after_wait(vci);
@@ -435,8 +448,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             tmem_wait_st();   // the previous iteration's window planes are in TMEM
             {
                 Real dp[VEC];
-                ld_vec<Real>(ringD + sl.bb + own, dp);
-                tmem_st4(tbase + sl.d[0], dp);
+                ld_vec<Real>(ringD + sl.bb, dp);
+                tmem_st4(sl.d[0], dp);
             }
             if constexpr (decltype(ONLY_FASTc)::value) {
                 stages(it, p, sl, std::true_type{});
@@ -454,19 +467,19 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const std::true_type only_fast{};
 
         if constexpr (MODE == kSlimRolled) {
-            Slots sl = Slots::at(0);
+            Slots sl = Slots::at(0, tbase, own);
             for (int it = 0; it < nit; ++it) {
                 if (!plane_step(it, sl, any)) break;
                 sl.advance();
             }
         } else if constexpr (MODE == kSlimUnrolled) {
             for (int it0 = 0; it0 < nit; it0 += kSlimU) {
-                if (!plane_step(it0, Slots::at(0), any)) break;
-                if (it0 + 1 >= nit || !plane_step(it0 + 1, Slots::at(1), any)) break;
-                if (it0 + 2 >= nit || !plane_step(it0 + 2, Slots::at(2), any)) break;
-                if (it0 + 3 >= nit || !plane_step(it0 + 3, Slots::at(3), any)) break;
-                if (it0 + 4 >= nit || !plane_step(it0 + 4, Slots::at(4), any)) break;
-                if (it0 + 5 >= nit || !plane_step(it0 + 5, Slots::at(5), any)) break;
+                if (!plane_step(it0, Slots::at(0, tbase, own), any)) break;
+                if (it0 + 1 >= nit || !plane_step(it0 + 1, Slots::at(1, tbase, own), any)) break;
+                if (it0 + 2 >= nit || !plane_step(it0 + 2, Slots::at(2, tbase, own), any)) break;
+                if (it0 + 3 >= nit || !plane_step(it0 + 3, Slots::at(3, tbase, own), any)) break;
+                if (it0 + 4 >= nit || !plane_step(it0 + 4, Slots::at(4, tbase, own), any)) break;
+                if (it0 + 5 >= nit || !plane_step(it0 + 5, Slots::at(5, tbase, own), any)) break;
             }
         } else {
             bool ok = true;
@@ -476,12 +489,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                                         p0 + kSlimU - 1 < fast_hi &&
                                         !(flux_owner && p0 <= kd + H && p0 + kSlimU - 1 >= kd + 2);
                 if (block_fast) {
-                    ok = plane_step(it0, Slots::at(0), only_fast) && plane_step(it0 + 1, Slots::at(1), only_fast) &&
-                         plane_step(it0 + 2, Slots::at(2), only_fast) &&
-                         plane_step(it0 + 3, Slots::at(3), only_fast) &&
-                         plane_step(it0 + 4, Slots::at(4), only_fast) && plane_step(it0 + 5, Slots::at(5), only_fast);
+                    ok = plane_step(it0, Slots::at(0, tbase, own), only_fast) && plane_step(it0 + 1, Slots::at(1, tbase, own), only_fast) &&
+                         plane_step(it0 + 2, Slots::at(2, tbase, own), only_fast) &&
+                         plane_step(it0 + 3, Slots::at(3, tbase, own), only_fast) &&
+                         plane_step(it0 + 4, Slots::at(4, tbase, own), only_fast) && plane_step(it0 + 5, Slots::at(5, tbase, own), only_fast);
                 } else {
-                    Slots sl = Slots::at(0);
+                    Slots sl = Slots::at(0, tbase, own);
                     for (int k = 0; k < kSlimU && it0 + k < nit && ok; ++k) {
                         ok = plane_step(it0 + k, sl, any);
                         sl.advance();
