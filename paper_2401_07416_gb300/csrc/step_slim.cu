@@ -61,39 +61,49 @@ struct SlimShape {
 };
 
 // Slots of one iteration (it = it0 + k, it0 a multiple of kSlimU), as this thread
-// uses them: element offsets of its own cell in the shared-memory rings and
-// absolute tensor-memory addresses of its columns, so that each access adds at
-// most a constant.
+// uses them: shared-memory addresses of its own cell in the rings and absolute
+// tensor-memory addresses of its columns, so that each access adds at most a
+// constant (folded into the instruction).  Ring layout from the first R slot, in
+// planes: R 0..5, I 6..8, d 9..11, then (Kahan) cI 12..14, cR 15..17, then the
+// stage planes.
 template <class C>
 struct SlimSlots {
     typedef SlimShape<C> SS;
     static constexpr int PLANE = C::PLANE, NRS = SS::NRS, NBS = SS::NBS, NDT = SS::NDT, H = C::H;
-    int r0, r1, r2;          // R at p, p-1, p-2 (offset of the thread's cell in the R ring)
-    int bb;                  // I, cI (p-1), cR (p-2), d (p): the thread's cell in the batch rings
-    int sbp, sbc;            // its cell in the stage planes read (previous iteration) and written
+    static constexpr uint32_t PB = 4u * PLANE;                    // bytes per plane
+    static constexpr uint32_t OFF_I = NRS * PB, OFF_D = OFF_I + NBS * PB;
+    static constexpr uint32_t OFF_CI = OFF_D + NBS * PB, OFF_CR = OFF_CI + NBS * PB;
+    static constexpr uint32_t OFF_SB = (C::KAHAN ? OFF_CR + NBS * PB : OFF_CI);
+    // from the I slot of a cell to the same cell of the other batch rings
+    static constexpr uint32_t D_FROM_I = OFF_D - OFF_I, CI_FROM_I = OFF_CI - OFF_I, CR_FROM_I = OFF_CR - OFF_I;
+    uint32_t r0, r1, r2;     // R at p, p-1, p-2
+    uint32_t bb;             // I at p-1 (cI, cR and d at fixed distances)
+    uint32_t sbp, sbc;       // stage planes read (previous iteration) and written
     uint32_t w0, w1, w2;     // window planes: old, center, new
     uint32_t d[H + 1];       // d at planes p, p-1, ..., p-H
-    int rend, bend;          // ends of the rings (offsets of the thread's cell)
+    uint32_t rend, bend;     // ends of the rings (the thread's cell one past the last slot)
     uint32_t dbeg, dend;     // first and one past the last d slot
     int bar;                 // barrier slot
     uint32_t par;            // its phase parity
-    __device__ __forceinline__ static SlimSlots at(int k, uint32_t tbase, int own)
+    // ring: shared address of the first R slot; own: the thread's cell in a plane
+    __device__ __forceinline__ static SlimSlots at(int k, uint32_t tbase, uint32_t ring, int own)
     {
         SlimSlots x;
-        x.r0 = own + (k % NRS) * PLANE;
-        x.r1 = own + ((k + NRS - 1) % NRS) * PLANE;
-        x.r2 = own + ((k + NRS - 2) % NRS) * PLANE;
-        x.bb = own + (k % NBS) * PLANE;
-        x.sbp = own + ((k + 1) & 1) * PLANE;
-        x.sbc = own + (k & 1) * PLANE;
+        const uint32_t cell = ring + 4u * static_cast<uint32_t>(own);
+        x.r0 = cell + (k % NRS) * PB;
+        x.r1 = cell + ((k + NRS - 1) % NRS) * PB;
+        x.r2 = cell + ((k + NRS - 2) % NRS) * PB;
+        x.bb = cell + OFF_I + (k % NBS) * PB;
+        x.sbp = cell + OFF_SB + ((k + 1) & 1) * PB;
+        x.sbc = cell + OFF_SB + (k & 1) * PB;
         x.w0 = tbase + static_cast<uint32_t>((k % 3) * SS::PHASE_COLS);
         x.w1 = tbase + static_cast<uint32_t>(((k + 1) % 3) * SS::PHASE_COLS);
         x.w2 = tbase + static_cast<uint32_t>(((k + 2) % 3) * SS::PHASE_COLS);
 #pragma unroll
         for (int j = 0; j <= H; ++j)
             x.d[j] = tbase + static_cast<uint32_t>(SS::WIN_COLS + ((k - j + 2 * NDT) % NDT) * SS::SLOT);
-        x.rend = own + NRS * PLANE;
-        x.bend = own + NBS * PLANE;
+        x.rend = cell + NRS * PB;
+        x.bend = cell + OFF_I + NBS * PB;
         x.dbeg = tbase + SS::WIN_COLS;
         x.dend = tbase + SS::WIN_COLS + NDT * SS::SLOT;
         x.bar = k % NBS;
@@ -105,11 +115,11 @@ struct SlimSlots {
     {
         r2 = r1;
         r1 = r0;
-        r0 += PLANE;
-        if (r0 == rend) r0 -= NRS * PLANE;
-        bb += PLANE;
-        if (bb == bend) bb -= NBS * PLANE;
-        const int t = sbp;
+        r0 += PB;
+        if (r0 == rend) r0 -= NRS * PB;
+        bb += PB;
+        if (bb == bend) bb -= NBS * PB;
+        const uint32_t t = sbp;
         sbp = sbc;
         sbc = t;
         const uint32_t w = w0;
@@ -126,6 +136,20 @@ struct SlimSlots {
         }
     }
 };
+
+// 16-byte shared-memory accesses at a 32-bit shared address (plus a constant).
+__device__ __forceinline__ void lds4(uint32_t a, float (&v)[4])
+{
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"(a)
+                 : "memory");
+}
+__device__ __forceinline__ void sts4(uint32_t a, const float (&v)[4])
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
+                 : "memory");
+}
 
 // MODE: how the z-march is laid out.
 //   kSlimUnrolled  unrolled by 6 with constant offsets: fewest instructions, but twelve
@@ -155,6 +179,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     Real *ringCR = ringCI + (KAHAN ? NBS : 0) * PLANE;   // Kahan only
     Real *sbuf = ringCR + (KAHAN ? NBS : 0) * PLANE;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sbuf + SS::NSB * PLANE);
+    const uint32_t uring = smem_u32(ringR);
+    static_assert(Slots::OFF_SB == static_cast<uint32_t>(4 * (NRS + NBS * (KAHAN ? 4 : 2)) * PLANE),
+                  "the slot layout follows the ring layout");
     __shared__ int s_item;
     __shared__ int s_abort;
     __shared__ uint32_t s_tmem;
@@ -276,15 +303,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         // The stages of iteration it (plane p) with its slots.
         auto stages = [&](const int it, const int p, const Slots &sl, auto FASTc) {
             constexpr bool FAST = decltype(FASTc)::value;
-            // this thread's cell in each ring slot of the iteration
-            const Real *R0 = ringR + sl.r0;                  // R at p
-            const Real *R1 = ringR + sl.r1;                  // R at p-1
-            const Real *R2 = ringR + sl.r2;                  // R at p-2
-            const Real *Ib = ringI + sl.bb;                  // I at p-1
-            [[maybe_unused]] const Real *CIb = ringCI + sl.bb;   // cI at p-1
-            [[maybe_unused]] const Real *CRb = ringCR + sl.bb;   // cR at p-2
-            const Real *sb_prev = sbuf + sl.sbp;
-            Real *sb_cur = sbuf + sl.sbc;
+            // neighbouring rows of the stage planes read (previous iteration)
+            const uint32_t sb_ym = sl.sbp + 4u * dym, sb_yp = sl.sbp + 4u * dyp;
             const bool p_out = !FAST && !zper && (p < 0 || p >= nz);
             Real zmh[VEC];    // z- neighbour of the previous stage = accumulator of this one
             Real prev[VEC];   // the previous stage's output: this stage's z+ neighbour
@@ -309,31 +329,30 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 Real zm[VEC], c[VEC], zp[VEC], ym[VEC], yp[VEC], dd[VEC], acc[VEC], cacc[VEC];
                 tmem_ld4(sl.d[s], dd);   // d at plane q
                 if (s == 1) {
-                    ld_vec<Real>(R2, zm);
-                    ld_vec<Real>(R1, c);
-                    ld_vec<Real>(R0, zp);
-                    ld_vec<Real>(Ib, acc);
-                    if constexpr (KAHAN) ld_vec<Real>(CIb, cacc);
+                    lds4(sl.r2, zm);                           // R at p-2
+                    lds4(sl.r1, c);                            // R at p-1
+                    lds4(sl.r0, zp);                           // R at p
+                    lds4(sl.bb, acc);                          // I at p-1
+                    if constexpr (KAHAN) lds4(sl.bb + Slots::CI_FROM_I, cacc);   // cI at p-1
 #pragma unroll
                     for (int v = 0; v < VEC; ++v)
                         if (p_out) zp[v] = 0.f;
-                    ld_vec<Real>(R1 + dym, ym);
-                    ld_vec<Real>(R1 + dyp, yp);
+                    lds4(sl.r1 + 4u * dym, ym);
+                    lds4(sl.r1 + 4u * dyp, yp);
                     tmem_wait_ld();
                     after_wait(dd);
                 } else {
                     tmem_ld4(sl.w0 + fcol(s - 2, 0), zm);
                     tmem_ld4(sl.w1 + fcol(s - 2, 0), c);
                     if (s >= 3 && KAHAN) tmem_ld4(sl.w0 + fcol(s - 3, 1), cacc);
-                    const Real *Sp = sb_prev + (s - 2) * 2 * PLANE;
-                    ld_vec<Real>(Sp + dym, ym);
-                    ld_vec<Real>(Sp + dyp, yp);
+                    lds4(sb_ym + (s - 2) * 2 * Slots::PB, ym);
+                    lds4(sb_yp + (s - 2) * 2 * Slots::PB, yp);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
                         zp[v] = prev[v];
                         acc[v] = zmh[v];
                     }
-                    if (s == 2 && KAHAN) ld_vec<Real>(CRb, cacc);
+                    if (s == 2 && KAHAN) lds4(sl.bb + Slots::CR_FROM_I, cacc);   // cR at p-2
                     tmem_wait_ld();
                     after_wait(dd);
                     after_wait(zm);
@@ -399,7 +418,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                         prev[v] = out[v];
                         zmh[v] = zm[v];
                     }
-                    st_vec<Real>(sb_cur + (s - 1) * 2 * PLANE, out);
+                    sts4(sl.sbc + (s - 1) * 2 * Slots::PB, out);
                 } else {
                     // I of the last step: the center of F_{H-1}'s window
                     Real vi[VEC], vci[VEC];
@@ -448,7 +467,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             tmem_wait_st();   // the previous iteration's window planes are in TMEM
             {
                 Real dp[VEC];
-                ld_vec<Real>(ringD + sl.bb, dp);
+                lds4(sl.bb + Slots::D_FROM_I, dp);
                 tmem_st4(sl.d[0], dp);
             }
             if constexpr (decltype(ONLY_FASTc)::value) {
@@ -467,19 +486,19 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const std::true_type only_fast{};
 
         if constexpr (MODE == kSlimRolled) {
-            Slots sl = Slots::at(0, tbase, own);
+            Slots sl = Slots::at(0, tbase, uring, own);
             for (int it = 0; it < nit; ++it) {
                 if (!plane_step(it, sl, any)) break;
                 sl.advance();
             }
         } else if constexpr (MODE == kSlimUnrolled) {
             for (int it0 = 0; it0 < nit; it0 += kSlimU) {
-                if (!plane_step(it0, Slots::at(0, tbase, own), any)) break;
-                if (it0 + 1 >= nit || !plane_step(it0 + 1, Slots::at(1, tbase, own), any)) break;
-                if (it0 + 2 >= nit || !plane_step(it0 + 2, Slots::at(2, tbase, own), any)) break;
-                if (it0 + 3 >= nit || !plane_step(it0 + 3, Slots::at(3, tbase, own), any)) break;
-                if (it0 + 4 >= nit || !plane_step(it0 + 4, Slots::at(4, tbase, own), any)) break;
-                if (it0 + 5 >= nit || !plane_step(it0 + 5, Slots::at(5, tbase, own), any)) break;
+                if (!plane_step(it0, Slots::at(0, tbase, uring, own), any)) break;
+                if (it0 + 1 >= nit || !plane_step(it0 + 1, Slots::at(1, tbase, uring, own), any)) break;
+                if (it0 + 2 >= nit || !plane_step(it0 + 2, Slots::at(2, tbase, uring, own), any)) break;
+                if (it0 + 3 >= nit || !plane_step(it0 + 3, Slots::at(3, tbase, uring, own), any)) break;
+                if (it0 + 4 >= nit || !plane_step(it0 + 4, Slots::at(4, tbase, uring, own), any)) break;
+                if (it0 + 5 >= nit || !plane_step(it0 + 5, Slots::at(5, tbase, uring, own), any)) break;
             }
         } else {
             bool ok = true;
@@ -489,12 +508,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                                         p0 + kSlimU - 1 < fast_hi &&
                                         !(flux_owner && p0 <= kd + H && p0 + kSlimU - 1 >= kd + 2);
                 if (block_fast) {
-                    ok = plane_step(it0, Slots::at(0, tbase, own), only_fast) && plane_step(it0 + 1, Slots::at(1, tbase, own), only_fast) &&
-                         plane_step(it0 + 2, Slots::at(2, tbase, own), only_fast) &&
-                         plane_step(it0 + 3, Slots::at(3, tbase, own), only_fast) &&
-                         plane_step(it0 + 4, Slots::at(4, tbase, own), only_fast) && plane_step(it0 + 5, Slots::at(5, tbase, own), only_fast);
+                    ok = plane_step(it0, Slots::at(0, tbase, uring, own), only_fast) && plane_step(it0 + 1, Slots::at(1, tbase, uring, own), only_fast) &&
+                         plane_step(it0 + 2, Slots::at(2, tbase, uring, own), only_fast) &&
+                         plane_step(it0 + 3, Slots::at(3, tbase, uring, own), only_fast) &&
+                         plane_step(it0 + 4, Slots::at(4, tbase, uring, own), only_fast) && plane_step(it0 + 5, Slots::at(5, tbase, uring, own), only_fast);
                 } else {
-                    Slots sl = Slots::at(0, tbase, own);
+                    Slots sl = Slots::at(0, tbase, uring, own);
                     for (int k = 0; k < kSlimU && it0 + k < nit && ok; ++k) {
                         ok = plane_step(it0 + k, sl, any);
                         sl.advance();
