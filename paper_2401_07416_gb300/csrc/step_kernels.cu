@@ -529,33 +529,33 @@ const Variant kVariants[] = {
     TDSE_VARIANT(1, 1, "f32_t1_w64_r48x2_pf2", float, 2, 16, 48, 2, false, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w128_r24x2_pf2", float, 2, 32, 24, 2, false, 2),
     Variant{1, 2, "f32_t2_roll_w32_r32x1_pf2_b2", &fill_roll_f32_t2_w32_r32x1_pf2_b2, &launch_roll_f32_t2_w32_r32x1_pf2_b2},
-    Variant{1, 2, "f32_t2_hyb_w32_r32x1_pf2_b2", &fill_hyb_f32_t2_w32_r32x1_pf2_b2, &launch_hyb_f32_t2_w32_r32x1_pf2_b2},
-    Variant{1, 2, "f32_t2_tmem_w32_r32x1_pf3_b2", &fill_tmem_f32_t2_w32_r32x1_pf3_b2, &launch_tmem_f32_t2_w32_r32x1_pf3_b2},
     Variant{1, 2, "f32_t2_roll_w32_r32x1_pf3_b2", &fill_roll_f32_t2_w32_r32x1_pf3_b2, &launch_roll_f32_t2_w32_r32x1_pf3_b2},
+    Variant{1, 2, "f32_t2_tmem_w32_r32x1_pf3_b2", &fill_tmem_f32_t2_w32_r32x1_pf3_b2, &launch_tmem_f32_t2_w32_r32x1_pf3_b2},
+    Variant{1, 2, "f32_t2_tmem_w32_r32x1_pf4_b2", &fill_tmem_f32_t2_w32_r32x1_pf4_b2, &launch_tmem_f32_t2_w32_r32x1_pf4_b2},
     Variant{1, 2, "f32_t2_roll_r32x1_pf3", &fill_roll_f32_t2_r32x1_pf3, &launch_roll_f32_t2_r32x1_pf3},
+    Variant{1, 2, "f32_t2_tmem_r32x1_pf3", &fill_tmem_f32_t2_r32x1_pf3, &launch_tmem_f32_t2_r32x1_pf3},
+    Variant{1, 2, "f32_t2_tmem_r32x1_pf4", &fill_tmem_f32_t2_r32x1_pf4, &launch_tmem_f32_t2_r32x1_pf4},
+    Variant{1, 2, "f32_t2_tmem_r32x2_pf2", &fill_tmem_f32_t2_r32x2_pf2, &launch_tmem_f32_t2_r32x2_pf2},
+    Variant{1, 2, "f32_t2_hyb_w32_r32x1_pf2_b2", &fill_hyb_f32_t2_w32_r32x1_pf2_b2, &launch_hyb_f32_t2_w32_r32x1_pf2_b2},
     Variant{1, 2, "f32_t2_ws_w32_r32x1_pf3_b2", &fill_ws_f32_t2_w32_r32x1_pf3_b2, &launch_ws_f32_t2_w32_r32x1_pf3_b2},
     Variant{1, 2, "f32_t2_ws_w32_r32x1_pf4_b2", &fill_ws_f32_t2_w32_r32x1_pf4_b2, &launch_ws_f32_t2_w32_r32x1_pf4_b2},
-    Variant{1, 2, "f32_t2_tmem_w32_r32x1_pf4_b2", &fill_tmem_f32_t2_w32_r32x1_pf4_b2, &launch_tmem_f32_t2_w32_r32x1_pf4_b2},
-    Variant{1, 2, "f32_t2_tmem_r32x1_pf4", &fill_tmem_f32_t2_r32x1_pf4, &launch_tmem_f32_t2_r32x1_pf4},
-    Variant{1, 2, "f32_t2_tmem_r32x1_pf3", &fill_tmem_f32_t2_r32x1_pf3, &launch_tmem_f32_t2_r32x1_pf3},
-    Variant{1, 2, "f32_t2_tmem_r32x2_pf2", &fill_tmem_f32_t2_r32x2_pf2, &launch_tmem_f32_t2_r32x2_pf2},
     TDSE_VARIANT(1, 2, "f32_t2_w64_r32x2_pf2", float, 4, 16, 32, 2, false, 2),
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x2_pf2", float, 2, 16, 32, 2, true, 2),
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x1_pf2", float, 2, 16, 32, 1, true, 2),
     Variant{2, 2, "k32_t2_roll_w32_r32x1_pf2_b2", &fill_roll_k32_t2_w32_r32x1_pf2_b2, &launch_roll_k32_t2_w32_r32x1_pf2_b2},
-    Variant{2, 2, "k32_t2_hyb_w32_r32x1_pf2_b2", &fill_hyb_k32_t2_w32_r32x1_pf2_b2, &launch_hyb_k32_t2_w32_r32x1_pf2_b2},
     Variant{2, 2, "k32_t2_tmem_w32_r32x1_pf2_b2", &fill_tmem_k32_t2_w32_r32x1_pf2_b2, &launch_tmem_k32_t2_w32_r32x1_pf2_b2},
-    Variant{2, 2, "k32_t2_roll_w32_r32x1_pf3_b2", &fill_roll_k32_t2_w32_r32x1_pf3_b2, &launch_roll_k32_t2_w32_r32x1_pf3_b2},
-    Variant{2, 2, "k32_t2_roll_r32x1_pf2", &fill_roll_k32_t2_r32x1_pf2, &launch_roll_k32_t2_r32x1_pf2},
-    Variant{2, 2, "k32_t2_roll_r32x1_pf3", &fill_roll_k32_t2_r32x1_pf3, &launch_roll_k32_t2_r32x1_pf3},
-    Variant{2, 2, "k32_t2_roll_w32_r28x1_pf2_b2", &fill_roll_k32_t2_w32_r28x1_pf2_b2, &launch_roll_k32_t2_w32_r28x1_pf2_b2},
-    Variant{2, 2, "k32_t2_slim_w32_r32x1_pf2_b2", &fill_slim_k32_t2_w32_r32x1_pf2_b2, &launch_slim_k32_t2_w32_r32x1_pf2_b2},
-    Variant{2, 2, "k32_t2_ws_w32_r32x1_pf2_b2", &fill_ws_k32_t2_w32_r32x1_pf2_b2, &launch_ws_k32_t2_w32_r32x1_pf2_b2},
     Variant{2, 2, "k32_t2_ws_r32x1_pf2", &fill_ws_k32_t2_r32x1_pf2, &launch_ws_k32_t2_r32x1_pf2},
+    Variant{2, 2, "k32_t2_roll_r32x1_pf2", &fill_roll_k32_t2_r32x1_pf2, &launch_roll_k32_t2_r32x1_pf2},
     Variant{2, 2, "k32_t2_tmem_r28x1_pf2", &fill_tmem_k32_t2_r28x1_pf2, &launch_tmem_k32_t2_r28x1_pf2},
-    Variant{2, 2, "k32_t2_tmem_r28x1_pf3", &fill_tmem_k32_t2_r28x1_pf3, &launch_tmem_k32_t2_r28x1_pf3},
     Variant{2, 2, "k32_t2_tmem_w32_r28x1_pf2_b2", &fill_tmem_k32_t2_w32_r28x1_pf2_b2, &launch_tmem_k32_t2_w32_r28x1_pf2_b2},
+    Variant{2, 2, "k32_t2_roll_w32_r28x1_pf2_b2", &fill_roll_k32_t2_w32_r28x1_pf2_b2, &launch_roll_k32_t2_w32_r28x1_pf2_b2},
     Variant{2, 2, "k32_t2_tmem_r32x1_pf2", &fill_tmem_k32_t2_r32x1_pf2, &launch_tmem_k32_t2_r32x1_pf2},
+    Variant{2, 2, "k32_t2_tmem_r28x1_pf3", &fill_tmem_k32_t2_r28x1_pf3, &launch_tmem_k32_t2_r28x1_pf3},
+    Variant{2, 2, "k32_t2_ws_w32_r32x1_pf2_b2", &fill_ws_k32_t2_w32_r32x1_pf2_b2, &launch_ws_k32_t2_w32_r32x1_pf2_b2},
+    Variant{2, 2, "k32_t2_slim_w32_r32x1_pf2_b2", &fill_slim_k32_t2_w32_r32x1_pf2_b2, &launch_slim_k32_t2_w32_r32x1_pf2_b2},
+    Variant{2, 2, "k32_t2_hyb_w32_r32x1_pf2_b2", &fill_hyb_k32_t2_w32_r32x1_pf2_b2, &launch_hyb_k32_t2_w32_r32x1_pf2_b2},
+    Variant{2, 2, "k32_t2_roll_r32x1_pf3", &fill_roll_k32_t2_r32x1_pf3, &launch_roll_k32_t2_r32x1_pf3},
+    Variant{2, 2, "k32_t2_roll_w32_r32x1_pf3_b2", &fill_roll_k32_t2_w32_r32x1_pf3_b2, &launch_roll_k32_t2_w32_r32x1_pf3_b2},
     TDSE_VARIANT(2, 2, "k32_t2_w64_r32x2_pf1", float, 4, 16, 32, 2, true, 1),
     Variant{1, 3, "f32_t3_tmem_r32x1_pf2", &fill_tmem_f32_t3_r32x1_pf2, &launch_tmem_f32_t3_r32x1_pf2},
     Variant{1, 3, "f32_t3_ws_r32x1_pf2", &fill_ws_f32_t3_r32x1_pf2, &launch_ws_f32_t3_r32x1_pf2},
