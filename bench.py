@@ -154,6 +154,16 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def kernel_function(variant: str) -> str:
+    """CUDA kernel that a fused-step variant launches (its name in ncu listings)."""
+    layout = variant.split("_")[2] if variant.count("_") >= 2 else ""
+    if layout in ("roll", "slim", "hyb"):
+        return "fused_step_slim_kernel"
+    if layout in ("tmem", "ws"):
+        return "fused_step_tmem_kernel"
+    return "fused_step_kernel"
+
+
 def ncu_traffic(variant: str, cells: int):
     """(DRAM bytes per launch of the dominant kernel from the committed ncu summary,
     scaled to `cells` grid nodes, or None; why it is None)."""
@@ -658,8 +668,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "traffic_source": traffic_note,
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS hbm_gbs)",
-                "kernel": f"{'fused_step_tmem_kernel' if 'tmem' in variant else 'fused_step_kernel'} "
-                          f"{variant} ({tb} steps per launch)",
+                "kernel": f"{kernel_function(variant)} {variant} ({tb} steps per launch)",
                 "algorithmic_bytes_per_launch": bytes_launch,
                 "bytes_per_node_per_launch": BYTES_PER_NODE[prec],
                 "avg_launch_ms": launch_ms, "launches": nlaunch,

@@ -474,12 +474,13 @@ __device__ __forceinline__ void observables_block(const MemberDev &m, int buf, d
     const Real *__restrict__ I = reinterpret_cast<const Real *>(m.I[buf]);
     const Real *__restrict__ D = reinterpret_cast<const Real *>(m.d);
     const int ngx = m.nx / V;
-    const long long ngrp = static_cast<long long>(ngx) * m.ny;
+    const int ngrp = ngx * m.ny;             // < 2^31: nx * ny is at most a few million
     const int nch = (m.nz + zch - 1) / zch;
-    const long long nitems = ngrp * nch;
+    const long long nitems = static_cast<long long>(ngrp) * nch;
     const Real cx = static_cast<Real>(m.cx), cy = static_cast<Real>(m.cy),
                cz = static_cast<Real>(m.cz);
-    const long long plane = m.plane, pitch = m.pitch;
+    const long long plane = m.plane;
+    const int pitch = static_cast<int>(m.pitch);
     auto ld = [](const Real *p, Real (&v)[V]) {
         if constexpr (V * sizeof(Real) == 16) {
             if constexpr (sizeof(Real) == 4) {
@@ -489,6 +490,9 @@ __device__ __forceinline__ void observables_block(const MemberDev &m, int buf, d
                 const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
                 v[0] = t.x; v[1] = t.y;
             }
+        } else if constexpr (V == 2 && sizeof(Real) == 4) {
+            const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+            v[0] = t.x; v[1] = t.y;
         } else {
 #pragma unroll
             for (int k = 0; k < V; ++k) v[k] = __ldg(p + k);
@@ -497,36 +501,40 @@ __device__ __forceinline__ void observables_block(const MemberDev &m, int buf, d
     double q = 0.0, pn = 0.0, e = 0.0;
     for (long long item = lb * static_cast<long long>(blockDim.x) + threadIdx.x;
          item < nitems; item += static_cast<long long>(nb) * blockDim.x) {
-        const long long grp = item % ngrp;
-        const int z0 = static_cast<int>(item / ngrp) * zch;
+        const int ch = static_cast<int>(item / ngrp);
+        const int grp = static_cast<int>(item - static_cast<long long>(ch) * ngrp);
+        const int z0 = ch * zch;
         const int z1 = min(z0 + zch, m.nz);
-        const int x0 = static_cast<int>(grp % ngx) * V, y = static_cast<int>(grp / ngx);
+        const int x0 = (grp % ngx) * V, y = grp / ngx;
         const long long base = static_cast<long long>(y + m.G) * pitch + (x0 + m.G);
-        const long long last = base + static_cast<long long>(m.nz - 1) * plane;
+        // running pointers to this column's node at plane z (advanced by one plane)
+        const Real *pr = R + base + static_cast<long long>(z0) * plane;
+        const Real *pi = I + base + static_cast<long long>(z0) * plane;
+        const Real *pd = D + base + static_cast<long long>(z0) * plane;
         Real rm[V], rc[V], im[V], ic[V];
         if (z0 > 0) {
-            ld(R + base + static_cast<long long>(z0 - 1) * plane, rm);
-            ld(I + base + static_cast<long long>(z0 - 1) * plane, im);
+            ld(pr - plane, rm);
+            ld(pi - plane, im);
         } else if (m.per_z) {
-            ld(R + last, rm);
-            ld(I + last, im);
+            ld(pr + static_cast<long long>(m.nz - 1) * plane, rm);
+            ld(pi + static_cast<long long>(m.nz - 1) * plane, im);
         } else {
 #pragma unroll
             for (int k = 0; k < V; ++k) rm[k] = im[k] = Real(0);
         }
-        ld(R + base + static_cast<long long>(z0) * plane, rc);
-        ld(I + base + static_cast<long long>(z0) * plane, ic);
+        ld(pr, rc);
+        ld(pi, ic);
         ColumnSum<Real> sq, sp, se;
-        // one plane at offset o, its z+1 neighbours given
-        auto plane_terms = [&](long long o, const Real (&rp)[V], const Real (&ip)[V]) {
+        // the plane at pr / pi / pd, its z+1 neighbours given
+        auto plane_terms = [&](const Real (&rp)[V], const Real (&ip)[V]) {
             Real d[V], ryp[V], rym[V], iyp[V], iym[V];
-            ld(D + o, d);
-            ld(R + o + pitch, ryp);
-            ld(R + o - pitch, rym);
-            ld(I + o + pitch, iyp);
-            ld(I + o - pitch, iym);
-            const Real rxl = __ldg(R + o - 1), rxr = __ldg(R + o + V);
-            const Real ixl = __ldg(I + o - 1), ixr = __ldg(I + o + V);
+            ld(pd, d);
+            ld(pr + pitch, ryp);
+            ld(pr - pitch, rym);
+            ld(pi + pitch, iyp);
+            ld(pi - pitch, iym);
+            const Real rxl = __ldg(pr - 1), rxr = __ldg(pr + V);
+            const Real ixl = __ldg(pi - 1), ixr = __ldg(pi + V);
 #pragma unroll
             for (int k = 0; k < V; ++k) {
                 const Real rsx = (k == 0 ? rxl : rc[k - 1]) + (k == V - 1 ? rxr : rc[k + 1]);
@@ -549,11 +557,13 @@ __device__ __forceinline__ void observables_block(const MemberDev &m, int buf, d
         const int zin = min(z1, m.nz - 1);   // planes whose z+1 neighbour lies in the grid
 #pragma unroll 2
         for (int z = z0; z < zin; ++z) {
-            const long long o = base + static_cast<long long>(z) * plane;
             Real rp[V], ip[V];
-            ld(R + o + plane, rp);
-            ld(I + o + plane, ip);
-            plane_terms(o, rp, ip);
+            ld(pr + plane, rp);
+            ld(pi + plane, ip);
+            plane_terms(rp, ip);
+            pr += plane;
+            pi += plane;
+            pd += plane;
         }
         if (z1 == m.nz) {   // top plane: periodic wrap or wall
             Real rp[V], ip[V];
@@ -564,7 +574,7 @@ __device__ __forceinline__ void observables_block(const MemberDev &m, int buf, d
 #pragma unroll
                 for (int k = 0; k < V; ++k) rp[k] = ip[k] = Real(0);
             }
-            plane_terms(last, rp, ip);
+            plane_terms(rp, ip);
         }
         q += sq.value();
         pn += sp.value();
@@ -576,7 +586,7 @@ __device__ __forceinline__ void observables_block(const MemberDev &m, int buf, d
 }
 
 template <typename Real, int V, int ZC>
-__global__ void __launch_bounds__(kObsThreads)
+__global__ void __launch_bounds__(kObsThreads, kObsBlocksPerSM)
     observables_kernel(MemberDev m, int buf, double *__restrict__ partials, int zch_arg)
 {
     __shared__ double sh[32];
@@ -587,7 +597,7 @@ __global__ void __launch_bounds__(kObsThreads)
 // of blocks contains it and does exactly the work of that member's block b - begin
 // in a launch of its own (same items, same order), so the sums are the same bits.
 template <typename Real, int V>
-__global__ void __launch_bounds__(kObsThreads)
+__global__ void __launch_bounds__(kObsThreads, kObsBlocksPerSM)
     observables_batch_kernel(const MemberDev *__restrict__ members, const ObsSlice *__restrict__ slices,
                              int nmembers, int buf, double *__restrict__ partials)
 {

@@ -158,6 +158,21 @@ __device__ __forceinline__ void st_vec<double>(double *p, const double (&v)[2])
     *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
 }
 
+// Global store of one vector with the streaming hint (st.global.cs: evicted first),
+// for output planes that this launch never reads back.
+template <typename Real>
+__device__ __forceinline__ void st_vec_stream(Real *p, const Real (&v)[VecOf<Real>::N]);
+template <>
+__device__ __forceinline__ void st_vec_stream<float>(float *p, const float (&v)[4])
+{
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+template <>
+__device__ __forceinline__ void st_vec_stream<double>(double *p, const double (&v)[2])
+{
+    __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+}
+
 // Rounded product that the compiler may not fuse into a following add: the
 // absorbing factor must round identically whether its product is stored
 // (one step per launch) or consumed in registers (several steps per launch).
@@ -318,7 +333,9 @@ __device__ __forceinline__ void fetch_item(const MemberDev *__restrict__ members
 
 // One output row of the last stage at offset o of the padded arrays: R, I (and the
 // compensation terms), plus the ghost copies of periodic axes when the row touches
-// a seam (both sides when an axis is shorter than twice the ghost width).
+// a seam (both sides when an axis is shorter than twice the ghost width).  The
+// stores are marked evict-first: this launch never reads its output planes, and in
+// L2 they would displace input planes whose halos neighbouring tiles still read.
 template <typename Real, bool KAHAN, int VEC>
 __device__ __forceinline__ void store_output_row(const ItemScalars &S, Real *outR, Real *outI,
                                                  Real *outCR, Real *outCI, long long o,
@@ -326,11 +343,12 @@ __device__ __forceinline__ void store_output_row(const ItemScalars &S, Real *out
                                                  const Real (&r)[VEC], const Real (&i)[VEC],
                                                  const Real (&cr)[VEC], const Real (&ci)[VEC])
 {
-    st_vec<Real>(outR + o, r);
-    st_vec<Real>(outI + o, i);
+    auto st_out = [](Real *p, const Real (&v)[VEC]) { st_vec_stream<Real>(p, v); };
+    st_out(outR + o, r);
+    st_out(outI + o, i);
     if constexpr (KAHAN) {
-        st_vec<Real>(outCR + o, cr);
-        st_vec<Real>(outCI + o, ci);
+        st_out(outCR + o, cr);
+        st_out(outCI + o, ci);
     }
     if (!seam) return;
     const int G = S.G, nx = S.nx, ny = S.ny;
@@ -348,11 +366,11 @@ __device__ __forceinline__ void store_output_row(const ItemScalars &S, Real *out
         for (int b = 0; b < ndx; ++b) {
             if (a == 0 && b == 0) continue;
             const long long og = o + dys[a] * pitch + dxs[b];
-            st_vec<Real>(outR + og, r);
-            st_vec<Real>(outI + og, i);
+            st_out(outR + og, r);
+            st_out(outI + og, i);
             if constexpr (KAHAN) {
-                st_vec<Real>(outCR + og, cr);
-                st_vec<Real>(outCI + og, ci);
+                st_out(outCR + og, cr);
+                st_out(outCI + og, ci);
             }
         }
 }

@@ -285,12 +285,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             const int L = L0 + j;
             uint64_t *bar = &bars[j % NBS];
             mbar_arrive_expect_tx(bar, SS::TX_BYTES);
-            tma_load_3d(ringR + (j % NRS) * PLANE, &M.tm_R[in_buf], bx, by, zwrap(L), bar);
-            tma_load_3d(ringD + (j % NBS) * PLANE, &M.tm_d, bx, by, zwrap(L), bar);
-            tma_load_3d(ringI + (j % NBS) * PLANE, &M.tm_I[in_buf], bx, by, zwrap(L - 1), bar);
+            auto load = [&](Real *dst, const CUtensorMap *map, int z) { tma_load_3d(dst, map, bx, by, z, bar); };
+            load(ringR + (j % NRS) * PLANE, &M.tm_R[in_buf], zwrap(L));
+            load(ringD + (j % NBS) * PLANE, &M.tm_d, zwrap(L));
+            load(ringI + (j % NBS) * PLANE, &M.tm_I[in_buf], zwrap(L - 1));
             if constexpr (KAHAN) {
-                tma_load_3d(ringCI + (j % NBS) * PLANE, &M.tm_cI[in_buf], bx, by, zwrap(L - 1), bar);
-                tma_load_3d(ringCR + (j % NBS) * PLANE, &M.tm_cR[in_buf], bx, by, zwrap(L - 2), bar);
+                load(ringCI + (j % NBS) * PLANE, &M.tm_cI[in_buf], zwrap(L - 1));
+                load(ringCR + (j % NBS) * PLANE, &M.tm_cR[in_buf], zwrap(L - 2));
             }
         };
         if (tid == 0) {

@@ -308,6 +308,33 @@ def test_every_fused_variant_bitwise_equal(T, name, precision):
             assert np.array_equal(a, b), (name, precision, tb, v)
 
 
+@pytest.mark.parametrize("precision", ["FP32", "FP32_KAHAN"])
+def test_z_chunk_lengths_bitwise_equal(T, precision):
+    """Any z-chunk length (short, ragged against nz, longer than the column) hands
+    each output node to exactly one work item that computes it the same way: states
+    and flux maps equal bit for bit."""
+    g = W.small_grid(76, 100, 40, h=(0.21, 0.19, 0.23), dt=0.004, bc=(0, 1, 1), mask=4,
+                     det_k=11, eta=0.5)                 # several tiles along x and y
+    V = W.random_potential(g, 106, 2.0)
+    L = g.lengths
+    p = W.Packet((0.5 * L[0], 0.45 * L[1], 0.55 * L[2]), (0.9, 1.1, 0.8), (0.4, -0.3, -1.8))
+    prec = getattr(T, precision)
+    ref = None
+    for chunk in (0, 9, 13, 17, 50, 1000):
+        s = make_sim(g, prec, 2)
+        T.tdse_set_chunk(s.ctx, 2, chunk)
+        s.set_potential(0, V)
+        s.set_packet(0, p)
+        s.step(14)
+        got = (*s.state(0), s.flux_map(0))
+        s.close()
+        if ref is None:
+            ref = got
+            continue
+        for a_, b_ in zip(got, ref):
+            assert np.array_equal(a_, b_), (precision, chunk)
+
+
 @pytest.mark.parametrize("precision", ["FP64", "FP32_KAHAN"])
 def test_eq10_absorbing_layer_matches_oracle(T, precision):
     """The paper's set-up of Eq. 10: one quadratic absorbing layer at the bottom of a
