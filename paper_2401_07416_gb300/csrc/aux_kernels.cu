@@ -875,12 +875,14 @@ void observables_shape(const MemberDev &m, int precision, int *nparts_out, int *
     const int vec = precision == 0 ? 2 : 4;          // one 16-byte vector per field and plane
     const bool vector = m.nx % vec == 0;
     const long long groups = static_cast<long long>(vector ? m.nx / vec : m.nx) * m.ny;
-    // z planes per work item: kObsZ on large grids; fewer (down to 4) where that
-    // would leave less than about one item per thread of kObsParts blocks, since a
-    // thread marches its planes one after the other (a 96 x 96 x 192 member: 4)
+    // z planes per work item: kObsZ on large grids; fewer (down to kObsZmin) where
+    // that would leave less than about one item per thread of kObsParts blocks, since
+    // a thread marches its planes one after the other (a 96 x 96 x 192 member: 16).
+    // Each item also reads the planes on either side of its chunk, so shorter chunks
+    // read more: 16 planes read 18.
     const long long want = (static_cast<long long>(kObsParts) * kObsThreads + groups - 1) / groups;
     const int zch = static_cast<int>(
-        std::min<long long>(kObsZ, std::max<long long>(4, (m.nz + want - 1) / want)));
+        std::min<long long>(kObsZ, std::max<long long>(kObsZmin, (m.nz + want - 1) / want)));
     const long long nitems = groups * ((m.nz + zch - 1) / zch);
     *zch_out = zch;
     *nparts_out = static_cast<int>(

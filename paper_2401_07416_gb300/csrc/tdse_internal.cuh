@@ -140,6 +140,7 @@ cudaError_t launch_observables_batch(const MemberDev *members, const ObsSlice *s
                                      cudaStream_t s);
 constexpr int kObsParts = 1216;     // fixed block count: the reduction order never changes
 constexpr int kObsZ = 64;           // largest z-chunk of an observables work item
+constexpr int kObsZmin = 16;        // smallest z-chunk of an observables work item
 constexpr int kObsThreads = 256;    // observables block size
 constexpr int kObsBlocksPerSM = 2;  // resident observables blocks per SM (up to 128 registers per thread)
 constexpr int kObsPartialsPerBlock = 5;   // Q, paper norm, energy, flux (last step, integrated)
