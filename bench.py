@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--variant", type=int, default=None,
                     help="kernel variant (with --tblock) instead of the autotuner's pick; "
                          "--ncu-case default 0")
+    ap.add_argument("--chunk", type=int, default=None,
+                    help="z-planes per work item with --variant (default: the makespan model's)")
     ap.add_argument("--no-extras", action="store_true", help="skip variants, e2e and CPU baseline")
     ap.add_argument("--adjoint-case", action="store_true",
                     help="one FP32+Kahan forward and adjoint of the 96x96x192 case (--steps steps) for ncu")
@@ -178,7 +180,10 @@ def ncu_traffic(variant: str, cells: int):
     h = kernel_source_hash()
     if e.get("source_hash") != h:
         return None, f"kernel sources changed since the capture ({e.get('source_hash')} != {h})"
-    return e["dram_bytes_per_launch"] * cells / e["cells"], "ncu capture on the 256x256x512 case, scaled by nodes"
+    if e["cells"] == cells:
+        return e["dram_bytes_per_launch"], f"single-pass ncu capture of this grid ({e.get('z_chunk')}-plane z-chunks)"
+    return (e["dram_bytes_per_launch"] * cells / e["cells"],
+            f"single-pass ncu capture of a {e['cells']}-node grid, scaled by nodes")
 
 
 # ------------------------------------------------------------------ CPU oracle timing
@@ -638,6 +643,8 @@ def main():
     s = make_ctx(T, wl, prec, tblock, autotune=not fixed)
     if fixed:
         T.tdse_set_variant(s.ctx, tblock, args.variant)
+        if args.chunk is not None:
+            T.tdse_set_chunk(s.ctx, tblock, args.chunk)
     tuning = s.tuning()
     V_dev = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
     T.tdse_get_potential(s.ctx, 0, V_dev)
@@ -769,7 +776,7 @@ def main():
                                "cos^2 absorbing layers, detector flux every step, "
                                "Q/E every 20 steps",
                    "precision": PREC_NAME[prec], "steps_per_launch": tb, "variant": variant,
-                   "nx": g.nx, "ny": g.ny, "nz": g.nz, "parallelism": f"replicas x{world}",
+                   "z_chunk": tuning["chunk"][tb], "nx": g.nx, "ny": g.ny, "nz": g.nz, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (state ~10 GB), no flush"},
         "roofline": roofline,
         "cpu_baseline": cpu,

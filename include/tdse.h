@@ -312,9 +312,9 @@ TDSE_API tdse_status tdse_get_profile(tdse_ctx *ctx, tdse_profile *out);
  * of steps per launch T (tdse_variant_count(precision, T) of them; a depth
  * without variants is not available for that precision).  tdse_autotune times
  * every variant on this context's own grids (`launches` launches each, after one
- * warm-up), keeps the fastest for each depth, tries it with z-chunks of 3/4 and
- * 1/2 of the makespan model's length (unless tdse_set_chunk fixed one) and keeps
- * the fastest, and, if the context was created with tblock = 0, picks the depth
+ * warm-up), keeps the fastest for each depth, tries it with z-chunks of 0.85,
+ * 0.7 and 0.5 of the makespan model's length (unless tdse_set_chunk fixed one) and
+ * keeps the fastest, and, if the context was created with tblock = 0, picks the depth
  * with the lowest time per step.  The state, flux
  * integral and step counter are saved before and restored after the trials.
  * Step sequences between two reductions are replayed from captured CUDA graphs

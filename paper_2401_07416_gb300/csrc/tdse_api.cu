@@ -1662,8 +1662,8 @@ tdse_status tdse_autotune(tdse_ctx *c, int launches)
         if (st == TDSE_OK && request == 0) {
             const int model = pl.chunk;
             int best_chunk = 0;
-            for (int frac4 : {3, 2}) {
-                const int L = model * frac4 / 4;
+            for (int frac20 : {17, 14, 10}) {
+                const int L = model * frac20 / 20;
                 if (L < 16) continue;
                 double per_step = 0.0;
                 pl.chunk_request = L;

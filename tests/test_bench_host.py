@@ -23,6 +23,8 @@ def test_traffic_is_scaled_by_nodes_and_tied_to_the_kernel_sources(tmp_path, mon
     monkeypatch.setattr(bench, "TRAFFIC_FILE", _traffic_file(tmp_path, {"v": entry}))
     t, why = bench.ncu_traffic("v", 25)
     assert t == 2500.0 and "scaled by nodes" in why
+    t, why = bench.ncu_traffic("v", 10)            # the captured grid itself: as captured
+    assert t == 1000.0 and "this grid" in why
     # a variant without a capture, and a capture taken on other sources, give None
     assert bench.ncu_traffic("w", 25)[0] is None
     stale = dict(entry, source_hash="0" * 16)
