@@ -49,6 +49,8 @@ TDSE_TMEM_DECL(ws_k32_t3_w32_r32x1_pf2)
 TDSE_TMEM_DECL(ws_f32_t3_r32x1_pf2)
 TDSE_TMEM_DECL(slim_k32_t2_w32_r32x1_pf2_b2)
 TDSE_TMEM_DECL(roll_k32_t2_w32_r32x1_pf2_b2)
+TDSE_TMEM_DECL(split_k32_t2_w32_r32x1_pf2_b2)
+TDSE_TMEM_DECL(split_f32_t2_w32_r32x1_pf2_b2)
 TDSE_TMEM_DECL(roll_k32_t2_w32_r28x1_pf2_b2)
 TDSE_TMEM_DECL(roll_f32_t2_w32_r32x1_pf2_b2)
 TDSE_TMEM_DECL(roll_k32_t2_w32_r32x1_pf3_b2)
@@ -529,6 +531,7 @@ const Variant kVariants[] = {
     TDSE_VARIANT(1, 1, "f32_t1_w64_r48x2_pf2", float, 2, 16, 48, 2, false, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w128_r24x2_pf2", float, 2, 32, 24, 2, false, 2),
     Variant{1, 2, "f32_t2_roll_w32_r32x1_pf2_b2", &fill_roll_f32_t2_w32_r32x1_pf2_b2, &launch_roll_f32_t2_w32_r32x1_pf2_b2},
+    Variant{1, 2, "f32_t2_split_w32_r32x1_pf2_b2", &fill_split_f32_t2_w32_r32x1_pf2_b2, &launch_split_f32_t2_w32_r32x1_pf2_b2},
     Variant{1, 2, "f32_t2_roll_w32_r32x1_pf3_b2", &fill_roll_f32_t2_w32_r32x1_pf3_b2, &launch_roll_f32_t2_w32_r32x1_pf3_b2},
     Variant{1, 2, "f32_t2_tmem_w32_r32x1_pf3_b2", &fill_tmem_f32_t2_w32_r32x1_pf3_b2, &launch_tmem_f32_t2_w32_r32x1_pf3_b2},
     Variant{1, 2, "f32_t2_tmem_w32_r32x1_pf4_b2", &fill_tmem_f32_t2_w32_r32x1_pf4_b2, &launch_tmem_f32_t2_w32_r32x1_pf4_b2},
@@ -553,6 +556,7 @@ const Variant kVariants[] = {
     Variant{2, 2, "k32_t2_tmem_r28x1_pf3", &fill_tmem_k32_t2_r28x1_pf3, &launch_tmem_k32_t2_r28x1_pf3},
     Variant{2, 2, "k32_t2_ws_w32_r32x1_pf2_b2", &fill_ws_k32_t2_w32_r32x1_pf2_b2, &launch_ws_k32_t2_w32_r32x1_pf2_b2},
     Variant{2, 2, "k32_t2_slim_w32_r32x1_pf2_b2", &fill_slim_k32_t2_w32_r32x1_pf2_b2, &launch_slim_k32_t2_w32_r32x1_pf2_b2},
+    Variant{2, 2, "k32_t2_split_w32_r32x1_pf2_b2", &fill_split_k32_t2_w32_r32x1_pf2_b2, &launch_split_k32_t2_w32_r32x1_pf2_b2},
     Variant{2, 2, "k32_t2_hyb_w32_r32x1_pf2_b2", &fill_hyb_k32_t2_w32_r32x1_pf2_b2, &launch_hyb_k32_t2_w32_r32x1_pf2_b2},
     Variant{2, 2, "k32_t2_roll_r32x1_pf3", &fill_roll_k32_t2_r32x1_pf3, &launch_roll_k32_t2_r32x1_pf3},
     Variant{2, 2, "k32_t2_roll_w32_r32x1_pf3_b2", &fill_roll_k32_t2_w32_r32x1_pf3_b2, &launch_roll_k32_t2_w32_r32x1_pf3_b2},

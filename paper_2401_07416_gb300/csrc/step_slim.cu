@@ -158,7 +158,13 @@ __device__ __forceinline__ void sts4(uint32_t a, const float (&v)[4])
 //   kSlimHybrid    blocks of 6 planes that all take the fast path run unrolled (six
 //                  copies of the fast stages), every other block the rolled loop.
 constexpr int kSlimUnrolled = 0, kSlimRolled = 1, kSlimHybrid = 2;
-template <class C, int MODE>
+// SPLIT: the CTA barrier per plane is split.  Each warp waits for its plane's loads
+// itself, runs stage 1 (which reads only the loaded rings and its own tensor
+// memory), then waits on an mbarrier that every warp arrives on when it finishes a
+// plane; only then does it publish stage 1's row to the stage plane and run the
+// stages that read the other warps' rows.  The loading thread refills a ring slot
+// after that same wait.  So a warp's stage 1 overlaps the other warps' last stages.
+template <class C, int MODE, bool SPLIT = false>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fused_step_slim_kernel(const MemberDev *__restrict__ members, const WorkDev *__restrict__ work,
                            int *counter, int *status, int in_buf, unsigned long long wait_ns)
@@ -184,6 +190,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                   "the slot layout follows the ring layout");
     __shared__ int s_item;
     __shared__ int s_abort;
+    __shared__ uint64_t s_done;   // SPLIT: every warp has finished the plane
     __shared__ uint32_t s_tmem;
     __shared__ ItemScalars S;
 
@@ -203,6 +210,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     if (tid == 0) {
         s_abort = 0;
         for (int b = 0; b < NBS; ++b) mbar_init(&bars[b], 1);
+        if constexpr (SPLIT) mbar_init(&s_done, C::NT / 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tmem_fence_before_sync();
@@ -266,11 +274,16 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         // barriers restart their phases with each item (every load of the previous
         // item has been waited for)
         if (tid == 0) {
-            if (!first_item)
+            if (!first_item) {
                 for (int b = 0; b < NBS; ++b) {
                     mbar_inval(&bars[b]);
                     mbar_init(&bars[b], 1);
                 }
+                if constexpr (SPLIT) {
+                    mbar_inval(&s_done);
+                    mbar_init(&s_done, C::NT / 32);
+                }
+            }
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         first_item = false;
@@ -302,15 +315,19 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         int waited = 0;
 
         // The stages of iteration it (plane p) with its slots.
-        auto stages = [&](const int it, const int p, const Slots &sl, auto FASTc) {
+        // stage-to-stage registers (kept across the two halves of a split plane)
+        Real zmh[VEC];    // z- neighbour of the previous stage = accumulator of this one
+        Real prev[VEC];   // the previous stage's output: this stage's z+ neighbour
+        Real held[VEC];   // SPLIT: stage 1's row, published after the plane barrier
+        bool has_held = false;
+        auto stages = [&](const int it, const int p, const Slots &sl, auto FASTc, auto SLOc, auto SHIc) {
             constexpr bool FAST = decltype(FASTc)::value;
+            constexpr int SLO = decltype(SLOc)::value, SHI = decltype(SHIc)::value;
             // neighbouring rows of the stage planes read (previous iteration)
             const uint32_t sb_ym = sl.sbp + 4u * dym, sb_yp = sl.sbp + 4u * dyp;
             const bool p_out = !FAST && !zper && (p < 0 || p >= nz);
-            Real zmh[VEC];    // z- neighbour of the previous stage = accumulator of this one
-            Real prev[VEC];   // the previous stage's output: this stage's z+ neighbour
 #pragma unroll
-            for (int s = 1; s <= H; ++s) {
+            for (int s = SLO; s <= SHI; ++s) {
                 if (!FAST && it < 2 * s) continue;   // pipeline filling
                 if (s > smax_w) continue;            // rows outside the cone
                 const int q = p - s;
@@ -419,7 +436,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                         prev[v] = out[v];
                         zmh[v] = zm[v];
                     }
-                    sts4(sl.sbc + (s - 1) * 2 * Slots::PB, out);
+                    if (SPLIT && s == 1) {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) held[v] = out[v];
+                        has_held = true;
+                    } else {
+                        sts4(sl.sbc + (s - 1) * 2 * Slots::PB, out);
+                    }
                 } else {
                     // I of the last step: the center of F_{H-1}'s window
                     Real vi[VEC], vci[VEC];
@@ -444,44 +467,90 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             }
         };
 
-        // One iteration: wait for plane L0 + it, refill, d to tensor memory, stages
-        // (ONLY_FAST: the caller knows the plane takes the fast path).
-        auto plane_step = [&](const int it, const Slots &sl, auto ONLY_FASTc) -> bool {
-            const int p = L0 + it;
-            if (tid == 0) {
-                if (mbar_wait_bounded(&bars[sl.bar], sl.par, wait_ns)) {
-                    waited = it + 1;
-                } else {
-                    atomicOr(status, 1);
-                    s_abort = 1;
-                }
-            }
-            __syncthreads();   // plane p has landed; the previous iteration's reads are done
-            if (s_abort) return false;
-            if (it + PF < nit) {
-                if (tid == 0) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue(it + PF);
-                }
-                issued = it + PF + 1;
-            }
-            tmem_wait_st();   // the previous iteration's window planes are in TMEM
-            {
-                Real dp[VEC];
-                lds4(sl.bb + Slots::D_FROM_I, dp);
-                tmem_st4(sl.d[0], dp);
-            }
+        // the stages SLO..SHI of plane p (ONLY_FAST: the caller knows the plane takes the fast path)
+        auto run_stages = [&](const int it, const int p, const Slots &sl, auto ONLY_FASTc, auto SLOc, auto SHIc) {
             if constexpr (decltype(ONLY_FASTc)::value) {
-                stages(it, p, sl, std::true_type{});
+                stages(it, p, sl, std::true_type{}, SLOc, SHIc);
             } else {
                 const bool fast = !tile_walls && it >= 2 * H && p >= fast_lo && p < fast_hi &&
                                   !(flux_owner && p >= kd + 2 && p <= kd + H);
                 if (fast)
-                    stages(it, p, sl, std::true_type{});
+                    stages(it, p, sl, std::true_type{}, SLOc, SHIc);
                 else
-                    stages(it, p, sl, std::false_type{});
+                    stages(it, p, sl, std::false_type{}, SLOc, SHIc);
             }
-            return true;
+        };
+        typedef std::integral_constant<int, 1> S1;
+        typedef std::integral_constant<int, 2> S2;
+        typedef std::integral_constant<int, H> SH;
+        // a bounded wait taken by a whole warp: it goes on only if every lane saw the
+        // phase complete; an expired wait raises the abort flag
+        auto warp_wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+            const int r = __reduce_min_sync(kFull, mbar_wait_or_abort(bar, parity, wait_ns, &s_abort));
+            if (r == 0) {
+                atomicOr(status, 1);
+                s_abort = 1;
+            }
+            return r == 1;
+        };
+
+        // One iteration: wait for plane L0 + it, refill, d to tensor memory, stages.
+        auto plane_step = [&](const int it, const Slots &sl, auto ONLY_FASTc) -> bool {
+            const int p = L0 + it;
+            if constexpr (!SPLIT) {
+                if (tid == 0) {
+                    if (mbar_wait_bounded(&bars[sl.bar], sl.par, wait_ns)) {
+                        waited = it + 1;
+                    } else {
+                        atomicOr(status, 1);
+                        s_abort = 1;
+                    }
+                }
+                __syncthreads();   // plane p has landed; the previous iteration's reads are done
+                if (s_abort) return false;
+                if (it + PF < nit) {
+                    if (tid == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(it + PF);
+                    }
+                    issued = it + PF + 1;
+                }
+                tmem_wait_st();   // the previous iteration's window planes are in TMEM
+                {
+                    Real dp[VEC];
+                    lds4(sl.bb + Slots::D_FROM_I, dp);
+                    tmem_st4(sl.d[0], dp);
+                }
+                run_stages(it, p, sl, ONLY_FASTc, S1{}, SH{});
+                return true;
+            } else {
+                if (!warp_wait(&bars[sl.bar], sl.par)) return false;   // plane p has landed
+                if (tid == 0) waited = it + 1;
+                tmem_wait_st();
+                {
+                    Real dp[VEC];
+                    lds4(sl.bb + Slots::D_FROM_I, dp);
+                    tmem_st4(sl.d[0], dp);
+                }
+                has_held = false;
+                run_stages(it, p, sl, ONLY_FASTc, S1{}, S1{});
+                // every warp has finished plane p - 1: its stage rows are readable, and
+                // the slots it read (the stage plane written next, the ring slot refilled
+                // next) are free
+                if (it > 0 && !warp_wait(&s_done, static_cast<uint32_t>((it - 1) & 1))) return false;
+                if (it + PF < nit) {
+                    if (tid == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(it + PF);
+                    }
+                    issued = it + PF + 1;
+                }
+                if (has_held) sts4(sl.sbc, held);
+                run_stages(it, p, sl, ONLY_FASTc, S2{}, SH{});
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(&s_done);
+                return true;
+            }
         };
         const std::false_type any{};
         const std::true_type only_fast{};
@@ -544,14 +613,14 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     if (warp == 0) tmem_dealloc(s_tmem, SS::NCOLS);
 }
 
-template <class C, int MODE>
+template <class C, int MODE, bool SPLIT>
 cudaError_t launch_slim_cfg(const StepLaunch &L)
 {
     typedef SlimShape<C> SS;
     static std::atomic<uint64_t> smem_allowed{0};   // one bit per device
-    cudaError_t e = allow_dynamic_smem(fused_step_slim_kernel<C, MODE>, SS::SMEM, smem_allowed);
+    cudaError_t e = allow_dynamic_smem(fused_step_slim_kernel<C, MODE, SPLIT>, SS::SMEM, smem_allowed);
     if (e != cudaSuccess) return e;
-    fused_step_slim_kernel<C, MODE><<<L.grid, C::NT, SS::SMEM, L.stream>>>(
+    fused_step_slim_kernel<C, MODE, SPLIT><<<L.grid, C::NT, SS::SMEM, L.stream>>>(
         L.members, L.work, L.counter, L.status, L.in_buf, L.wait_ns);
     return cudaGetLastError();
 }
@@ -570,14 +639,17 @@ void fill_slim_config(StepConfig *cfg)
 
 }  // namespace
 
-#define TDSE_SLIM_VARIANT(FN, MODE, ...)                                                \
-    cudaError_t launch_##FN(const StepLaunch &L) { return launch_slim_cfg<Cfg<__VA_ARGS__>, MODE>(L); } \
+#define TDSE_SLIM_VARIANT_S(FN, MODE, SPLIT, ...)                                        \
+    cudaError_t launch_##FN(const StepLaunch &L) { return launch_slim_cfg<Cfg<__VA_ARGS__>, MODE, SPLIT>(L); } \
     void fill_##FN(StepConfig *cfg) { fill_slim_config<Cfg<__VA_ARGS__>>(cfg); }
+#define TDSE_SLIM_VARIANT(FN, MODE, ...) TDSE_SLIM_VARIANT_S(FN, MODE, false, __VA_ARGS__)
 
 // Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan, planes prefetched, CTAs per SM,
 //     d kept in TMEM, own rings>; "slim": unrolled, "roll": rolled, "hyb": hybrid (MODE)
 TDSE_SLIM_VARIANT(slim_k32_t2_w32_r32x1_pf2_b2, kSlimUnrolled, float, 4, 8, 32, 1, true, 2, 2, true, true)
 TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf2_b2, kSlimRolled, float, 4, 8, 32, 1, true, 2, 2, true, true)
+TDSE_SLIM_VARIANT_S(split_k32_t2_w32_r32x1_pf2_b2, kSlimRolled, true, float, 4, 8, 32, 1, true, 2, 2, true, true)
+TDSE_SLIM_VARIANT_S(split_f32_t2_w32_r32x1_pf2_b2, kSlimRolled, true, float, 4, 8, 32, 1, false, 2, 2, true, true)
 TDSE_SLIM_VARIANT(roll_k32_t2_w32_r28x1_pf2_b2, kSlimRolled, float, 4, 8, 28, 1, true, 2, 2, true, true)
 TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf2_b2, kSlimRolled, float, 4, 8, 32, 1, false, 2, 2, true, true)
 TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf3_b2, kSlimRolled, float, 4, 8, 32, 1, true, 3, 2, true, true)

@@ -96,12 +96,31 @@ def test_allocator_null_gives_enomem(T, prec, tblock):
     assert run_with_allocator(T, prec, tblock, CountingAllocator(T)) == T.OK
 
 
-@pytest.mark.parametrize("prec,tblock", [("FP64", 1), ("FP32", 1), ("FP32", 2), ("FP32_KAHAN", 2)])
-def test_expired_wait_gives_etimeout_and_fails_the_context(T, prec, tblock):
+def variant_index(T, prec, tblock, name):
+    for v in range(T.tdse_variant_count(prec, tblock)):
+        g, _ = small_case()
+        ctx = T.tdse_create([T.params_from_grid(g, prec, tblock)])
+        try:
+            T.tdse_set_variant(ctx, tblock, v)
+            if T.tdse_get_tuning(ctx)["name"][tblock] == name:
+                return v
+        finally:
+            T.tdse_destroy(ctx)
+    raise LookupError(name)
+
+
+@pytest.mark.parametrize("prec,tblock,variant", [
+    ("FP64", 1, None), ("FP32", 1, None), ("FP32", 2, None), ("FP32_KAHAN", 2, None),
+    # split plane barrier: every warp waits for its loads and for the other warps itself
+    ("FP32", 2, "f32_t2_split_w32_r32x1_pf2_b2"), ("FP32_KAHAN", 2, "k32_t2_split_w32_r32x1_pf2_b2")])
+def test_expired_wait_gives_etimeout_and_fails_the_context(T, prec, tblock, variant):
     from paper_2401_07416_gb300.sim import Sim
     prec = getattr(T, prec)
+    v = None if variant is None else variant_index(T, prec, tblock, variant)
     g, p = small_case()
     s = Sim(g, precision=prec, tblock=tblock)
+    if v is not None:
+        T.tdse_set_variant(s.ctx, tblock, v)
     s.set_packet(0, p)
     s.step(tblock)                        # a normal launch first
     T.tdse_set_wait_limit(s.ctx, 0)
@@ -118,6 +137,8 @@ def test_expired_wait_gives_etimeout_and_fails_the_context(T, prec, tblock):
     ref = None
     for _ in range(2):
         with Sim(g, precision=prec, tblock=tblock) as s2:
+            if v is not None:
+                T.tdse_set_variant(s2.ctx, tblock, v)
             s2.set_packet(0, p)
             s2.step(20)
             got = s2.state(0)
