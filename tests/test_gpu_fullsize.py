@@ -3,9 +3,8 @@
 * Graph replay and every kernel variant chosen by the autotuner give results
   bitwise equal to direct launches (the per-node arithmetic never changes).
 * 128x128x256 diffraction run at full size: FP64 GPU vs oracle (1e-11) and FP32 /
-  FP32+Kahan vs oracle (rel L2 <= 1e-4, |dQ|/Q <= 1e-5) over 400 steps; over the
-  full 4000 steps FP32 / FP32+Kahan vs the oracle-pinned FP64 GPU path (same
-  tolerances; the FP64 oracle at this size takes minutes per run).
+  FP32+Kahan vs oracle (rel L2 <= 1e-4, |dQ|/Q <= 1e-5) over 400 steps, and all
+  three against the oracle over the full 4000 steps.
 * 48-member organic-film batch: one persistent launch per step block, autotuned,
   members bitwise equal to solo runs, one member vs the oracle.
 * 512x512x1024 throughput run: the state after 4 steps (the launch configuration
@@ -115,18 +114,31 @@ def test_config2_full_size_vs_oracle(T, config2_oracle):
         assert np.linalg.norm(F - Fo) < 1e-3 * np.linalg.norm(Fo)
 
 
-def test_config2_4000_steps_fp32_vs_fp64(T):
+def test_config2_4000_steps_vs_oracle(T):
+    """The whole 4000-step run of the 128x128x256 diffraction workload, every GPU
+    precision against the FP64 oracle directly (about a minute of oracle time on 16
+    host cores): FP64 to 1e-11 of the field's scale, FP32 and FP32+Kahan to the stated 1e-4 relative L2
+    in psi and 1e-5 relative drift of Q, the time-integrated flux map to 1e-3."""
     wl = W.config2(W.FP64)
-    R64, I64, F64, o64, _ = run(T, wl, T.FP64, wl.steps)
-    errs = {}
-    for prec in (T.FP32, T.FP32_KAHAN):
-        R, I, F, o, _ = run(T, wl, prec, wl.steps)
-        errs[prec] = (rel_l2(R, I, R64, I64), abs(o["Q"] - o64["Q"]) / o64["Q"],
-                      np.linalg.norm(F - F64) / np.linalg.norm(F64))
-        assert errs[prec][0] < 1e-4
-        assert errs[prec][1] < 1e-5
-        assert errs[prec][2] < 1e-3
-    print("config2 4000 steps vs FP64 GPU (rel L2 psi, |dQ|/Q, rel L2 F):", errs)
+    g = wl.grid
+    V = oracle.potential_atoms(g, wl.atoms)
+    R0, I0 = oracle.initial_state(g, wl.packet, V)
+    Ro, Io, Fo, _ = oracle.run(g, V, R0, I0, wl.steps)
+    oo = oracle.observables(g, V, Ro, Io)
+    R, I, F, o, _ = run(T, wl, T.FP64, wl.steps)
+    scale = max(np.abs(Ro).max(), np.abs(Io).max())
+    e64 = max(np.abs(R - Ro).max(), np.abs(I - Io).max()) / scale
+    errs = {"FP64": e64, "FP64_Q": abs(o["Q"] - oo["Q"]) / oo["Q"],
+            "FP64_F": np.abs(F - Fo).max() / np.abs(Fo).max()}
+    for name in ("FP32", "FP32_KAHAN"):
+        R, I, F, o, _ = run(T, wl, getattr(T, name), wl.steps)
+        errs[name] = (rel_l2(R, I, Ro, Io), abs(o["Q"] - oo["Q"]) / oo["Q"],
+                      np.linalg.norm(F - Fo) / np.linalg.norm(Fo))
+        assert errs[name][0] < 1e-4
+        assert errs[name][1] < 1e-5
+        assert errs[name][2] < 1e-3
+    print("config2 4000 steps vs oracle (FP64: max rel; FP32 forms: rel L2 psi, |dQ|/Q, rel L2 F):", errs)
+    assert e64 < TOL64 and errs["FP64_Q"] < TOL64 and errs["FP64_F"] < TOL64
 
 
 def test_config3_batch_autotuned_equals_solo_and_oracle(T):
