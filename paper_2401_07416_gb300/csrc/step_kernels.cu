@@ -523,9 +523,11 @@ struct Variant {
 
 // Kernel variants per (precision, fused steps): register-window kernels
 // (TDSE_VARIANT: Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan,
-// planes prefetched, CTAs per SM>) and tensor-memory-window kernels (step_tmem.cu).
-// Measured on GB300 (512x512x1024 slab): the first entry of each (precision, steps)
-// group is the fastest and the default; the others remain for the autotuner.
+// planes prefetched, CTAs per SM>), tensor-memory-window kernels with run-time rings
+// (step_tmem.cu: tmem_*, producer-warp ws_*) and with late loads and rolling slots
+// (step_slim.cu: roll_*, split_*, slim_*, hyb_*).  Measured on GB300 (512x512x1024
+// grid): the first entry of each (precision, steps) group is the fastest and the
+// default; the others remain for the autotuner.
 const Variant kVariants[] = {
     TDSE_VARIANT(1, 1, "f32_t1_w64_r24x2_pf2_b2", float, 2, 16, 24, 2, false, 2, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w64_r48x2_pf2", float, 2, 16, 48, 2, false, 2),

@@ -14,9 +14,14 @@
 //     R, read as a stencil at p-1 and by its owner at p and p-2, keeps 6 slots.
 //   - Every period is a divisor of 6: the R ring (6), the other rings and
 //     barriers (3), the three-plane windows (3), the double-buffered stage planes
-//     (2) and the d slots in tensor memory (6).  The z-march is unrolled by 6, so
-//     each iteration's slots are constants, and the barriers are re-initialised for
-//     each work item so that their phases restart with it.
+//     (2) and the d slots in tensor memory (6), and the barriers are
+//     re-initialised for each work item so that their phases restart with it.
+//     The z-march is laid out three ways (MODE): unrolled by 6, so that each
+//     iteration's slots are constants; a plain loop whose slots (32-bit shared
+//     addresses and absolute tensor-memory columns of this thread's cell) step by
+//     constants in registers, the default, whose code fits the instruction cache;
+//     or unrolled blocks of fast-path planes inside that loop.
+//   - SPLIT variants replace the CTA barrier per plane by per-warp waits (below).
 #include <type_traits>
 
 #include "step_common.cuh"
