@@ -349,7 +349,7 @@ def launch_stats(prof, depth):
 def ncu_case(args):
     """A mid-size (256x256x512, ~1.3 GB) run of the fused kernel for ncu captures:
     the 512x512x1024 workload's spacing, slab geometry scaled, two warm-up launches
-    then `--steps` steps, kernel variant fixed by --variant."""
+    then `--steps` steps, kernel variant fixed by --variant (z-chunk by --chunk)."""
     import torch
     torch.cuda.set_device(0)
     from paper_2401_07416_gb300 import build as B
@@ -363,6 +363,8 @@ def ncu_case(args):
     atoms = W.square_slab(8, 4, 1.6, 0.4 * 25.6, 12.8, 12.8, W.rng_for(5), 0.05)
     with Sim(g, precision=prec, tblock=tb) as s:
         T.tdse_set_variant(s.ctx, tb, args.variant or 0)
+        if args.chunk is not None:
+            T.tdse_set_chunk(s.ctx, tb, args.chunk)
         s.set_atoms(0, atoms)
         s.set_packet(0, W.Packet((6.4, 6.4, 12.74), (0.0, 0.0, 2.0), (0.0, 0.0, -1.9)))
         s.step(2 * tb)

@@ -312,11 +312,12 @@ TDSE_API tdse_status tdse_get_profile(tdse_ctx *ctx, tdse_profile *out);
  * of steps per launch T (tdse_variant_count(precision, T) of them; a depth
  * without variants is not available for that precision).  tdse_autotune times
  * every variant on this context's own grids (`launches` launches each, after one
- * warm-up), keeps the fastest for each depth, tries it with z-chunks of 0.85,
- * 0.7 and 0.5 of the makespan model's length (unless tdse_set_chunk fixed one) and
- * keeps the fastest, and, if the context was created with tblock = 0, picks the depth
- * with the lowest time per step.  The state, flux
- * integral and step counter are saved before and restored after the trials.
+ * warm-up) at z-chunks of 1, 0.7, 0.5, 0.35 and 0.2 of the makespan model's
+ * length for it (only the fixed one if tdse_set_chunk fixed one), then the
+ * fastest pair at 0.85, 0.9, 1.1 and 1.15 of its chunk, keeps the fastest for
+ * each depth and, if the context was created with tblock = 0, picks the depth
+ * with the lowest time per step.  The state, flux integral and step counter are
+ * saved before and restored after the trials.
  * Step sequences between two reductions are replayed from captured CUDA graphs
  * unless tdse_set_graphs(ctx, 0) was called (with profiling on, only sequences
  * whose launches all have one depth are replayed). */

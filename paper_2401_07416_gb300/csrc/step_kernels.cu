@@ -56,6 +56,10 @@ TDSE_TMEM_DECL(roll_f32_t2_w32_r32x1_pf2_b2)
 TDSE_TMEM_DECL(roll_k32_t2_w32_r32x1_pf3_b2)
 TDSE_TMEM_DECL(roll_k32_t2_r32x1_pf2)
 TDSE_TMEM_DECL(roll_k32_t2_r32x1_pf3)
+TDSE_TMEM_DECL(split_k32_t2_r32x1_pf2)
+TDSE_TMEM_DECL(split_k32_t2_r32x1_pf3)
+TDSE_TMEM_DECL(split_f32_t2_r32x1_pf2)
+TDSE_TMEM_DECL(split_f32_t2_r32x1_pf3)
 TDSE_TMEM_DECL(roll_f32_t2_w32_r32x1_pf3_b2)
 TDSE_TMEM_DECL(roll_f32_t2_r32x1_pf3)
 TDSE_TMEM_DECL(hyb_k32_t2_w32_r32x1_pf2_b2)
@@ -525,15 +529,18 @@ struct Variant {
 // (TDSE_VARIANT: Cfg<Real, 2T, threads per row, rows, rows per thread, Kahan,
 // planes prefetched, CTAs per SM>), tensor-memory-window kernels with run-time rings
 // (step_tmem.cu: tmem_*, producer-warp ws_*) and with late loads and rolling slots
-// (step_slim.cu: roll_*, split_*, slim_*, hyb_*).  Measured on GB300 (512x512x1024
-// grid): the first entry of each (precision, steps) group is the fastest and the
-// default; the others remain for the autotuner.
+// (step_slim.cu: roll_*, split_*, slim_*, hyb_*).  The first entry of each
+// (precision, steps) group is the default: the fastest on GB300 (512x512x1024 grid)
+// at the makespan model's z-chunk.  The autotuner times every entry at several
+// chunks; some (the one-CTA split forms) win only at chunks the model does not pick.
 const Variant kVariants[] = {
     TDSE_VARIANT(1, 1, "f32_t1_w64_r24x2_pf2_b2", float, 2, 16, 24, 2, false, 2, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w64_r48x2_pf2", float, 2, 16, 48, 2, false, 2),
     TDSE_VARIANT(1, 1, "f32_t1_w128_r24x2_pf2", float, 2, 32, 24, 2, false, 2),
     Variant{1, 2, "f32_t2_roll_w32_r32x1_pf2_b2", &fill_roll_f32_t2_w32_r32x1_pf2_b2, &launch_roll_f32_t2_w32_r32x1_pf2_b2},
     Variant{1, 2, "f32_t2_split_w32_r32x1_pf2_b2", &fill_split_f32_t2_w32_r32x1_pf2_b2, &launch_split_f32_t2_w32_r32x1_pf2_b2},
+    Variant{1, 2, "f32_t2_split_r32x1_pf2", &fill_split_f32_t2_r32x1_pf2, &launch_split_f32_t2_r32x1_pf2},
+    Variant{1, 2, "f32_t2_split_r32x1_pf3", &fill_split_f32_t2_r32x1_pf3, &launch_split_f32_t2_r32x1_pf3},
     Variant{1, 2, "f32_t2_roll_w32_r32x1_pf3_b2", &fill_roll_f32_t2_w32_r32x1_pf3_b2, &launch_roll_f32_t2_w32_r32x1_pf3_b2},
     Variant{1, 2, "f32_t2_tmem_w32_r32x1_pf3_b2", &fill_tmem_f32_t2_w32_r32x1_pf3_b2, &launch_tmem_f32_t2_w32_r32x1_pf3_b2},
     Variant{1, 2, "f32_t2_tmem_w32_r32x1_pf4_b2", &fill_tmem_f32_t2_w32_r32x1_pf4_b2, &launch_tmem_f32_t2_w32_r32x1_pf4_b2},
@@ -561,6 +568,8 @@ const Variant kVariants[] = {
     Variant{2, 2, "k32_t2_split_w32_r32x1_pf2_b2", &fill_split_k32_t2_w32_r32x1_pf2_b2, &launch_split_k32_t2_w32_r32x1_pf2_b2},
     Variant{2, 2, "k32_t2_hyb_w32_r32x1_pf2_b2", &fill_hyb_k32_t2_w32_r32x1_pf2_b2, &launch_hyb_k32_t2_w32_r32x1_pf2_b2},
     Variant{2, 2, "k32_t2_roll_r32x1_pf3", &fill_roll_k32_t2_r32x1_pf3, &launch_roll_k32_t2_r32x1_pf3},
+    Variant{2, 2, "k32_t2_split_r32x1_pf2", &fill_split_k32_t2_r32x1_pf2, &launch_split_k32_t2_r32x1_pf2},
+    Variant{2, 2, "k32_t2_split_r32x1_pf3", &fill_split_k32_t2_r32x1_pf3, &launch_split_k32_t2_r32x1_pf3},
     Variant{2, 2, "k32_t2_roll_w32_r32x1_pf3_b2", &fill_roll_k32_t2_w32_r32x1_pf3_b2, &launch_roll_k32_t2_w32_r32x1_pf3_b2},
     TDSE_VARIANT(2, 2, "k32_t2_w64_r32x2_pf1", float, 4, 16, 32, 2, true, 1),
     Variant{1, 3, "f32_t3_tmem_r32x1_pf2", &fill_tmem_f32_t3_r32x1_pf2, &launch_tmem_f32_t3_r32x1_pf2},

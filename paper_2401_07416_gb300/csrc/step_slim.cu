@@ -660,6 +660,10 @@ TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf2_b2, kSlimRolled, float, 4, 8, 32, 1,
 TDSE_SLIM_VARIANT(roll_k32_t2_w32_r32x1_pf3_b2, kSlimRolled, float, 4, 8, 32, 1, true, 3, 2, true, true)
 TDSE_SLIM_VARIANT(roll_k32_t2_r32x1_pf2, kSlimRolled, float, 4, 16, 32, 1, true, 2, 1, true, true)
 TDSE_SLIM_VARIANT(roll_k32_t2_r32x1_pf3, kSlimRolled, float, 4, 16, 32, 1, true, 3, 1, true, true)
+TDSE_SLIM_VARIANT_S(split_k32_t2_r32x1_pf2, kSlimRolled, true, float, 4, 16, 32, 1, true, 2, 1, true, true)
+TDSE_SLIM_VARIANT_S(split_k32_t2_r32x1_pf3, kSlimRolled, true, float, 4, 16, 32, 1, true, 3, 1, true, true)
+TDSE_SLIM_VARIANT_S(split_f32_t2_r32x1_pf2, kSlimRolled, true, float, 4, 16, 32, 1, false, 2, 1, true, true)
+TDSE_SLIM_VARIANT_S(split_f32_t2_r32x1_pf3, kSlimRolled, true, float, 4, 16, 32, 1, false, 3, 1, true, true)
 TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf3_b2, kSlimRolled, float, 4, 8, 32, 1, false, 3, 2, true, true)
 TDSE_SLIM_VARIANT(roll_f32_t2_r32x1_pf3, kSlimRolled, float, 4, 16, 32, 1, false, 3, 1, true, true)
 TDSE_SLIM_VARIANT(hyb_k32_t2_w32_r32x1_pf2_b2, kSlimHybrid, float, 4, 8, 32, 1, true, 2, 2, true, true)

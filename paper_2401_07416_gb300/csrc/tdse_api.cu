@@ -1647,35 +1647,51 @@ tdse_status tdse_autotune(tdse_ctx *c, int launches)
         };
         StepPlan &pl = c->plans[T];
         const int request = pl.chunk_request;   // a chunk fixed by tdse_set_chunk stays
-        for (int v = 0; v < step_variant_count(c->precision, T) && st == TDSE_OK; ++v) {
+        // Every variant at z-chunks of 1, 0.7, 0.5, 0.35 and 0.2 of the makespan
+        // model's length for it, then the best pair at 0.85 .. 1.15 of its chunk.
+        // Shorter chunks cost pipeline fill but keep neighbouring tiles close in z
+        // (their shared halo rows are still in L2), and the number of work items
+        // against the number of CTAs decides how full the last wave is; the model
+        // counts only the fill and the waves, so both are measured.
+        int best_req = request;
+        std::vector<int> tried;
+        auto try_chunk = [&](int v, int req) -> tdse_status {
             double per_step = 0.0;
-            if ((st = build_plan(c, T, v)) != TDSE_OK || (st = trial(&per_step)) != TDSE_OK) break;
+            pl.chunk_request = req;
+            TRY(build_plan(c, T, v));
+            TRY(trial(&per_step));
             if (per_step < best) {
                 best = per_step;
                 bestv = v;
+                best_req = req;
+            }
+            return TDSE_OK;
+        };
+        for (int v = 0; v < step_variant_count(c->precision, T) && st == TDSE_OK; ++v) {
+            pl.chunk_request = request;
+            if ((st = build_plan(c, T, v)) != TDSE_OK) break;
+            const int model = pl.chunk;
+            tried.clear();
+            for (int frac20 : {20, 14, 10, 7, 4}) {
+                if (request > 0 && frac20 != 20) break;
+                const int L = frac20 == 20 ? request : model * frac20 / 20;
+                if (frac20 != 20 && (L < 16 || std::find(tried.begin(), tried.end(), L) != tried.end())) continue;
+                tried.push_back(frac20 == 20 ? model : L);
+                if ((st = try_chunk(v, L)) != TDSE_OK) break;
             }
         }
-        if (st == TDSE_OK) st = build_plan(c, T, bestv);
-        // shorter z-chunks for the chosen variant: more pipeline fill per plane, but
-        // neighbouring tiles start and finish closer together and share their halo
-        // rows through L2 (the makespan model counts the first only)
         if (st == TDSE_OK && request == 0) {
-            const int model = pl.chunk;
-            int best_chunk = 0;
-            for (int frac20 : {17, 14, 10}) {
-                const int L = model * frac20 / 20;
-                if (L < 16) continue;
-                double per_step = 0.0;
-                pl.chunk_request = L;
-                if ((st = build_plan(c, T, bestv)) != TDSE_OK || (st = trial(&per_step)) != TDSE_OK) break;
-                if (per_step < best) {
-                    best = per_step;
-                    best_chunk = L;
+            if ((st = build_plan(c, T, bestv)) == TDSE_OK) {   // best_req as built: its chunk
+                const int L0 = pl.chunk;
+                for (int frac20 : {17, 18, 22, 23}) {
+                    const int L = L0 * frac20 / 20;
+                    if (L < 16 || L == L0) continue;
+                    if ((st = try_chunk(bestv, L)) != TDSE_OK) break;
                 }
             }
-            pl.chunk_request = best_chunk;
-            if (st == TDSE_OK) st = build_plan(c, T, bestv);
         }
+        pl.chunk_request = best_req;
+        if (st == TDSE_OK) st = build_plan(c, T, bestv);
         c->tuned_ms_per_step[T] = best;
     }
     cudaEventDestroy(e0);
