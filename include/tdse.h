@@ -141,9 +141,12 @@ TDSE_API tdse_status tdse_set_stream(tdse_ctx *ctx, void *cuda_stream);
  * (Sec. 2.3 interpolates a DFT potential; any gridded V is accepted).  V is a host
  * pointer (on_device = 0) or a device pointer (on_device = 1); it is copied into the
  * member's resident FP64 copy, from which the step's diagonal d = -2 (cx + cy + cz)
- * - cv V is built.  A host buffer may be reused when the call returns (it waits for
- * the copy); a device buffer once the stream has passed this call.  A failed copy
- * (ECUDA) leaves the member's potential undefined until the next successful call. */
+ * - cv V is built.  Page-locked host memory (cudaHostAlloc, cudaHostRegister, a
+ * pinned torch tensor) is read directly by the kernel that builds d; pageable host
+ * memory is copied first.  A host buffer may be reused when the call returns (it
+ * waits for the transfer); a device buffer once the stream has passed this call.  A
+ * failed transfer (ECUDA) leaves the member's potential undefined until the next
+ * successful call. */
 TDSE_API tdse_status tdse_set_potential(tdse_ctx *ctx, int member, const double *V, int on_device);
 
 /* Potential of member m interpolated from one periodic cell (Sec. 2.3: the

@@ -937,9 +937,21 @@ tdse_status tdse_set_potential(tdse_ctx *c, int member, const double *V, int on_
     Member &mb = c->m[member];
     const size_t bytes = static_cast<size_t>(mb.dev.nx) * mb.dev.ny * mb.dev.nz * sizeof(double);
     const double *Vd = V;
-    if (!on_device) {   // host V lands in the resident FP64 copy; d is built from it in place
-        CUDA_TRY(c, cudaMemcpyAsync(mb.V64, V, bytes, cudaMemcpyHostToDevice, c->stream));
-        Vd = mb.V64;
+    if (!on_device) {
+        // Pinned (page-locked, mapped) host V: the d kernel reads it over the host link
+        // itself and writes the resident FP64 copy on the way.  A copy-engine transfer
+        // issued right after a long run of kernels was measured at 135-155 ms for 2.1 GB
+        // where the kernel's reads took 19-25 ms (10 ms either way otherwise).  Pageable
+        // host V goes through a copy into the resident copy first.
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, V) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+            a.devicePointer != nullptr) {
+            Vd = static_cast<const double *>(a.devicePointer);
+        } else {
+            cudaGetLastError();   // a failed query leaves no error behind
+            CUDA_TRY(c, cudaMemcpyAsync(mb.V64, V, bytes, cudaMemcpyHostToDevice, c->stream));
+            Vd = mb.V64;
+        }
     }
     tdse_status st = potential_to_d(c, mb, Vd);
     if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // the host buffer is free again

@@ -112,7 +112,8 @@ def variant_index(T, prec, tblock, name):
 @pytest.mark.parametrize("prec,tblock,variant", [
     ("FP64", 1, None), ("FP32", 1, None), ("FP32", 2, None), ("FP32_KAHAN", 2, None),
     # split plane barrier: every warp waits for its loads and for the other warps itself
-    ("FP32", 2, "f32_t2_split_w32_r32x1_pf2_b2"), ("FP32_KAHAN", 2, "k32_t2_split_w32_r32x1_pf2_b2")])
+    ("FP32", 2, "f32_t2_split_w32_r32x1_pf2_b2"), ("FP32_KAHAN", 2, "k32_t2_split_w32_r32x1_pf2_b2"),
+    ("FP32_KAHAN", 2, "k32_t2_split_r32x1_pf3")])
 def test_expired_wait_gives_etimeout_and_fails_the_context(T, prec, tblock, variant):
     from paper_2401_07416_gb300.sim import Sim
     prec = getattr(T, prec)

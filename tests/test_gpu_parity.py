@@ -308,6 +308,40 @@ def test_every_fused_variant_bitwise_equal(T, name, precision):
             assert np.array_equal(a, b), (name, precision, tb, v)
 
 
+@pytest.mark.parametrize("precision", ["FP64", "FP32_KAHAN"])
+def test_potential_from_pinned_pageable_and_device_buffers(T, precision):
+    """tdse_set_potential takes V from pageable host memory (copied first), from
+    page-locked host memory (read directly by the d kernel; also at an offset of one
+    element, so not 16-byte aligned) and from the device: the resident V and the
+    states after 10 steps are the same bits."""
+    import torch
+    g, V, p = case("mixed", seed=7)
+    prec = getattr(T, precision)
+    n = V.size
+    big = torch.empty(n + 1, dtype=torch.float64, pin_memory=True)
+    big[1:] = torch.from_numpy(V.ravel())
+    pinned = torch.empty(V.shape, dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.from_numpy(V))
+    sources = {"pageable": V, "pinned": pinned, "pinned+8B": big[1:].view(V.shape),
+               "device": torch.from_numpy(V).cuda()}
+    ref = None
+    for name, src in sources.items():
+        s = make_sim(g, prec, 0)
+        T.tdse_set_potential(s.ctx, 0, src)
+        back = np.zeros(V.shape)
+        T.tdse_get_potential(s.ctx, 0, back)
+        assert np.array_equal(back, V), name
+        s.set_packet(0, p)
+        s.step(10)
+        got = (*s.state(0), s.flux_map(0))
+        s.close()
+        if ref is None:
+            ref = got
+            continue
+        for a_, b_ in zip(got, ref):
+            assert np.array_equal(a_, b_), name
+
+
 @pytest.mark.parametrize("precision", ["FP32", "FP32_KAHAN"])
 def test_z_chunk_lengths_bitwise_equal(T, precision):
     """Any z-chunk length (short, ragged against nz, longer than the column) hands
