@@ -159,7 +159,7 @@ def kernel_source_hash() -> str:
 def kernel_function(variant: str) -> str:
     """CUDA kernel that a fused-step variant launches (its name in ncu listings)."""
     layout = variant.split("_")[2] if variant.count("_") >= 2 else ""
-    if layout in ("roll", "slim", "hyb"):
+    if layout in ("roll", "slim", "hyb", "split"):
         return "fused_step_slim_kernel"
     if layout in ("tmem", "ws"):
         return "fused_step_tmem_kernel"

@@ -217,7 +217,8 @@ struct Cfg {
     static constexpr int TX = W - 2 * HX;
     static constexpr int TY = ROWS - 2 * H;
     static constexpr int NT = TPX * ROWS / RPT;
-    static constexpr int RW = 32 / TPX * RPT;           // rows per warp
+    static constexpr bool ROW_IN_WARP = 32 % TPX == 0;  // every region row sits inside one warp
+    static constexpr int RW = ROW_IN_WARP ? 32 / TPX * RPT : 0;   // rows per warp
     static constexpr int PLANE = W * ROWS;
     static constexpr int PLANE_BYTES = PLANE * static_cast<int>(sizeof(Real));
     static constexpr int NFC = KAHAN ? 2 : 1;           // a field (and its compensation) per slot
@@ -230,7 +231,7 @@ struct Cfg {
     static constexpr int NPLANES = (NR + NI) * NFC + ND + NSB;
     static constexpr size_t SMEM = static_cast<size_t>(NPLANES) * PLANE_BYTES + 8 * NB + 128;
     static constexpr uint32_t TX_BYTES = PLANE_BYTES * (2 * NFC + 1);
-    static_assert(TPX <= 32 && 32 % TPX == 0, "a region row must sit inside one warp");
+    static_assert(TPX <= 32 && NT % 32 == 0, "whole warps");
     static_assert(ROWS % RPT == 0, "rows per thread must divide the region");
     static_assert(TX > 0 && TY > 0, "halo larger than region");
     static_assert(W <= 256 && ROWS <= 256, "TMA box dimension limit");

@@ -60,6 +60,9 @@ TDSE_TMEM_DECL(split_k32_t2_r32x1_pf2)
 TDSE_TMEM_DECL(split_k32_t2_r32x1_pf3)
 TDSE_TMEM_DECL(split_f32_t2_r32x1_pf2)
 TDSE_TMEM_DECL(split_f32_t2_r32x1_pf3)
+TDSE_TMEM_DECL(split_k32_t2_w72_r32x1_pf2)
+TDSE_TMEM_DECL(split_f32_t2_w72_r32x1_pf2)
+TDSE_TMEM_DECL(split_f32_t2_w72_r32x1_pf3)
 TDSE_TMEM_DECL(roll_f32_t2_w32_r32x1_pf3_b2)
 TDSE_TMEM_DECL(roll_f32_t2_r32x1_pf3)
 TDSE_TMEM_DECL(hyb_k32_t2_w32_r32x1_pf2_b2)
@@ -77,6 +80,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     fused_step_kernel(const MemberDev *__restrict__ members, const WorkDev *__restrict__ work,
                       int *counter, int *status, int in_buf, unsigned long long wait_ns)
 {
+    static_assert(C::ROW_IN_WARP, "x neighbours by shuffles need each region row inside one warp");
     typedef typename C::Real Real;
     constexpr int H = C::H, VEC = C::VEC, W = C::W, ROWS = C::ROWS, PLANE = C::PLANE;
     constexpr int RPT = C::RPT, NB = C::NB, PF = C::PF, NR = C::NR, NI = C::NI, ND = C::ND;
@@ -552,6 +556,8 @@ const Variant kVariants[] = {
     Variant{1, 2, "f32_t2_ws_w32_r32x1_pf3_b2", &fill_ws_f32_t2_w32_r32x1_pf3_b2, &launch_ws_f32_t2_w32_r32x1_pf3_b2},
     Variant{1, 2, "f32_t2_ws_w32_r32x1_pf4_b2", &fill_ws_f32_t2_w32_r32x1_pf4_b2, &launch_ws_f32_t2_w32_r32x1_pf4_b2},
     TDSE_VARIANT(1, 2, "f32_t2_w64_r32x2_pf2", float, 4, 16, 32, 2, false, 2),
+    Variant{1, 2, "f32_t2_split_w72_r32x1_pf2", &fill_split_f32_t2_w72_r32x1_pf2, &launch_split_f32_t2_w72_r32x1_pf2},
+    Variant{1, 2, "f32_t2_split_w72_r32x1_pf3", &fill_split_f32_t2_w72_r32x1_pf3, &launch_split_f32_t2_w72_r32x1_pf3},
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x2_pf2", float, 2, 16, 32, 2, true, 2),
     TDSE_VARIANT(2, 1, "k32_t1_w64_r32x1_pf2", float, 2, 16, 32, 1, true, 2),
     Variant{2, 2, "k32_t2_roll_w32_r32x1_pf2_b2", &fill_roll_k32_t2_w32_r32x1_pf2_b2, &launch_roll_k32_t2_w32_r32x1_pf2_b2},
@@ -572,6 +578,7 @@ const Variant kVariants[] = {
     Variant{2, 2, "k32_t2_split_r32x1_pf3", &fill_split_k32_t2_r32x1_pf3, &launch_split_k32_t2_r32x1_pf3},
     Variant{2, 2, "k32_t2_roll_w32_r32x1_pf3_b2", &fill_roll_k32_t2_w32_r32x1_pf3_b2, &launch_roll_k32_t2_w32_r32x1_pf3_b2},
     TDSE_VARIANT(2, 2, "k32_t2_w64_r32x2_pf1", float, 4, 16, 32, 2, true, 1),
+    Variant{2, 2, "k32_t2_split_w72_r32x1_pf2", &fill_split_k32_t2_w72_r32x1_pf2, &launch_split_k32_t2_w72_r32x1_pf2},
     Variant{1, 3, "f32_t3_tmem_r32x1_pf2", &fill_tmem_f32_t3_r32x1_pf2, &launch_tmem_f32_t3_r32x1_pf2},
     Variant{1, 3, "f32_t3_ws_r32x1_pf2", &fill_ws_f32_t3_r32x1_pf2, &launch_ws_f32_t3_r32x1_pf2},
     Variant{1, 4, "f32_t4_tmem_w32_r40x1_pf2", &fill_tmem_f32_t4_w32_r40x1_pf2, &launch_tmem_f32_t4_w32_r40x1_pf2},

@@ -142,7 +142,13 @@ struct SlimSlots {
     }
 };
 
-// 16-byte shared-memory accesses at a 32-bit shared address (plus a constant).
+// Shared-memory accesses at a 32-bit shared address (plus a constant).
+__device__ __forceinline__ float lds1(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
 __device__ __forceinline__ void lds4(uint32_t a, float (&v)[4])
 {
     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -203,9 +209,16 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int warp = tid >> 5;
     const int qx = tid % C::TPX;
     const int r0 = tid / C::TPX;                         // this thread's region row
-    const int warp_row0 = warp * C::RW;
+    // region rows of this warp (a row may continue in the neighbouring warp when
+    // the threads of a row do not divide 32)
+    const int warp_row0 = (warp * 32) / C::TPX, warp_row1 = (warp * 32 + 31) / C::TPX;
     // stages this warp runs: its rows leave the cone of stage s for s > smax_w
-    const int smax_w = min(warp_row0 + C::RW - 1, ROWS - 1 - warp_row0);
+    const int smax_w = min(warp_row1, ROWS - 1 - warp_row0);
+    // lanes whose x neighbour in the row sits in another warp: they read it from
+    // the shared plane that holds the stage's input row
+    const int lane = tid & 31;
+    const bool x_from_smem_l = !C::ROW_IN_WARP && lane == 0 && qx > 0;
+    const bool x_from_smem_r = !C::ROW_IN_WARP && lane == 31 && qx < C::TPX - 1;
     const int own = r0 * W + qx * VEC;
     const int off_ym = (r0 > 0 ? r0 - 1 : r0) * W + qx * VEC;
     const int off_yp = (r0 + 1 < ROWS ? r0 + 1 : r0) * W + qx * VEC;
@@ -392,8 +405,15 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 
                 Real out[VEC], cout[VEC];
                 {
-                    const Real xl = __shfl_up_sync(kFull, c[VEC - 1], 1);
-                    const Real xr = __shfl_down_sync(kFull, c[0], 1);
+                    Real xl = __shfl_up_sync(kFull, c[VEC - 1], 1);
+                    Real xr = __shfl_down_sync(kFull, c[0], 1);
+                    if constexpr (!C::ROW_IN_WARP) {
+                        // the stage's input row: R at p-1 in its ring (stage 1), else the
+                        // stage plane of F_{s-1} written in the previous iteration
+                        const uint32_t crow = s == 1 ? sl.r1 : sl.sbp + (s - 2) * 2 * Slots::PB;
+                        if (x_from_smem_l) xl = lds1(crow - 4u);
+                        if (x_from_smem_r) xr = lds1(crow + 4u * VEC);
+                    }
                     update_row_f32<KAHAN, VEC>(odd, c, xl, xr, ym, yp, zm, zp, dd, acc, cacc, cx2, cy2,
                                                cz2, out, cout);
                 }
@@ -664,6 +684,10 @@ TDSE_SLIM_VARIANT_S(split_k32_t2_r32x1_pf2, kSlimRolled, true, float, 4, 16, 32,
 TDSE_SLIM_VARIANT_S(split_k32_t2_r32x1_pf3, kSlimRolled, true, float, 4, 16, 32, 1, true, 3, 1, true, true)
 TDSE_SLIM_VARIANT_S(split_f32_t2_r32x1_pf2, kSlimRolled, true, float, 4, 16, 32, 1, false, 2, 1, true, true)
 TDSE_SLIM_VARIANT_S(split_f32_t2_r32x1_pf3, kSlimRolled, true, float, 4, 16, 32, 1, false, 3, 1, true, true)
+// 72 x 32 boxes (64 x 24 tiles): 18 threads per row, so rows continue across warps
+TDSE_SLIM_VARIANT_S(split_k32_t2_w72_r32x1_pf2, kSlimRolled, true, float, 4, 18, 32, 1, true, 2, 1, true, true)
+TDSE_SLIM_VARIANT_S(split_f32_t2_w72_r32x1_pf2, kSlimRolled, true, float, 4, 18, 32, 1, false, 2, 1, true, true)
+TDSE_SLIM_VARIANT_S(split_f32_t2_w72_r32x1_pf3, kSlimRolled, true, float, 4, 18, 32, 1, false, 3, 1, true, true)
 TDSE_SLIM_VARIANT(roll_f32_t2_w32_r32x1_pf3_b2, kSlimRolled, float, 4, 8, 32, 1, false, 3, 2, true, true)
 TDSE_SLIM_VARIANT(roll_f32_t2_r32x1_pf3, kSlimRolled, float, 4, 16, 32, 1, false, 3, 1, true, true)
 TDSE_SLIM_VARIANT(hyb_k32_t2_w32_r32x1_pf2_b2, kSlimHybrid, float, 4, 8, 32, 1, true, 2, 2, true, true)

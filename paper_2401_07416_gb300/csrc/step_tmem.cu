@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(TmemSync<C, WS>::THREADS, C::MINB)
                            int *counter, int *status, int in_buf,
                            unsigned long long wait_ns)
 {
+    static_assert(C::ROW_IN_WARP, "x neighbours by shuffles need each region row inside one warp");
     typedef float Real;
     typedef TmemShape<C> TS;
     constexpr int H = C::H, VEC = C::VEC, W = C::W, ROWS = C::ROWS, PLANE = C::PLANE;
