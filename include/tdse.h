@@ -317,8 +317,9 @@ TDSE_API tdse_status tdse_get_profile(tdse_ctx *ctx, tdse_profile *out);
  * every variant on this context's own grids (`launches` launches each, after one
  * warm-up) at z-chunks of 1, 0.7, 0.5, 0.35 and 0.2 of the makespan model's
  * length for it (only the fixed one if tdse_set_chunk fixed one), then the
- * fastest pair at 0.85, 0.9, 1.1 and 1.15 of its chunk, keeps the fastest for
- * each depth and, if the context was created with tblock = 0, picks the depth
+ * fastest pair at 0.85, 0.9, 0.95, 1.05, 1.1 and 1.15 of its chunk; the four fastest pairs
+ * are then timed twice more in turn, each keeping its best time, and the fastest
+ * is kept for each depth.  If the context was created with tblock = 0, it picks the depth
  * with the lowest time per step.  The state, flux integral and step counter are
  * saved before and restored after the trials.
  * Step sequences between two reductions are replayed from captured CUDA graphs
