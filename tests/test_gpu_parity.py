@@ -208,6 +208,30 @@ def test_batched_members_equal_solo_runs(T):
             assert np.array_equal(batch[i][1], F)
 
 
+@pytest.mark.parametrize("precision", ["FP32_KAHAN", "FP32", "FP64"])
+def test_batch_graph_replay_equals_direct_launches(T, precision):
+    """Uneven members in one context: step sequences replayed from captured CUDA
+    graphs (the default) give the same states, flux maps and observation records,
+    bit for bit, as the same launches issued one by one."""
+    prec = getattr(T, precision)
+    cs = [case(n, seed=6) for n in ["walls", "slab", "mixed"]]
+    out = []
+    for graphs in (True, False):
+        s = make_sim([c[0] for c in cs], prec)
+        if not graphs:
+            T.tdse_set_graphs(s.ctx, False)
+        for i, (g, V, p) in enumerate(cs):
+            s.set_potential(i, V)
+            s.set_packet(i, p)
+        s.step(45)   # segments of 20, 20 and 5 steps between observation points
+        s.step(35)   # the 20-step segment again (a replay of its captured graph)
+        out.append([(*s.state(i), s.flux_map(i), s.history(i)) for i in range(len(cs))])
+        s.close()
+    for i in range(len(cs)):
+        for a, b in zip(out[0][i], out[1][i]):
+            assert np.array_equal(a, b), i
+
+
 @pytest.mark.parametrize("precision", ["FP32_KAHAN", "FP64"])
 def test_batched_reductions_equal_solo_reductions(T, precision):
     """A context with several members reduces all of them in one launch: every
