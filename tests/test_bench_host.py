@@ -1,5 +1,6 @@
 """Host-side helpers of bench.py, on CPU: the DRAM traffic lookup of the dominant
-kernel and the parsing of the clock samples taken during the timed region."""
+kernel, the kernel each variant name launches, and the parsing of the clock
+samples taken during the timed region."""
 import json
 import os
 import sys
@@ -55,3 +56,23 @@ def test_clock_summary_median_and_throttle_reasons():
 
 def test_clock_summary_without_sampler_says_unavailable():
     assert bench.ClockSampler(0).summary()["reasons"] == ["unavailable"]
+
+
+def test_kernel_named_for_each_variant_family():
+    """The roofline line names the CUDA kernel a variant launches (its name in ncu
+    launch lists): rolling-slot layouts, split barriers included, run the slim
+    kernel, tensor-memory and producer-warp layouts the tensor-memory kernel, and
+    the register-window variants the plain fused kernel."""
+    cases = {
+        "k32_t2_split_r32x1_pf3": "fused_step_slim_kernel",
+        "f32_t2_split_w72_r32x1_pf2": "fused_step_slim_kernel",
+        "k32_t2_roll_w32_r32x1_pf2_b2": "fused_step_slim_kernel",
+        "k32_t2_hyb_w32_r32x1_pf2_b2": "fused_step_slim_kernel",
+        "k32_t2_slim_w32_r32x1_pf2_b2": "fused_step_slim_kernel",
+        "k32_t2_tmem_w32_r32x1_pf2_b2": "fused_step_tmem_kernel",
+        "f32_t3_ws_r32x1_pf2": "fused_step_tmem_kernel",
+        "k32_t1_w64_r32x2_pf2": "fused_step_kernel",
+        "f64_t1_w64_r16x2_pf1_b2": "fused_step_kernel",
+    }
+    for variant, kernel in cases.items():
+        assert bench.kernel_function(variant) == kernel, variant
