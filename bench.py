@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=None,
                     help="z-planes per work item with --variant (default: the makespan model's)")
     ap.add_argument("--no-extras", action="store_true", help="skip variants, e2e and CPU baseline")
+    ap.add_argument("--batch-case", action="store_true",
+                    help="the 48-film batch (FP32+Kahan, variant and z-chunk fixed by --variant / "
+                         "--chunk, default 0 and the model's) for ncu: two launches, then --steps steps")
     ap.add_argument("--adjoint-case", action="store_true",
                     help="one FP32+Kahan forward and adjoint of the 96x96x192 case (--steps steps) for ncu")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -602,12 +605,39 @@ def adjoint_case(args):
                       "adjoint_s": el, "us_per_step": el / args.steps * 1e6}), flush=True)
 
 
+def batch_case(args):
+    """The 48-film batch of uneven grids (FP32+Kahan, two steps per launch) for ncu
+    captures of its fused launches: kernel variant fixed by --variant (z-chunk by
+    --chunk), one untimed two-step launch and a reduction, then `--steps` steps."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2401_07416_gb300 import build as B
+    B.build()
+    from paper_2401_07416_gb300 import tdse as T
+    from paper_2401_07416_gb300.sim import Sim
+    members = W.config3(48, W.FP32_KAHAN)
+    with Sim([m.grid for m in members], precision=W.FP32_KAHAN, tblock=2) as s:
+        T.tdse_set_variant(s.ctx, 2, args.variant or 0)
+        if args.chunk is not None:
+            T.tdse_set_chunk(s.ctx, 2, args.chunk)
+        for i, m in enumerate(members):
+            s.set_atoms(i, m.atoms)
+            s.set_packet(i, m.packet)
+        s.step(2)
+        s.step(args.steps)
+        torch.cuda.synchronize()
+        print(json.dumps({"batch_case": True, "members": len(members),
+                          "cells": sum(m.grid.cells for m in members), "tuning": s.tuning()}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.ncu_case:
         return ncu_case(args)
+    if args.batch_case:
+        return batch_case(args)
     if args.adjoint_case:
         return adjoint_case(args)
 
